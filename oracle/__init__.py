@@ -1,0 +1,265 @@
+"""VBCSR oracle: plain, slow, obviously correct CPU reference of the hot path.
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the repository smoke check and the
+benchmark's CPU-baseline / reference legs may import this package; the
+product library never does, and this package imports nothing from it.
+
+Contents, each following the passage it cites:
+
+* ``spmm``          Y = alpha H X + beta Y, scalar-expanded FP64 loop (C),
+                    Sec. III.B "Matrix multiplication"
+* ``spmm_adjoint``  Y = alpha H^T X + beta Y, Eq. (1) with real values (C)
+* ``sddmm``         D_ij = alpha A_i B_j^T + beta D_ij on the stored pattern (C);
+                    the gradient of H X with respect to the stored values
+* ``to_dense``      dense assembly of the block operator (Sec. II.A)
+* ``chebyshev_moments`` / ``moment_loss_grad``  the kernel-polynomial-method
+                    recurrence of Sec. V (t_{n+1} = 2 H~ t_n - t_{n-1}) and the
+                    reverse-mode gradient of L = sum_n mu_n^2
+
+A pattern argument is any object with the attributes ``row_bsize``,
+``col_bsize``, ``block_row_ptr`` and ``block_col_idx`` (numpy arrays).
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vbcsr_oracle.c")
+_SO = os.path.join(_HERE, "_lib", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile vbcsr_oracle.c with gcc into oracle/_lib/liboracle.so."""
+    with _lock:
+        if (not force and os.path.exists(_SO)
+                and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+            return _SO
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                        "-ffp-contract=off", _SRC, "-o", tmp], check=True)
+        os.replace(tmp, _SO)
+        return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        i64, p, d, i32 = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        L.oracle_spmm.argtypes = [i64, i64, p, p, p, p, p, i64, d, p, i64, d, p, i64, i64, i64, i32]
+        L.oracle_spmm_adjoint.argtypes = [i64, i64, p, p, p, p, p, i64, d, p, i64, d, p, i64]
+        L.oracle_sddmm.argtypes = [i64, i64, p, p, p, p, i64, d, p, i64, p, i64, d, p, i32]
+        for f in (L.oracle_spmm, L.oracle_spmm_adjoint, L.oracle_sddmm):
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    a = np.ascontiguousarray(a, dtype=dt)
+    return a, a.ctypes.data
+
+
+def _pat(pat):
+    rb, prb = _c(pat.row_bsize, np.int32)
+    cb, pcb = _c(pat.col_bsize, np.int32)
+    rp, prp = _c(pat.block_row_ptr, np.int64)
+    ci, pci = _c(pat.block_col_idx, np.int32)
+    return (rb, cb, rp, ci), (len(rb), len(cb), prb, pcb, prp, pci)
+
+
+def n_rows(pat) -> int:
+    return int(np.asarray(pat.row_bsize, np.int64).sum())
+
+
+def n_cols(pat) -> int:
+    return int(np.asarray(pat.col_bsize, np.int64).sum())
+
+
+# ----------------------------------------------------------------------------
+# the three products (C loops)
+
+
+def spmm(pat, values, X, alpha=1.0, beta=0.0, Y=None, row_range=None, nthreads=1):
+    """Y = alpha H X + beta Y (Sec. III.B). X is [n_cols, k] (row-major, any
+    leading dimension via a 2-D view). Returns Y as a new [n_rows, k] array
+    (Y is copied first when beta != 0). row_range=(b0, b1) restricts the
+    computation to block rows b0..b1-1; other rows of the result are then
+    whatever Y held (zero if Y is None)."""
+    keep, args = _pat(pat)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    k = X.shape[1]
+    out = np.zeros((n_rows(pat), k)) if Y is None else np.array(Y, dtype=np.float64, order="C", copy=True)
+    v, pv = _c(values, np.float64)
+    b0, b1 = (0, len(keep[0])) if row_range is None else row_range
+    rc = _load().oracle_spmm(*args, pv, k, float(alpha), X.ctypes.data, k, float(beta),
+                             out.ctypes.data, k, int(b0), int(b1), int(nthreads))
+    if rc:
+        raise MemoryError("oracle_spmm")
+    return out
+
+
+def spmm_adjoint(pat, values, X, alpha=1.0, beta=0.0, Y=None):
+    """Y = alpha H^T X + beta Y (Eq. 1, real values). X is [n_rows, k]."""
+    keep, args = _pat(pat)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    k = X.shape[1]
+    out = np.zeros((n_cols(pat), k)) if Y is None else np.array(Y, dtype=np.float64, order="C", copy=True)
+    v, pv = _c(values, np.float64)
+    rc = _load().oracle_spmm_adjoint(*args, pv, k, float(alpha), X.ctypes.data, k, float(beta),
+                                     out.ctypes.data, k)
+    if rc:
+        raise MemoryError("oracle_spmm_adjoint")
+    return out
+
+
+def sddmm(pat, A, B, alpha=1.0, beta=0.0, D=None, nthreads=1):
+    """D_ij[p,q] = alpha sum_c A[r_i+p, c] B[c_j+q, c] + beta D_ij[p,q] on the
+    stored blocks, in packed value order. A is [n_rows, k], B is [n_cols, k]."""
+    keep, args = _pat(pat)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    k = A.shape[1]
+    assert B.shape[1] == k
+    rb, cb, rp, ci = keep
+    nnz = int((rb[np.repeat(np.arange(len(rb)), np.diff(rp))].astype(np.int64) * cb[ci]).sum())
+    out = np.zeros(nnz) if D is None else np.array(D, dtype=np.float64, copy=True)
+    rc = _load().oracle_sddmm(*args, k, float(alpha), A.ctypes.data, k, B.ctypes.data, k,
+                              float(beta), out.ctypes.data, int(nthreads))
+    if rc:
+        raise MemoryError("oracle_sddmm")
+    return out
+
+
+# ----------------------------------------------------------------------------
+# dense assembly (Sec. II.A: block (i, j) is a dense b_i x b_j matrix at
+# scalar rows r_i.. and columns c_j..)
+
+
+def to_dense(pat, values) -> np.ndarray:
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(rb)])
+    c = np.concatenate([[0], np.cumsum(cb)])
+    H = np.zeros((r[-1], c[-1]))
+    off = 0
+    for i in range(len(rb)):
+        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
+            j = int(pat.block_col_idx[b])
+            n = int(rb[i] * cb[j])
+            H[r[i]:r[i + 1], c[j]:c[j + 1]] += np.asarray(values[off:off + n]).reshape(rb[i], cb[j])
+            off += n
+    return H
+
+
+# ----------------------------------------------------------------------------
+# kernel polynomial method (Sec. V): Chebyshev recurrence and moments
+
+
+def gershgorin_bounds(pat, values):
+    """(E_min, E_max) from Gershgorin discs over scalar rows: every eigenvalue
+    of a square H lies in [min_p (H_pp - R_p), max_p (H_pp + R_p)], R_p the
+    off-diagonal absolute row sum."""
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(rb)])
+    c = np.concatenate([[0], np.cumsum(cb)])
+    N = int(r[-1])
+    absrow = np.zeros(N)
+    diag = np.zeros(N)
+    off = 0
+    for i in range(len(rb)):
+        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
+            j = int(pat.block_col_idx[b])
+            blk = np.asarray(values[off:off + rb[i] * cb[j]]).reshape(rb[i], cb[j])
+            off += rb[i] * cb[j]
+            absrow[r[i]:r[i + 1]] += np.abs(blk).sum(axis=1)
+            for p in range(rb[i]):
+                col = c[j] + np.arange(cb[j])
+                hit = np.nonzero(col == r[i] + p)[0]
+                if len(hit):
+                    diag[r[i] + p] += blk[p, hit[0]]
+    radius = absrow - np.abs(diag)
+    return float((diag - radius).min()), float((diag + radius).max())
+
+
+def cheb_scale(pat, values, pad: float = 1.01):
+    """Centre c and half-width d so that H~ = (H - c I) / d has its spectrum
+    inside [-1, 1]: c = (E+ + E-)/2, d = pad * (E+ - E-)/2."""
+    lo, hi = gershgorin_bounds(pat, values)
+    return 0.5 * (hi + lo), pad * 0.5 * (hi - lo)
+
+
+def shift_scale_values(pat, values, c, d) -> np.ndarray:
+    """Packed values of H~ = (H - c I) / d (c subtracted on the scalar diagonal)."""
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(rb)])
+    cc = np.concatenate([[0], np.cumsum(cb)])
+    out = np.array(values, dtype=np.float64, copy=True)
+    off = 0
+    for i in range(len(rb)):
+        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
+            j = int(pat.block_col_idx[b])
+            for p in range(rb[i]):
+                for q in range(cb[j]):
+                    if r[i] + p == cc[j] + q:
+                        out[off + p * cb[j] + q] -= c
+            off += rb[i] * cb[j]
+    return out / d
+
+
+def chebyshev_vectors(pat, values_t, R, n_moments):
+    """t_0 = R, t_1 = H~ R, t_{n+1} = 2 H~ t_n - t_{n-1}; returns [t_0 .. t_{M-1}]."""
+    t = [np.array(R, dtype=np.float64)]
+    if n_moments > 1:
+        t.append(spmm(pat, values_t, t[0]))
+    for n in range(1, n_moments - 1):
+        t.append(spmm(pat, values_t, t[n], alpha=2.0, beta=-1.0, Y=t[n - 1]))
+    return t
+
+
+def chebyshev_moments(pat, values_t, R, n_moments) -> np.ndarray:
+    """mu_n = <R, t_n> / (N * n_vec) for n = 0 .. n_moments - 1 (stochastic
+    trace estimate of T_n(H~) / N, kernel polynomial method)."""
+    R = np.asarray(R, dtype=np.float64)
+    t = chebyshev_vectors(pat, values_t, R, n_moments)
+    return np.array([float(np.sum(R * tn)) for tn in t]) / R.size
+
+
+def moment_loss(pat, values_t, R, n_moments) -> float:
+    """L = sum_n mu_n^2."""
+    return float(np.sum(chebyshev_moments(pat, values_t, R, n_moments) ** 2))
+
+
+def moment_loss_grad(pat, values_t, R, n_moments) -> np.ndarray:
+    """dL/dH~ on the stored values, by the reverse recurrence:
+
+    g_n = dL/dt_n (direct) = 2 mu_n R / (N n_vec),
+    lam_n = g_n + 2 H~^T lam_{n+1} - lam_{n+2}   (lam_M = lam_{M+1} = 0, n >= 1),
+    dL/dH~ = lam_1 t_0^T + sum_{n=1}^{M-2} 2 lam_{n+1} t_n^T   (on the pattern).
+    """
+    R = np.asarray(R, dtype=np.float64)
+    M = n_moments
+    t = chebyshev_vectors(pat, values_t, R, M)
+    mu = np.array([float(np.sum(R * tn)) for tn in t]) / R.size
+    g = [2.0 * mu[n] * R / R.size for n in range(M)]
+    lam = [None] * (M + 2)
+    zero = np.zeros_like(R)
+    lam[M] = zero
+    lam[M + 1] = zero
+    for n in range(M - 1, 0, -1):
+        lam[n] = g[n] + spmm_adjoint(pat, values_t, lam[n + 1], alpha=2.0) - lam[n + 2]
+    grad = np.zeros(len(np.asarray(values_t)))
+    if M > 1:
+        grad += sddmm(pat, lam[1], t[0])
+    for n in range(1, M - 1):
+        grad += sddmm(pat, lam[n + 1], t[n], alpha=2.0)
+    return grad

@@ -1,0 +1,251 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against something the mathematics fixes: a
+hand-worked example, dense matrix algebra, SciPy's CSR / BSR products on the
+uniform-block special cases (Sec. II.B backend equivalence), symmetry and
+adjoint identities, closed forms of the Chebyshev recurrence, and central
+finite differences for the gradient.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import synthetic as syn
+from synthetic.structures import BlockPattern
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _hand():
+    with open(os.path.join(GOLDEN, "tiny_hand.json")) as f:
+        g = json.load(f)
+    pat = BlockPattern(np.array(g["row_bsize"]), np.array(g["col_bsize"]),
+                       np.array(g["block_row_ptr"]), np.array(g["block_col_idx"]))
+    return g, pat, np.array(g["values"], dtype=np.float64)
+
+
+def test_hand_worked_example():
+    g, pat, v = _hand()
+    X = np.array(g["X"], dtype=np.float64)
+    assert np.array_equal(oracle.to_dense(pat, v), np.array(g["dense_H"], dtype=np.float64))
+    assert np.array_equal(oracle.spmm(pat, v, X), np.array(g["HX"], dtype=np.float64))
+    Y0 = np.array(g["Y0"], dtype=np.float64)
+    assert np.array_equal(oracle.spmm(pat, v, X, 2.0, -1.0, Y0),
+                          np.array(g["alpha2_beta_minus1"], dtype=np.float64))
+    assert np.array_equal(oracle.spmm_adjoint(pat, v, X), np.array(g["HtX"], dtype=np.float64))
+    assert np.array_equal(oracle.sddmm(pat, X, X), np.array(g["sddmm_X_X"], dtype=np.float64))
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_spmm_matches_dense_random_rectangular(seed):
+    pat = syn.random_pattern(17, 11, (1, 2, 3, 5, 8), 0.3, seed, empty_rows=3, unsorted=True)
+    v = syn.random_values(pat, seed)
+    H = oracle.to_dense(pat, v)
+    rng = np.random.default_rng(seed)
+    for k in (1, 3, 8):
+        X = rng.standard_normal((pat.n_cols, k))
+        Y0 = rng.standard_normal((pat.n_rows, k))
+        for alpha, beta in ((1.0, 0.0), (-0.5, 1.0), (2.0, -1.0), (0.0, 0.7)):
+            ref = alpha * (H @ X) + beta * Y0
+            got = oracle.spmm(pat, v, X, alpha, beta, Y0)
+            assert _rel(got, ref) < 1e-14
+            # adjoint against the dense transpose
+            Xa = rng.standard_normal((pat.n_rows, k))
+            Ya = rng.standard_normal((pat.n_cols, k))
+            ref_a = alpha * (H.T @ Xa) + beta * Ya
+            assert _rel(oracle.spmm_adjoint(pat, v, Xa, alpha, beta, Ya), ref_a) < 1e-14
+
+
+def test_beta_zero_does_not_read_y():
+    pat = syn.random_pattern(6, 6, (2, 3), 0.5, 3)
+    v = syn.random_values(pat, 3)
+    X = np.ones((pat.n_cols, 2))
+    Y0 = np.full((pat.n_rows, 2), np.nan)
+    assert np.isfinite(oracle.spmm(pat, v, X, 1.0, 0.0, Y0)).all()
+    assert np.isfinite(oracle.spmm_adjoint(pat, v, np.ones((pat.n_rows, 2)), 1.0, 0.0,
+                                           np.full((pat.n_cols, 2), np.nan))).all()
+
+
+def test_tiny_multispecies_against_dense():
+    w = syn.tiny_multispecies(0)
+    pat, v = w.pattern, w.values
+    X = syn.normal_panel(pat.n_cols, 8, 0)
+    H = oracle.to_dense(pat, v)
+    assert H.shape == (1300, 1300)
+    assert _rel(oracle.spmm(pat, v, X), H @ X) < 1e-14
+
+
+def _uniform_pattern(n, b, density, seed):
+    rng = np.random.default_rng(seed)
+    mask = rng.random((n, n)) < density
+    np.fill_diagonal(mask, True)
+    ptr = np.concatenate([[0], np.cumsum(mask.sum(1))])
+    cols = np.concatenate([np.nonzero(mask[i])[0] for i in range(n)])
+    return BlockPattern(np.full(n, b), np.full(n, b), ptr, cols)
+
+
+def test_uniform_b1_is_scipy_csr():
+    pat = _uniform_pattern(300, 1, 0.05, 4)
+    v = syn.random_values(pat, 4)
+    A = sp.csr_matrix((v, pat.block_col_idx, pat.block_row_ptr), shape=(300, 300))
+    X = syn.normal_panel(300, 5, 4)
+    assert _rel(oracle.spmm(pat, v, X), A @ X) < 1e-14
+    assert _rel(oracle.spmm_adjoint(pat, v, X), A.T @ X) < 1e-14
+
+
+def test_uniform_b8_is_scipy_bsr():
+    n, b = 60, 8
+    pat = _uniform_pattern(n, b, 0.1, 5)
+    v = syn.random_values(pat, 5)
+    A = sp.bsr_matrix((v.reshape(-1, b, b), pat.block_col_idx, pat.block_row_ptr),
+                      shape=(n * b, n * b))
+    X = syn.normal_panel(n * b, 16, 5)
+    assert _rel(oracle.spmm(pat, v, X), A @ X) < 1e-14
+    assert _rel(oracle.spmm_adjoint(pat, v, X), A.T @ X) < 1e-14
+    # the same operator held as b=1 CSR must agree too
+    Acsr = A.tocsr()
+    assert _rel(oracle.spmm(pat, v, X), Acsr @ X) < 1e-14
+
+
+def test_symmetric_operator_quadratic_form():
+    """X^T H X is symmetric when H = H^T (the generator's H_ji = H_ij^T)."""
+    w = syn.tiny_multispecies(0)
+    X = syn.normal_panel(w.pattern.n_cols, 8, 0)
+    Q = X.T @ oracle.spmm(w.pattern, w.values, X)
+    assert np.abs(Q - Q.T).max() < 1e-12 * np.abs(Q).max()
+    # and the adjoint equals the forward product for a symmetric H
+    assert _rel(oracle.spmm_adjoint(w.pattern, w.values, X), oracle.spmm(w.pattern, w.values, X)) < 1e-14
+
+
+def test_adjoint_dot_product_identity():
+    pat = syn.random_pattern(23, 19, (1, 4, 9, 13), 0.2, 7, empty_rows=2)
+    v = syn.random_values(pat, 7)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((pat.n_cols, 4))
+    Y = rng.standard_normal((pat.n_rows, 4))
+    lhs = np.sum(Y * oracle.spmm(pat, v, X))
+    rhs = np.sum(oracle.spmm_adjoint(pat, v, Y) * X)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_sddmm_matches_dense_masked_product():
+    pat = syn.random_pattern(13, 9, (1, 4, 9, 13), 0.3, 8, empty_rows=2, unsorted=True)
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((pat.n_rows, 7))
+    B = rng.standard_normal((pat.n_cols, 7))
+    D0 = rng.standard_normal(pat.nnz)
+    dense = A @ B.T
+    ones = np.ones(pat.nnz)
+    mask = oracle.to_dense(pat, ones) > 0
+    got = oracle.sddmm(pat, A, B, 0.5, -2.0, D0)
+    # scatter the packed result back to dense and compare on the pattern
+    G = oracle.to_dense(pat, got)
+    G0 = oracle.to_dense(pat, D0)
+    assert np.allclose(G[mask], (0.5 * dense - 2.0 * G0)[mask], rtol=0, atol=1e-13)
+    # gradient identity: d/dv <Y, H X> = sddmm(Y, X)
+    X = rng.standard_normal((pat.n_cols, 3))
+    Y = rng.standard_normal((pat.n_rows, 3))
+    g = oracle.sddmm(pat, Y, X)
+    v = syn.random_values(pat, 8)
+    f0 = np.sum(Y * oracle.spmm(pat, v, X))
+    e = np.zeros_like(v)
+    idx = rng.choice(len(v), 10, replace=False)
+    for i in idx:
+        e[:] = 0
+        e[i] = 1.0
+        assert abs((np.sum(Y * oracle.spmm(pat, v + e, X)) - f0) - g[i]) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# Chebyshev recurrence (kernel polynomial method, Sec. V)
+
+
+def _diag_pattern(d):
+    n = len(d)
+    return BlockPattern(np.ones(n), np.ones(n), np.arange(n + 1), np.arange(n)), np.asarray(d, float)
+
+
+def test_chebyshev_diagonal_closed_form():
+    """H~ diagonal: with +-1 vectors t_n = T_n(H~) R exactly, so
+    mu_n = (1/N) sum_p T_n(h_pp) = (1/N) sum_p cos(n arccos h_pp)."""
+    h = np.linspace(-0.95, 0.9, 37)
+    pat, v = _diag_pattern(h)
+    R = syn.rademacher_panel(37, 4, 0)
+    mu = oracle.chebyshev_moments(pat, v, R, 20)
+    ref = np.array([np.mean(np.cos(n * np.arccos(h))) for n in range(20)])
+    assert np.abs(mu - ref).max() < 1e-13
+
+
+def test_chebyshev_zero_operator():
+    """H~ = 0: T_n(0) = cos(n pi / 2) = 1, 0, -1, 0, ..."""
+    pat, v = _diag_pattern(np.zeros(10))
+    R = syn.rademacher_panel(10, 3, 1)
+    mu = oracle.chebyshev_moments(pat, v, R, 12)
+    exact = np.array([1.0, 0.0, -1.0, 0.0] * 3)
+    assert np.array_equal(mu, exact)
+
+
+def test_chebyshev_periodic_chain_exact_trace():
+    """Periodic chain with hopping -1: eigenvalues -2 cos(2 pi m / N). With
+    d = 2.02, c = 0 and R = sqrt(N) * identity (unit vectors scaled to the
+    norm of a +-1 vector) the moments are the exact normalised traces
+    (1/N) sum_m T_n(lambda_m / d)."""
+    N = 24
+    ptr = np.arange(0, 3 * N + 1, 3)
+    cols = np.concatenate([sorted([(i - 1) % N, i, (i + 1) % N]) for i in range(N)])
+    pat = BlockPattern(np.ones(N), np.ones(N), ptr, cols)
+    v = np.array([0.0 if c == i else -1.0 for i in range(N) for c in sorted([(i - 1) % N, i, (i + 1) % N])])
+    lam = -2 * np.cos(2 * np.pi * np.arange(N) / N)
+    lo, hi = oracle.gershgorin_bounds(pat, v)
+    assert lo <= lam.min() + 1e-12 and hi >= lam.max() - 1e-12
+    c, d = 0.0, 2.02
+    vt = oracle.shift_scale_values(pat, v, c, d)
+    mu = oracle.chebyshev_moments(pat, vt, np.sqrt(N) * np.eye(N), 30)
+    ref = np.array([np.mean(np.cos(n * np.arccos(lam / d))) for n in range(30)])
+    assert np.abs(mu - ref).max() < 1e-13
+
+
+def test_chebyshev_scaled_spectrum_and_bounded_moments():
+    w = syn.tiny_multispecies(0)
+    c, d = oracle.cheb_scale(w.pattern, w.values)
+    vt = oracle.shift_scale_values(w.pattern, w.values, c, d)
+    ev = np.linalg.eigvalsh(oracle.to_dense(w.pattern, vt))
+    assert ev.min() > -1.0 and ev.max() < 1.0
+    R = syn.rademacher_panel(w.pattern.n_rows, 4, 0)
+    mu = oracle.chebyshev_moments(w.pattern, vt, R, 30)
+    assert abs(mu[0] - 1.0) < 1e-15
+    assert np.all(np.abs(mu) <= 1.0 + 1e-12)
+    # the moments equal the dense-polynomial traces of the same random vectors
+    Ht = oracle.to_dense(w.pattern, vt)
+    T0, T1 = R, Ht @ R
+    ref = [np.sum(R * T0) / R.size, np.sum(R * T1) / R.size]
+    for n in range(2, 30):
+        T0, T1 = T1, 2 * Ht @ T1 - T0
+        ref.append(np.sum(R * T1) / R.size)
+    assert np.abs(mu - np.array(ref)).max() < 1e-12
+
+
+def test_moment_loss_gradient_central_differences():
+    pat = syn.random_pattern(9, 9, (1, 2, 4), 0.35, 11)
+    # square, with diagonal blocks only where sizes match
+    pat = BlockPattern(pat.row_bsize, pat.row_bsize, pat.block_row_ptr, pat.block_col_idx)
+    v = 0.3 * syn.random_values(pat, 11)
+    R = syn.rademacher_panel(pat.n_rows, 3, 2)
+    M = 8
+    g = oracle.moment_loss_grad(pat, v, R, M)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(v), 20, replace=False):
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd = (oracle.moment_loss(pat, vp, R, M) - oracle.moment_loss(pat, vm, R, M)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i]))
