@@ -1,0 +1,277 @@
+/*
+ * vbcsr.h -- C ABI of the GB300 (sm_103a) variable-block sparse library.
+ *
+ * A VBCSR operator H has n_brows block rows and n_bcols block columns. Block
+ * row i holds b_i = row_bsize[i] scalar rows starting at r_i = sum_{i'<i} b_i';
+ * block column j holds b_j = col_bsize[j] scalar columns starting at
+ * c_j = sum_{j'<j} b_j'. The stored blocks of row i are the columns
+ * J(i) = block_col_idx[block_row_ptr[i] .. block_row_ptr[i+1]); block (i, j) is a
+ * dense b_i x b_j matrix (the variable-block CSR format of Sec. II.A of the
+ * paper "Accelerating Atom Simulations with Variable-Block Sparse Matrix
+ * Library").
+ *
+ * User value order ("packed order"): blocks in block_row_ptr / block_col_idx
+ * order, each block row-major. Panels X and Y are row-major [rows, k] with a
+ * leading dimension ld >= k, in the matrix dtype.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: VBCSR_OK (0) or a negative vbcsr_status. On error a
+ *    thread-local message is available from vbcsr_last_error_detail().
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls
+ *    are asynchronous on that stream and never synchronise the host, except
+ *    vbcsr_check and the host-buffer calls that say so.
+ *  - Every argument is validated on the host before anything is launched;
+ *    an invalid call launches nothing and leaves its outputs untouched.
+ *  - Pointers are borrowed for the duration of the call only. Device pointers
+ *    must belong to the device that was current at vbcsr_create.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef VBCSR_H
+#define VBCSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vbcsr_matrix vbcsr_t;
+
+typedef enum {
+    VBCSR_OK = 0,
+    VBCSR_ERR_INVALID_ARG = -1,   /* null pointer, negative size, ld < k, bad enum   */
+    VBCSR_ERR_PATTERN = -2,       /* bad block_row_ptr, column out of range, duplicate
+                                     block in a row, block size < 1 or too large     */
+    VBCSR_ERR_CUDA = -3,          /* a CUDA runtime call failed                       */
+    VBCSR_ERR_NO_MEMORY = -4,     /* device or host allocation failed                 */
+    VBCSR_ERR_UNSUPPORTED = -5,   /* valid request outside what this build supports   */
+    VBCSR_ERR_DEVICE_CHECK = -6,  /* a kernel's self-check recorded an error          */
+    VBCSR_ERR_ALIAS = -7          /* output overlaps an input that it may not alias   */
+} vbcsr_status;
+
+typedef enum {
+    VBCSR_F64 = 0,                /* values, X and Y are double */
+    VBCSR_F32 = 1                 /* values, X and Y are float  */
+} vbcsr_dtype;
+
+/*
+ * Arithmetic of the block products. X, Y, alpha, beta and the epilogue stay in
+ * the matrix dtype in every mode; the mixed modes keep an FP32 copy of the
+ * values (built on first use, refreshed by vbcsr_set_values).
+ *  NATIVE  products and accumulation in the matrix dtype (FP64 FMA / FP32 FMA)
+ *  F32     values and X rounded to FP32, FP32 FMA, FP32 accumulation
+ *  TF32    one TF32 tensor-core product per block product, FP32 accumulation
+ *  TF32X3  v = hi + lo with hi = tf32(v), lo = tf32(v - hi) for values and X;
+ *          hi*hi + hi*lo + lo*hi on the tensor cores, FP32 accumulation
+ *  BF16X2  the same split with bf16 pieces, FP32 accumulation
+ */
+typedef enum {
+    VBCSR_PREC_NATIVE = 0,
+    VBCSR_PREC_F32 = 1,
+    VBCSR_PREC_TF32 = 2,
+    VBCSR_PREC_TF32X3 = 3,
+    VBCSR_PREC_BF16X2 = 4
+} vbcsr_precision;
+
+typedef struct {
+    int64_t n_brows, n_bcols;     /* block rows / block columns                      */
+    int64_t n_rows, n_cols;       /* scalar rows / columns                           */
+    int64_t nblk;                 /* stored blocks                                   */
+    int64_t nnz;                  /* stored scalar entries (sum of b_i * b_j)        */
+    int64_t panel_elems;          /* device value elements incl. alignment padding   */
+    int64_t device_bytes;         /* device memory held by the handle                */
+    int32_t dtype;                /* vbcsr_dtype                                     */
+    int32_t n_shape_classes;      /* distinct (b_i, b_j) pairs among stored blocks   */
+    int32_t n_row_classes;        /* distinct work heights used by the forward plan  */
+    int32_t n_structs;            /* independent structures (1 unless batched)      */
+} vbcsr_info_t;
+
+/* Optional fused epilogue of vbcsr_spmm_ex (all fields may be zero/NULL). */
+typedef struct {
+    double gamma;                 /* Y += gamma * Z after the product (Z ignored if 0) */
+    const void *Z;                /* device, [rows of Y, k], may equal neither X nor Y */
+    int64_t ldz;
+    const void *R;                /* device, [rows of Y, k]; with dot_out set, the call
+                                     also writes *dot_out = sum(R .* Y_new) in FP64    */
+    int64_t ldr;
+    double *dot_out;              /* device pointer to one double, or NULL             */
+} vbcsr_epilogue_t;
+
+/* ---- status -------------------------------------------------------------- */
+
+/* Static, thread-safe description of a status code. */
+const char *vbcsr_error_string(int status);
+/* Message of the last failing call on this host thread ("" if none). */
+const char *vbcsr_last_error_detail(void);
+
+/* ---- construction -------------------------------------------------------- */
+
+/*
+ * Builds a handle from a VBCSR pattern and packed values (Sec. II.A; the
+ * shape-class registry and shape-grouped value pages of Sec. III.B are built
+ * here, once).
+ *  n_brows, n_bcols  >= 0
+ *  row_bsize[n_brows], col_bsize[n_bcols]   host, block sizes in [1, 4096]
+ *  block_row_ptr[n_brows+1]   host, block_row_ptr[0] = 0, non-decreasing
+ *  block_col_idx[nblk]        host, in [0, n_bcols), no duplicate in a row
+ *                             (any order inside a row)
+ *  values     packed order, nnz elements of `dtype`; host memory when
+ *             values_on_device = 0, device memory when 1
+ * The library copies everything it needs; the caller keeps ownership of its
+ * buffers. The scalar sizes must stay below 2^31. Errors: INVALID_ARG,
+ * PATTERN, NO_MEMORY, CUDA. The call synchronises `stream` before returning.
+ */
+int vbcsr_create(vbcsr_t **out, int64_t n_brows, int64_t n_bcols,
+                 const int32_t *row_bsize, const int32_t *col_bsize,
+                 const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                 const void *values, int dtype, int values_on_device, void *stream);
+
+/*
+ * Builds one handle over n_structs independent structures (a block-diagonal
+ * operator), so that one launch serves all of them.
+ *  struct_brow_offsets[n_structs+1], struct_bcol_offsets[n_structs+1]  host,
+ *      first block row / block column of every structure (offsets[0] = 0,
+ *      offsets[n_structs] = n_brows / n_bcols)
+ *  block_col_idx holds column indices LOCAL to the structure of the row
+ *  (0 .. its block-column count - 1); everything else as in vbcsr_create with
+ *  global block rows. X and Y are the concatenated panels of all structures.
+ */
+int vbcsr_create_batched(vbcsr_t **out, int64_t n_structs,
+                         const int64_t *struct_brow_offsets, const int64_t *struct_bcol_offsets,
+                         const int32_t *row_bsize, const int32_t *col_bsize,
+                         const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                         const void *values, int dtype, int values_on_device, void *stream);
+
+/* Frees every device and host resource of the handle; NULL is accepted. The
+   caller must make sure no work using the handle is still in flight. */
+int vbcsr_destroy(vbcsr_t *A);
+
+/* ---- values ---------------------------------------------------------------- */
+
+/* Replaces all values (packed order, nnz elements of the matrix dtype; host
+   when on_device = 0, else device) on the fixed pattern. Asynchronous on
+   `stream` for device input; host input is staged and the call synchronises. */
+int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, void *stream);
+
+/* Copies all values out in packed order (host when on_device = 0, else device).
+   Host output synchronises `stream`. */
+int vbcsr_get_values(const vbcsr_t *A, void *values, int on_device, void *stream);
+
+/* ---- products ---------------------------------------------------------------- */
+
+/*
+ * Y = alpha * H * X + beta * Y   (Sec. III.B, "Matrix multiplication": every
+ * block row accumulates A_ij X_j over j in J(i)).
+ *  X  device [n_cols, k], leading dimension ldx >= k
+ *  Y  device [n_rows, k], leading dimension ldy >= k; Y must not overlap X
+ *  beta == 0: Y is not read (NaN in Y does not propagate)
+ *  alpha == 0: H and X are not read
+ *  k == 0 or n_rows == 0: nothing is launched
+ * Each output row block is written exactly once (no atomics).
+ * Errors: INVALID_ARG, ALIAS, UNSUPPORTED (precision), NO_MEMORY, CUDA.
+ */
+int vbcsr_spmm(vbcsr_t *A, int64_t k, double alpha, const void *X, int64_t ldx,
+               double beta, void *Y, int64_t ldy, int precision, void *stream);
+
+/*
+ * Y = alpha * H^T * X + beta * Y   (Eq. 1: Y_j += A_ij^dagger X_i for j in J(i);
+ * values are real, so the dagger is a transpose). X is [n_rows, k], Y is
+ * [n_cols, k]; otherwise as vbcsr_spmm. A transposed index of the pattern
+ * (no value copy) lets every output row block be written once, without atomics.
+ */
+int vbcsr_spmm_adjoint(vbcsr_t *A, int64_t k, double alpha, const void *X, int64_t ldx,
+                       double beta, void *Y, int64_t ldy, int precision, void *stream);
+
+/*
+ * vbcsr_spmm (transpose = 0) or vbcsr_spmm_adjoint (transpose = 1) with a
+ * fused epilogue (may be NULL):
+ *   Y = alpha * op(H) X + beta * Y + gamma * Z,   *dot_out = sum(R .* Y)
+ * This is one step of the Chebyshev recurrence and of its reverse (adjoint)
+ * recurrence in the kernel polynomial method of Sec. V. The dot product is
+ * reduced in a fixed order (deterministic for a given launch configuration).
+ */
+int vbcsr_spmm_ex(vbcsr_t *A, int transpose, int64_t k, double alpha, const void *X,
+                  int64_t ldx, double beta, void *Y, int64_t ldy,
+                  const vbcsr_epilogue_t *epilogue, int precision, void *stream);
+
+/*
+ * Pattern-sampled dense product, the gradient of <G, H X> with respect to the
+ * stored values:
+ *   D_ij[p, q] = alpha * sum_c Aop[r_i + p, c] * Bop[c_j + q, c] + beta * D_ij[p, q]
+ * for every stored block (i, j), written in packed order.
+ *  Aop  device [n_rows, k], lda >= k;  Bop  device [n_cols, k], ldb >= k
+ *  D    device, nnz elements of the matrix dtype; beta == 0: D is not read
+ * (This operation has no counterpart in the paper.)
+ */
+int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop, int64_t lda,
+                const void *Bop, int64_t ldb, double beta, void *D, void *stream);
+
+/*
+ * Chebyshev moments of the kernel polynomial method (Sec. V) for an operator
+ * already shifted and scaled to H~ with spectrum inside [-1, 1]:
+ *   t_0 = R,  t_1 = H~ R,  t_{n+1} = 2 H~ t_n - t_{n-1},
+ *   moments[n] = sum(R .* t_n) / (n_rows * k),   n = 0 .. n_moments - 1.
+ * The recurrence and the moments are FP64 (matrix dtype F64 required); the
+ * block products use `precision`.
+ *  R        device [n_rows, k], ldr >= k (square operator: n_rows == n_cols)
+ *  moments  device, n_moments doubles
+ *  work     device, 2 * n_rows * k doubles (scratch panels)
+ *  ckpt     device or NULL; when given with ckpt_every >= 1, the pairs
+ *           (t_m, t_{m+1}) for m = 0, ckpt_every, 2*ckpt_every, ... (m+1 <
+ *           n_moments) are stored consecutively, each panel n_rows * k doubles
+ *           with leading dimension k: ceil((n_moments - 1) / ckpt_every) pairs.
+ */
+int vbcsr_chebyshev(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                    double *moments, double *work, double *ckpt, int64_t ckpt_every,
+                    int precision, void *stream);
+
+/*
+ * Reverse-mode gradient of the moments of vbcsr_chebyshev with respect to the
+ * stored values of H~ (packed order), given dL/dmu_n = grad_mu[n]:
+ *   g_n = grad_mu[n] R / (n_rows * k),
+ *   lam_{M-1} = g_{M-1},  lam_n = g_n + 2 H~^T lam_{n+1} - lam_{n+2}  (n >= 1),
+ *   dL/dH~ = lam_1 t_0^T + sum_{n=1}^{M-2} 2 lam_{n+1} t_n^T   on the stored blocks.
+ * The t_n are recomputed segment by segment from the checkpoint pairs that
+ * vbcsr_chebyshev stored with the same ckpt_every, so memory stays at
+ * O(ckpt_every) panels.
+ *  grad_mu  device, n_moments doubles (copied to the host: the call
+ *           synchronises `stream` once at its start)
+ *  ckpt     device, as written by vbcsr_chebyshev
+ *  dvalues  device, nnz doubles, overwritten
+ *  work     device, (2 + 2 * ckpt_every) * n_rows * k doubles
+ * (The adjoint recurrence has no counterpart in the paper; it differentiates
+ * the kernel-polynomial moments of Sec. V.)
+ */
+int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                             const double *grad_mu, const double *ckpt, int64_t ckpt_every,
+                             double *dvalues, double *work, int precision, void *stream);
+
+/* ---- inspection ---------------------------------------------------------- */
+
+int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out);
+
+/*
+ * Shape-class registry (Sec. III.B: every distinct (b_i, b_j) of a stored
+ * block is registered as a shape class). Writes up to `cap` classes sorted by
+ * (b_i, b_j) into bi[], bj[], count[] and returns the number of classes (>= 0)
+ * or a negative status.
+ */
+int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, int64_t *count, int32_t cap);
+
+/*
+ * Tuning of the forward kernel: KC output columns per warp pass (1, 2, 4, 8,
+ * 16 or 32; 0 = automatic from k) and warps per CTA (1, 2, 4 or 8; 0 =
+ * automatic). Applies to later calls on this handle.
+ */
+int vbcsr_set_tuning(vbcsr_t *A, int32_t kc, int32_t warps_per_cta);
+
+/* Synchronises `stream`, then reads and clears the handle's device error
+   word: VBCSR_OK, or VBCSR_ERR_DEVICE_CHECK with the recorded code in the
+   detail message. */
+int vbcsr_check(vbcsr_t *A, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBCSR_H */

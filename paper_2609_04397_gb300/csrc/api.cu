@@ -1,0 +1,920 @@
+// C ABI of the library: validation, the planner (shape-class registry,
+// shape-grouped value pages, work items), and dispatch of the product kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/vbcsr.h"
+#include "internal.cuh"
+
+using namespace vbcsr;
+
+// ---------------------------------------------------------------------------
+// status handling
+
+static thread_local std::string g_detail;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_detail = buf;
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(VBCSR_ERR_NO_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(VBCSR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, what)                        \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+extern "C" const char *vbcsr_error_string(int status) {
+    switch (status) {
+        case VBCSR_OK: return "ok";
+        case VBCSR_ERR_INVALID_ARG: return "invalid argument";
+        case VBCSR_ERR_PATTERN: return "invalid block pattern";
+        case VBCSR_ERR_CUDA: return "CUDA error";
+        case VBCSR_ERR_NO_MEMORY: return "out of memory";
+        case VBCSR_ERR_UNSUPPORTED: return "unsupported request";
+        case VBCSR_ERR_DEVICE_CHECK: return "device self-check failed";
+        case VBCSR_ERR_ALIAS: return "output aliases an input";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *vbcsr_last_error_detail(void) { return g_detail.c_str(); }
+
+// ---------------------------------------------------------------------------
+// handle
+
+namespace {
+
+struct Bucket {
+    int B;
+    int64_t begin, count;   // range in the items array
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct vbcsr_matrix {
+    int device = 0;
+    int dtype = VBCSR_F64;
+    size_t esize = 8;
+    int64_t n_brows = 0, n_bcols = 0, n_rows = 0, n_cols = 0, nblk = 0, nnz = 0, panel_elems = 0;
+    int32_t n_structs = 1;
+    int kc = 0, warps = 0;
+    int debug_checks = 0;
+
+    // host copies
+    std::vector<int32_t> row_b, col_b;
+    std::vector<int64_t> row_off, col_off;
+    std::vector<int64_t> uoff;                 // packed-order offset of user block u (nblk + 1)
+    std::vector<int32_t> cls_bi, cls_bj;       // shape-class registry
+    std::vector<int64_t> cls_count;
+
+    std::vector<Bucket> fwd_buckets, adj_buckets;
+
+    // device
+    std::vector<DevBuf> bufs;
+    void *panel = nullptr;        // values in panels (dtype)
+    float *panel32 = nullptr;     // FP32 copy for the mixed modes (FP64 operators), lazily built
+    bool panel32_valid = false;
+    WorkItem *fwd_items = nullptr, *adj_items = nullptr;
+    int32_t *fl_xrow = nullptr, *fl_pcol = nullptr, *fl_w = nullptr, *fl_kp = nullptr, *fl_bi = nullptr;
+    int64_t *fl_uoff = nullptr, *fl_pbase = nullptr;
+    int64_t *tl_pbase = nullptr;
+    int32_t *tl_kp = nullptr, *tl_bi = nullptr, *tl_xrow = nullptr, *tl_vcol = nullptr;
+    int64_t *prow_ptr = nullptr, *d_row_off = nullptr;
+    int32_t *d_row_b = nullptr;
+    double *partials = nullptr;
+    int *err = nullptr;
+    int64_t device_bytes = 0;
+
+    ~vbcsr_matrix() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != device) cudaSetDevice(device);
+        for (auto &b : bufs)
+            if (b.p) cudaFree(b.p);
+        if (cur != device) cudaSetDevice(cur);
+    }
+
+    template <typename T>
+    cudaError_t alloc(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return e;
+        bufs.push_back({q, count * sizeof(T)});
+        device_bytes += (int64_t)(count * sizeof(T));
+        *p = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+};
+
+template <typename T>
+static cudaError_t upload(vbcsr_matrix *A, T **dst, const std::vector<T> &src, cudaStream_t s) {
+    cudaError_t e = A->alloc(dst, src.size());
+    if (e != cudaSuccess) return e;
+    if (src.empty()) return cudaSuccess;
+    e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);   // host vectors are freed by the caller afterwards
+}
+
+// ---------------------------------------------------------------------------
+// validation and planning
+
+static const int32_t kMaxBlockSize = 4096;
+
+static int validate_pattern(int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
+                            const int32_t *col_bsize, const int64_t *block_row_ptr,
+                            const int32_t *block_col_idx) {
+    if (n_brows < 0 || n_bcols < 0) return fail(VBCSR_ERR_INVALID_ARG, "negative block count");
+    if (n_brows > 0 && !row_bsize) return fail(VBCSR_ERR_INVALID_ARG, "row_bsize is NULL");
+    if (n_bcols > 0 && !col_bsize) return fail(VBCSR_ERR_INVALID_ARG, "col_bsize is NULL");
+    if (!block_row_ptr) return fail(VBCSR_ERR_INVALID_ARG, "block_row_ptr is NULL");
+    int64_t rows = 0, cols = 0;
+    for (int64_t i = 0; i < n_brows; ++i) {
+        if (row_bsize[i] < 1 || row_bsize[i] > kMaxBlockSize)
+            return fail(VBCSR_ERR_PATTERN, "row_bsize[%lld] = %d outside [1, %d]", (long long)i, row_bsize[i],
+                        kMaxBlockSize);
+        rows += row_bsize[i];
+    }
+    for (int64_t j = 0; j < n_bcols; ++j) {
+        if (col_bsize[j] < 1 || col_bsize[j] > kMaxBlockSize)
+            return fail(VBCSR_ERR_PATTERN, "col_bsize[%lld] = %d outside [1, %d]", (long long)j, col_bsize[j],
+                        kMaxBlockSize);
+        cols += col_bsize[j];
+    }
+    if (rows >= (1LL << 31) || cols >= (1LL << 31))
+        return fail(VBCSR_ERR_PATTERN, "scalar size %lld x %lld reaches 2^31", (long long)rows, (long long)cols);
+    if (block_row_ptr[0] != 0) return fail(VBCSR_ERR_PATTERN, "block_row_ptr[0] = %lld, expected 0",
+                                           (long long)block_row_ptr[0]);
+    for (int64_t i = 0; i < n_brows; ++i)
+        if (block_row_ptr[i + 1] < block_row_ptr[i])
+            return fail(VBCSR_ERR_PATTERN, "block_row_ptr decreases at row %lld", (long long)i);
+    const int64_t nblk = block_row_ptr[n_brows];
+    if (nblk > 0 && !block_col_idx) return fail(VBCSR_ERR_INVALID_ARG, "block_col_idx is NULL");
+    if (nblk >= (1LL << 31)) return fail(VBCSR_ERR_PATTERN, "%lld blocks reach 2^31", (long long)nblk);
+    std::vector<int32_t> tmp;
+    for (int64_t i = 0; i < n_brows; ++i) {
+        tmp.assign(block_col_idx + block_row_ptr[i], block_col_idx + block_row_ptr[i + 1]);
+        for (int32_t c : tmp)
+            if (c < 0 || c >= n_bcols)
+                return fail(VBCSR_ERR_PATTERN, "column %d of block row %lld outside [0, %lld)", c, (long long)i,
+                            (long long)n_bcols);
+        std::sort(tmp.begin(), tmp.end());
+        for (size_t e = 1; e < tmp.size(); ++e)
+            if (tmp[e] == tmp[e - 1])
+                return fail(VBCSR_ERR_PATTERN, "duplicate block (%lld, %d)", (long long)i, tmp[e]);
+    }
+    return VBCSR_OK;
+}
+
+static int ceil_to(int64_t v, int m) { return (int)((v + m - 1) / m * m); }
+
+static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
+                 const int32_t *col_bsize, const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                 const void *values, int values_on_device, cudaStream_t s) {
+    A->n_brows = n_brows;
+    A->n_bcols = n_bcols;
+    A->row_b.assign(row_bsize, row_bsize + n_brows);
+    A->col_b.assign(col_bsize, col_bsize + n_bcols);
+    A->row_off.assign(n_brows + 1, 0);
+    A->col_off.assign(n_bcols + 1, 0);
+    for (int64_t i = 0; i < n_brows; ++i) A->row_off[i + 1] = A->row_off[i] + row_bsize[i];
+    for (int64_t j = 0; j < n_bcols; ++j) A->col_off[j + 1] = A->col_off[j] + col_bsize[j];
+    A->n_rows = A->row_off[n_brows];
+    A->n_cols = A->col_off[n_bcols];
+    const int64_t nblk = block_row_ptr[n_brows];
+    A->nblk = nblk;
+
+    // packed-order offsets
+    A->uoff.assign(nblk + 1, 0);
+    for (int64_t i = 0; i < n_brows; ++i)
+        for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u)
+            A->uoff[u + 1] = A->uoff[u] + (int64_t)row_bsize[i] * col_bsize[block_col_idx[u]];
+    A->nnz = A->uoff[nblk];
+
+    // shape-class registry (Sec. III.B): every distinct (b_i, b_j)
+    {
+        std::map<std::pair<int32_t, int32_t>, int64_t> reg;
+        for (int64_t i = 0; i < n_brows; ++i)
+            for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u)
+                reg[{row_bsize[i], col_bsize[block_col_idx[u]]}] += 1;
+        for (auto &kv : reg) {
+            A->cls_bi.push_back(kv.first.first);
+            A->cls_bj.push_back(kv.first.second);
+            A->cls_count.push_back(kv.second);
+        }
+    }
+
+    // plan order: blocks of every row sorted by column
+    std::vector<int32_t> perm(nblk);   // plan block -> user block
+    for (int64_t i = 0; i < n_brows; ++i) {
+        const int64_t b0 = block_row_ptr[i], b1 = block_row_ptr[i + 1];
+        for (int64_t u = b0; u < b1; ++u) perm[u] = (int32_t)u;
+        std::sort(perm.begin() + b0, perm.begin() + b1,
+                  [&](int32_t x, int32_t y) { return block_col_idx[x] < block_col_idx[y]; });
+    }
+
+    // panel widths; pages ordered by row height
+    std::vector<int64_t> K(n_brows, 0), Kp(n_brows, 0), poff(n_brows, 0);
+    for (int64_t i = 0; i < n_brows; ++i) {
+        int64_t w = 0;
+        for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u) w += col_bsize[block_col_idx[u]];
+        if (w >= (1LL << 31) - kPadK) return fail(VBCSR_ERR_PATTERN, "block row %lld too wide", (long long)i);
+        K[i] = w;
+        Kp[i] = ceil_to(w, kPadK);
+    }
+    std::vector<int64_t> page_order(n_brows);
+    for (int64_t i = 0; i < n_brows; ++i) page_order[i] = i;
+    std::stable_sort(page_order.begin(), page_order.end(),
+                     [&](int64_t x, int64_t y) { return row_bsize[x] < row_bsize[y]; });
+    int64_t pos = 0;
+    for (int64_t i : page_order) {
+        poff[i] = pos;
+        pos += (int64_t)row_bsize[i] * Kp[i];
+    }
+    A->panel_elems = pos;
+
+    // plan block list
+    std::vector<int32_t> fl_xrow(nblk), fl_pcol(nblk), fl_w(nblk), fl_kp(nblk), fl_bi(nblk);
+    std::vector<int64_t> fl_uoff(nblk), fl_pbase(nblk), prow_ptr(block_row_ptr, block_row_ptr + n_brows + 1);
+    for (int64_t i = 0; i < n_brows; ++i) {
+        int64_t pc = 0;
+        for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
+            const int32_t u = perm[l];
+            const int32_t j = block_col_idx[u];
+            fl_xrow[l] = (int32_t)A->col_off[j];
+            fl_pcol[l] = (int32_t)pc;
+            fl_w[l] = col_bsize[j];
+            fl_kp[l] = (int32_t)Kp[i];
+            fl_bi[l] = row_bsize[i];
+            fl_uoff[l] = A->uoff[u];
+            fl_pbase[l] = poff[i] + pc;
+            pc += col_bsize[j];
+        }
+    }
+
+    // forward work items, bucketed by row count
+    {
+        std::vector<std::vector<WorkItem>> bk(kMaxB + 1);
+        for (int64_t i : page_order) {
+            for (int32_t r0 = 0; r0 < row_bsize[i]; r0 += kMaxB) {
+                WorkItem w;
+                w.B = std::min(kMaxB, row_bsize[i] - r0);
+                w.vbase = poff[i] + (int64_t)r0 * Kp[i];
+                w.yrow = A->row_off[i] + r0;
+                w.lbegin = block_row_ptr[i];
+                w.nlist = (int32_t)(block_row_ptr[i + 1] - block_row_ptr[i]);
+                w.K = (int32_t)K[i];
+                w.Kp = (int32_t)Kp[i];
+                bk[w.B].push_back(w);
+            }
+        }
+        std::vector<WorkItem> items;
+        for (int b = 1; b <= kMaxB; ++b) {
+            if (bk[b].empty()) continue;
+            A->fwd_buckets.push_back({b, (int64_t)items.size(), (int64_t)bk[b].size()});
+            items.insert(items.end(), bk[b].begin(), bk[b].end());
+        }
+        CUDA_TRY(upload(A, &A->fwd_items, items, s), "upload forward items");
+    }
+
+    // transposed list and adjoint work items
+    {
+        std::vector<int64_t> tptr(n_bcols + 1, 0);
+        for (int64_t l = 0; l < nblk; ++l) tptr[block_col_idx[perm[l]] + 1] += 1;
+        for (int64_t j = 0; j < n_bcols; ++j) tptr[j + 1] += tptr[j];
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        std::vector<int64_t> tl_pbase(nblk);
+        std::vector<int32_t> tl_kp(nblk), tl_bi(nblk), tl_xrow(nblk), tl_vcol(nblk);
+        for (int64_t i = 0; i < n_brows; ++i) {           // rows increasing inside each column
+            for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
+                const int32_t j = block_col_idx[perm[l]];
+                const int64_t e = fill[j]++;
+                tl_pbase[e] = fl_pbase[l];
+                tl_kp[e] = (int32_t)Kp[i];
+                tl_bi[e] = row_bsize[i];
+                tl_xrow[e] = (int32_t)A->row_off[i];
+            }
+        }
+        std::vector<int64_t> Kt(n_bcols, 0);
+        for (int64_t j = 0; j < n_bcols; ++j) {
+            int64_t v = 0;
+            for (int64_t e = tptr[j]; e < tptr[j + 1]; ++e) {
+                tl_vcol[e] = (int32_t)v;
+                v += tl_bi[e];
+            }
+            if (v >= (1LL << 31)) return fail(VBCSR_ERR_PATTERN, "block column %lld too tall", (long long)j);
+            Kt[j] = v;
+        }
+        std::vector<int64_t> col_order(n_bcols);
+        for (int64_t j = 0; j < n_bcols; ++j) col_order[j] = j;
+        std::stable_sort(col_order.begin(), col_order.end(),
+                         [&](int64_t x, int64_t y) { return col_bsize[x] < col_bsize[y]; });
+        std::vector<std::vector<WorkItem>> bk(kMaxB + 1);
+        for (int64_t j : col_order) {
+            for (int32_t q0 = 0; q0 < col_bsize[j]; q0 += kMaxB) {
+                WorkItem w;
+                w.B = std::min(kMaxB, col_bsize[j] - q0);
+                w.vbase = 0;
+                w.yrow = A->col_off[j] + q0;
+                w.lbegin = tptr[j];
+                w.nlist = (int32_t)(tptr[j + 1] - tptr[j]);
+                w.K = (int32_t)Kt[j];
+                w.Kp = q0;
+                bk[w.B].push_back(w);
+            }
+        }
+        std::vector<WorkItem> items;
+        for (int b = 1; b <= kMaxB; ++b) {
+            if (bk[b].empty()) continue;
+            A->adj_buckets.push_back({b, (int64_t)items.size(), (int64_t)bk[b].size()});
+            items.insert(items.end(), bk[b].begin(), bk[b].end());
+        }
+        CUDA_TRY(upload(A, &A->adj_items, items, s), "upload adjoint items");
+        CUDA_TRY(upload(A, &A->tl_pbase, tl_pbase, s), "upload");
+        CUDA_TRY(upload(A, &A->tl_kp, tl_kp, s), "upload");
+        CUDA_TRY(upload(A, &A->tl_bi, tl_bi, s), "upload");
+        CUDA_TRY(upload(A, &A->tl_xrow, tl_xrow, s), "upload");
+        CUDA_TRY(upload(A, &A->tl_vcol, tl_vcol, s), "upload");
+    }
+
+    CUDA_TRY(upload(A, &A->fl_xrow, fl_xrow, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_pcol, fl_pcol, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_w, fl_w, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_kp, fl_kp, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_bi, fl_bi, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_uoff, fl_uoff, s), "upload");
+    CUDA_TRY(upload(A, &A->fl_pbase, fl_pbase, s), "upload");
+    CUDA_TRY(upload(A, &A->prow_ptr, prow_ptr, s), "upload");
+    CUDA_TRY(upload(A, &A->d_row_off, A->row_off, s), "upload");
+    CUDA_TRY(upload(A, &A->d_row_b, A->row_b, s), "upload");
+    CUDA_TRY(A->alloc(&A->partials, kPartialsCap), "alloc partials");
+    CUDA_TRY(A->alloc(&A->err, 1), "alloc error word");
+    CUDA_TRY(cudaMemsetAsync(A->err, 0, sizeof(int), s), "memset");
+
+    // value pages
+    unsigned char *panel = nullptr;
+    CUDA_TRY(A->alloc(&panel, (size_t)A->panel_elems * A->esize), "alloc value pages");
+    A->panel = panel;
+    CUDA_TRY(cudaMemsetAsync(A->panel, 0, (size_t)A->panel_elems * A->esize, s), "memset");
+    if (A->nnz > 0) {
+        const void *src = values;
+        void *staged = nullptr;
+        if (!values_on_device) {
+            CUDA_TRY(cudaMalloc(&staged, (size_t)A->nnz * A->esize), "alloc staging");
+            cudaError_t e = cudaMemcpyAsync(staged, values, (size_t)A->nnz * A->esize, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) { cudaFree(staged); return cuda_fail(e, "copy values"); }
+            src = staged;
+        }
+        cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, true, nblk, A->fl_uoff, A->fl_pbase,
+                                              A->fl_kp, A->fl_bi, A->fl_w, src, A->panel, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        if (staged) cudaFree(staged);
+        if (e != cudaSuccess) return cuda_fail(e, "scatter values");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "scatter values");
+    }
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    return VBCSR_OK;
+}
+
+static int create_common(vbcsr_t **out, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
+                         const int32_t *col_bsize, const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                         const void *values, int dtype, int values_on_device, void *stream, int32_t n_structs) {
+    if (!out) return fail(VBCSR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dtype != VBCSR_F64 && dtype != VBCSR_F32) return fail(VBCSR_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (values_on_device != 0 && values_on_device != 1)
+        return fail(VBCSR_ERR_INVALID_ARG, "values_on_device must be 0 or 1");
+    int rc = validate_pattern(n_brows, n_bcols, row_bsize, col_bsize, block_row_ptr, block_col_idx);
+    if (rc) return rc;
+    if (!values && block_row_ptr[n_brows] > 0) return fail(VBCSR_ERR_INVALID_ARG, "values is NULL");
+    vbcsr_matrix *A = new (std::nothrow) vbcsr_matrix();
+    if (!A) return fail(VBCSR_ERR_NO_MEMORY, "host allocation");
+    cudaError_t e = cudaGetDevice(&A->device);
+    if (e != cudaSuccess) { delete A; return cuda_fail(e, "cudaGetDevice"); }
+    A->dtype = dtype;
+    A->esize = dtype == VBCSR_F64 ? 8 : 4;
+    A->n_structs = n_structs;
+    const char *dbg = getenv("VBCSR_DEBUG_CHECKS");
+    A->debug_checks = (dbg && dbg[0] && dbg[0] != '0') ? 1 : 0;
+    try {
+        rc = build(A, n_brows, n_bcols, row_bsize, col_bsize, block_row_ptr, block_col_idx, values,
+                   values_on_device, (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        rc = fail(VBCSR_ERR_NO_MEMORY, "host allocation in planner");
+    }
+    if (rc) { delete A; return rc; }
+    *out = A;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_create(vbcsr_t **out, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
+                            const int32_t *col_bsize, const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                            const void *values, int dtype, int values_on_device, void *stream) {
+    return create_common(out, n_brows, n_bcols, row_bsize, col_bsize, block_row_ptr, block_col_idx, values, dtype,
+                         values_on_device, stream, 1);
+}
+
+extern "C" int vbcsr_create_batched(vbcsr_t **out, int64_t n_structs, const int64_t *sbo, const int64_t *sco,
+                                    const int32_t *row_bsize, const int32_t *col_bsize,
+                                    const int64_t *block_row_ptr, const int32_t *block_col_idx,
+                                    const void *values, int dtype, int values_on_device, void *stream) {
+    if (!out) return fail(VBCSR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_structs < 1 || n_structs >= (1LL << 31)) return fail(VBCSR_ERR_INVALID_ARG, "n_structs %lld", (long long)n_structs);
+    if (!sbo || !sco || !block_row_ptr) return fail(VBCSR_ERR_INVALID_ARG, "offset array is NULL");
+    if (sbo[0] != 0 || sco[0] != 0) return fail(VBCSR_ERR_PATTERN, "structure offsets must start at 0");
+    for (int64_t s = 0; s < n_structs; ++s)
+        if (sbo[s + 1] < sbo[s] || sco[s + 1] < sco[s])
+            return fail(VBCSR_ERR_PATTERN, "structure offsets decrease at %lld", (long long)s);
+    const int64_t n_brows = sbo[n_structs], n_bcols = sco[n_structs];
+    if (n_brows < 0 || n_bcols < 0) return fail(VBCSR_ERR_INVALID_ARG, "negative size");
+    if (block_row_ptr[0] != 0) return fail(VBCSR_ERR_PATTERN, "block_row_ptr[0] must be 0");
+    for (int64_t i = 0; i < n_brows; ++i)
+        if (block_row_ptr[i + 1] < block_row_ptr[i]) return fail(VBCSR_ERR_PATTERN, "block_row_ptr decreases");
+    const int64_t nblk = block_row_ptr[n_brows];
+    if (nblk > 0 && !block_col_idx) return fail(VBCSR_ERR_INVALID_ARG, "block_col_idx is NULL");
+    std::vector<int32_t> gcol;
+    try {
+        gcol.resize(nblk);
+    } catch (const std::bad_alloc &) {
+        return fail(VBCSR_ERR_NO_MEMORY, "host allocation");
+    }
+    for (int64_t s = 0; s < n_structs; ++s) {
+        const int64_t ncol_s = sco[s + 1] - sco[s];
+        for (int64_t i = sbo[s]; i < sbo[s + 1]; ++i)
+            for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u) {
+                const int32_t c = block_col_idx[u];
+                if (c < 0 || c >= ncol_s)
+                    return fail(VBCSR_ERR_PATTERN, "local column %d of block row %lld outside structure %lld", c,
+                                (long long)i, (long long)s);
+                gcol[u] = (int32_t)(c + sco[s]);
+            }
+    }
+    return create_common(out, n_brows, n_bcols, row_bsize, col_bsize, block_row_ptr, gcol.data(), values, dtype,
+                         values_on_device, stream, (int32_t)n_structs);
+}
+
+extern "C" int vbcsr_destroy(vbcsr_t *A) {
+    delete A;
+    return VBCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// values
+
+static int refresh_panel32(vbcsr_t *A, cudaStream_t s) {
+    if (A->dtype != VBCSR_F64) return VBCSR_OK;
+    if (!A->panel32) CUDA_TRY(A->alloc(&A->panel32, (size_t)A->panel_elems), "alloc FP32 value copy");
+    CUDA_TRY(launch_convert_f64_to_f32((const double *)A->panel, A->panel32, A->panel_elems, s), "convert");
+    A->panel32_valid = true;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (on_device != 0 && on_device != 1) return fail(VBCSR_ERR_INVALID_ARG, "on_device must be 0 or 1");
+    if (A->nnz == 0) return VBCSR_OK;
+    if (!values) return fail(VBCSR_ERR_INVALID_ARG, "values is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *src = values;
+    void *staged = nullptr;
+    if (!on_device) {
+        CUDA_TRY(cudaMalloc(&staged, (size_t)A->nnz * A->esize), "alloc staging");
+        cudaError_t e = cudaMemcpyAsync(staged, values, (size_t)A->nnz * A->esize, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { cudaFree(staged); return cuda_fail(e, "copy values"); }
+        src = staged;
+    }
+    cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, true, A->nblk, A->fl_uoff, A->fl_pbase, A->fl_kp,
+                                          A->fl_bi, A->fl_w, src, A->panel, s);
+    if (staged) {
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(staged);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "set_values");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "set_values");
+    if (A->panel32) return refresh_panel32(A, s);
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_get_values(const vbcsr_t *Ac, void *values, int on_device, void *stream) {
+    vbcsr_t *A = const_cast<vbcsr_t *>(Ac);
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (on_device != 0 && on_device != 1) return fail(VBCSR_ERR_INVALID_ARG, "on_device must be 0 or 1");
+    if (A->nnz == 0) return VBCSR_OK;
+    if (!values) return fail(VBCSR_ERR_INVALID_ARG, "values is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dst = values;
+    void *staged = nullptr;
+    if (!on_device) {
+        CUDA_TRY(cudaMalloc(&staged, (size_t)A->nnz * A->esize), "alloc staging");
+        dst = staged;
+    }
+    cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, false, A->nblk, A->fl_uoff, A->fl_pbase,
+                                          A->fl_kp, A->fl_bi, A->fl_w, dst, A->panel, s);
+    if (staged) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(values, staged, (size_t)A->nnz * A->esize, cudaMemcpyDeviceToHost, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(staged);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "get_values");
+    return VBCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// products
+
+namespace vbcsr {
+const void *fma_f64_kernel(bool trans);
+const void *fma_f32_kernel(bool trans);
+const void *fma_f32_on_f64_kernel(bool trans);
+const void *mma_kernel_ptr(int mode, bool xdouble, bool trans);
+}  // namespace vbcsr
+
+// True when the [rows, k] windows of two row-major panels share an element.
+// Disjoint column slices of one wider panel (equal leading dimensions) do not.
+static bool overlap(const void *a, int64_t rows_a, int64_t lda, const void *b, int64_t rows_b, int64_t ldb,
+                    int64_t k, size_t es) {
+    if (rows_a == 0 || rows_b == 0) return false;
+    const char *a0 = (const char *)a, *a1 = a0 + ((rows_a - 1) * lda + k) * (int64_t)es;
+    const char *b0 = (const char *)b, *b1 = b0 + ((rows_b - 1) * ldb + k) * (int64_t)es;
+    if (!(a0 < b1 && b0 < a1)) return false;
+    if (lda == ldb && lda > 1) {
+        const int64_t bytes = (int64_t)(b0 - a0);
+        if (bytes % (int64_t)es == 0) {
+            const int64_t d = bytes / (int64_t)es;
+            const int64_t r = ((d % lda) + lda) % lda;
+            if (r >= k && r <= lda - k) return false;
+        }
+    }
+    return true;
+}
+
+static int auto_kc(int64_t k) {
+    int kc = 1;
+    while (kc < k && kc < 32) kc <<= 1;
+    return kc;
+}
+
+static int cached_cap(const void *kernel, int warps, size_t smem) {
+    static std::map<std::pair<const void *, int>, int> cache;
+    auto key = std::make_pair(kernel, warps);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int c = max_resident_ctas(kernel, warps * 32, smem);
+    cache[key] = c;
+    return c;
+}
+
+static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const void *X, int64_t ldx, double beta,
+                       void *Y, int64_t ldy, const vbcsr_epilogue_t *epi, int precision, cudaStream_t s) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
+    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_BF16X2)
+        return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+    const int64_t xrows = trans ? A->n_rows : A->n_cols;
+    const int64_t yrows = trans ? A->n_cols : A->n_rows;
+    const bool want_dot = epi && epi->dot_out;
+    if (k == 0 || yrows == 0) {
+        if (want_dot) CUDA_TRY(cudaMemsetAsync(epi->dot_out, 0, sizeof(double), s), "memset dot");
+        return VBCSR_OK;
+    }
+    if (ldx < k || ldy < k) return fail(VBCSR_ERR_INVALID_ARG, "leading dimension below k");
+    if (!Y) return fail(VBCSR_ERR_INVALID_ARG, "Y is NULL");
+    if (alpha != 0.0 && xrows > 0 && !X) return fail(VBCSR_ERR_INVALID_ARG, "X is NULL");
+    if (alpha != 0.0 && X && overlap(X, xrows, ldx, Y, yrows, ldy, k, A->esize))
+        return fail(VBCSR_ERR_ALIAS, "Y overlaps X");
+    const double gamma = epi ? epi->gamma : 0.0;
+    if (gamma != 0.0 && (!epi->Z || epi->ldz < k)) return fail(VBCSR_ERR_INVALID_ARG, "epilogue Z / ldz");
+    if (want_dot && (!epi->R || epi->ldr < k)) return fail(VBCSR_ERR_INVALID_ARG, "epilogue R / ldr");
+
+    const bool f64 = A->dtype == VBCSR_F64;
+    int mode = precision;
+    if (!f64 && mode == VBCSR_PREC_F32) mode = VBCSR_PREC_NATIVE;
+    if (f64 && mode != VBCSR_PREC_NATIVE && !A->panel32_valid) {
+        int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+
+    ProdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.values = (f64 && mode != VBCSR_PREC_NATIVE) ? (const void *)A->panel32 : A->panel;
+    a.fl = {A->fl_xrow, A->fl_pcol, A->fl_w};
+    a.tl = {A->tl_pbase, A->tl_kp, A->tl_bi, A->tl_xrow, A->tl_vcol};
+    a.k = k;
+    a.kc = A->kc ? A->kc : auto_kc(k);
+    a.alpha = alpha;
+    a.beta = beta;
+    a.gamma = gamma;
+    a.X = X;
+    a.ldx = ldx;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.Z = gamma != 0.0 ? epi->Z : nullptr;
+    a.ldz = gamma != 0.0 ? epi->ldz : 0;
+    a.R = want_dot ? epi->R : nullptr;
+    a.ldr = want_dot ? epi->ldr : 0;
+    a.x_rows = xrows;
+    a.err = A->err;
+    a.debug_checks = A->debug_checks;
+    a.warps = A->warps ? A->warps : 4;
+
+    const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
+    const WorkItem *items = trans ? A->adj_items : A->fwd_items;
+    const void *kern = nullptr;
+    size_t smem = 0;
+    if (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32) {
+        kern = (mode == VBCSR_PREC_NATIVE) ? (f64 ? fma_f64_kernel(trans) : fma_f32_kernel(trans))
+                                           : fma_f32_on_f64_kernel(trans);
+        smem = fma_smem_bytes(trans, a.warps);
+    } else {
+        kern = mma_kernel_ptr(mode, f64, trans);
+        if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
+        a.warps = 4;
+        smem = mma_smem_bytes(trans, a.warps);
+    }
+    const int cap = cached_cap(kern, a.warps, smem);
+
+    int64_t used = 0;
+    for (const Bucket &b : buckets) {
+        a.items = items + b.begin;
+        a.n_items = b.count;
+        const int64_t need = (b.count + a.warps - 1) / a.warps;
+        a.grid = (int)std::min<int64_t>(need, cap);
+        if (want_dot) {
+            if (used + a.grid > kPartialsCap) return fail(VBCSR_ERR_UNSUPPORTED, "too many CTAs for the dot");
+            a.partials = A->partials + used;
+            used += a.grid;
+        }
+        cudaError_t e;
+        if (mode == VBCSR_PREC_NATIVE)
+            e = f64 ? launch_fma_f64(b.B, trans, a, s) : launch_fma_f32(b.B, trans, a, s);
+        else if (mode == VBCSR_PREC_F32)
+            e = launch_fma_f32_on_f64(b.B, trans, a, s);
+        else
+            e = launch_mma(mode, f64, trans, a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "product launch");
+    }
+    if (want_dot) CUDA_TRY(launch_finalize_dot(A->partials, used, 1.0, epi->dot_out, s), "dot finalize");
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_spmm(vbcsr_t *A, int64_t k, double alpha, const void *X, int64_t ldx, double beta, void *Y,
+                          int64_t ldy, int precision, void *stream) {
+    return run_product(A, false, k, alpha, X, ldx, beta, Y, ldy, nullptr, precision, (cudaStream_t)stream);
+}
+
+extern "C" int vbcsr_spmm_adjoint(vbcsr_t *A, int64_t k, double alpha, const void *X, int64_t ldx, double beta,
+                                  void *Y, int64_t ldy, int precision, void *stream) {
+    return run_product(A, true, k, alpha, X, ldx, beta, Y, ldy, nullptr, precision, (cudaStream_t)stream);
+}
+
+extern "C" int vbcsr_spmm_ex(vbcsr_t *A, int transpose, int64_t k, double alpha, const void *X, int64_t ldx,
+                             double beta, void *Y, int64_t ldy, const vbcsr_epilogue_t *epi, int precision,
+                             void *stream) {
+    if (transpose != 0 && transpose != 1) return fail(VBCSR_ERR_INVALID_ARG, "transpose must be 0 or 1");
+    return run_product(A, transpose == 1, k, alpha, X, ldx, beta, Y, ldy, epi, precision, (cudaStream_t)stream);
+}
+
+extern "C" int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop, int64_t lda, const void *Bop,
+                           int64_t ldb, double beta, void *D, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
+    if (A->nnz == 0) return VBCSR_OK;
+    if (!D) return fail(VBCSR_ERR_INVALID_ARG, "D is NULL");
+    if (k > 0 && alpha != 0.0) {
+        if (!Aop || !Bop) return fail(VBCSR_ERR_INVALID_ARG, "operand is NULL");
+        if (lda < k || ldb < k) return fail(VBCSR_ERR_INVALID_ARG, "leading dimension below k");
+    }
+    SddmmArgs a;
+    a.n_brows = A->n_brows;
+    a.prow_ptr = A->prow_ptr;
+    a.row_off = A->d_row_off;
+    a.row_b = A->d_row_b;
+    a.fl_xrow = A->fl_xrow;
+    a.fl_w = A->fl_w;
+    a.fl_uoff = A->fl_uoff;
+    a.k = alpha != 0.0 ? k : 0;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.A = Aop;
+    a.lda = lda;
+    a.B = Bop;
+    a.ldb = ldb;
+    a.D = D;
+    CUDA_TRY(launch_sddmm(A->dtype == VBCSR_F64, a, (cudaStream_t)stream), "sddmm launch");
+    return VBCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev moments (kernel polynomial method, Sec. V)
+
+extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                               double *moments, double *work, double *ckpt, int64_t ckpt_every, int precision,
+                               void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
+    if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
+    if (k < 1 || n_moments < 1) return fail(VBCSR_ERR_INVALID_ARG, "k and n_moments must be >= 1");
+    if (!R || !moments || !work || ldr < k) return fail(VBCSR_ERR_INVALID_ARG, "R / moments / work / ldr");
+    if (ckpt && ckpt_every < 1) return fail(VBCSR_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = A->n_rows, panel = N * k;
+    const double scale = 1.0 / ((double)N * (double)k);
+    double *buf[2] = {work, work + panel};
+
+    int64_t used = 0;
+    CUDA_TRY(launch_dot_panels(true, N, k, R, ldr, R, ldr, A->partials, kPartialsCap, &used, s), "dot");
+    CUDA_TRY(launch_finalize_dot(A->partials, used, scale, moments, s), "dot");
+    if (n_moments == 1) return VBCSR_OK;
+
+    vbcsr_epilogue_t epi;
+    memset(&epi, 0, sizeof(epi));
+    epi.R = R;
+    epi.ldr = ldr;
+    // t_1 = H~ R  -> buf[1];  t_0 (a copy of R) -> buf[0]
+    epi.dot_out = moments + 1;
+    int rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s);
+    if (rc) return rc;
+    auto store_pair = [&](int64_t m, const double *tm, int64_t ldm, const double *tm1) -> int {
+        if (!ckpt || m % ckpt_every) return VBCSR_OK;
+        double *slot = ckpt + (m / ckpt_every) * 2 * panel;
+        CUDA_TRY(launch_copy_panel(N, k, tm, ldm, slot, k, s), "checkpoint");
+        CUDA_TRY(launch_copy_panel(N, k, tm1, k, slot + panel, k, s), "checkpoint");
+        return VBCSR_OK;
+    };
+    if ((rc = store_pair(0, R, ldr, buf[1]))) return rc;
+    if (n_moments == 2) return VBCSR_OK;
+    CUDA_TRY(launch_copy_panel(N, k, R, ldr, buf[0], k, s), "copy R");
+    // t_{n+1} = 2 H~ t_n - t_{n-1}: t_n in buf[n & 1], t_{n-1} (overwritten by t_{n+1}) in buf[(n+1) & 1]
+    for (int64_t n = 1; n + 1 < n_moments; ++n) {
+        double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
+        epi.dot_out = moments + n + 1;
+        rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s);
+        if (rc) return rc;
+        if ((rc = store_pair(n, tn, k, tprev))) return rc;
+    }
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t M,
+                                        const double *grad_mu, const double *ckpt, int64_t E, double *dvalues,
+                                        double *work, int precision, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
+    if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
+    if (k < 1 || M < 1 || E < 1) return fail(VBCSR_ERR_INVALID_ARG, "k, n_moments and ckpt_every must be >= 1");
+    if (!R || ldr < k || !grad_mu || !dvalues || !work || (M > 1 && !ckpt))
+        return fail(VBCSR_ERR_INVALID_ARG, "NULL argument or ldr < k");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = A->n_rows, panel = N * k, wide = E * k;
+    if (A->nnz) CUDA_TRY(cudaMemsetAsync(dvalues, 0, (size_t)A->nnz * sizeof(double), s), "memset");
+    if (M < 2) return VBCSR_OK;
+    std::vector<double> gm(M);
+    CUDA_TRY(cudaMemcpyAsync(gm.data(), grad_mu, M * sizeof(double), cudaMemcpyDeviceToHost, s), "copy grad_mu");
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    const double scale = 1.0 / ((double)N * (double)k);
+    double *cur = work, *nxt = work + panel;          // lam_{n+1}, lam_{n+2}
+    double *T = work + 2 * panel, *L = T + N * wide;  // [N, E k] segment panels
+    // lam_{M-1} = g_{M-1};  lam_M = 0
+    CUDA_TRY(launch_axpby(N, k, gm[M - 1] * scale, R, ldr, 0.0, cur, k, s), "axpby");
+    CUDA_TRY(cudaMemsetAsync(nxt, 0, (size_t)panel * sizeof(double), s), "memset");
+    const int64_t nseg = (M - 1 + E - 1) / E;
+    bool first = true;
+    int rc;
+    vbcsr_epilogue_t epi;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t n_lo = sg * E, n_hi = std::min((sg + 1) * E - 1, M - 2);
+        const int64_t cnt = n_hi - n_lo + 1;
+        const double *pair = ckpt + sg * 2 * panel;
+        // recompute t_{n_lo} .. t_{n_hi} into the column slots of T
+        CUDA_TRY(launch_copy_panel(N, k, pair, k, T, wide, s), "restore checkpoint");
+        if (cnt > 1) CUDA_TRY(launch_copy_panel(N, k, pair + panel, k, T + k, wide, s), "restore checkpoint");
+        for (int64_t e = 1; e + 1 < cnt; ++e) {
+            memset(&epi, 0, sizeof(epi));
+            epi.gamma = -1.0;
+            epi.Z = T + (e - 1) * k;
+            epi.ldz = wide;
+            rc = run_product(A, false, k, 2.0, T + e * k, wide, 0.0, T + (e + 1) * k, wide, &epi, precision, s);
+            if (rc) return rc;
+        }
+        for (int64_t n = n_hi; n >= n_lo; --n) {
+            const int64_t e = n - n_lo;
+            CUDA_TRY(launch_axpby(N, k, n >= 1 ? 2.0 : 1.0, cur, k, 0.0, L + e * k, wide, s), "axpby");
+            if (n >= 1) {
+                memset(&epi, 0, sizeof(epi));
+                epi.gamma = gm[n] * scale;
+                epi.Z = R;
+                epi.ldz = ldr;
+                rc = run_product(A, true, k, 2.0, cur, k, -1.0, nxt, k, &epi, precision, s);
+                if (rc) return rc;
+                std::swap(cur, nxt);
+            }
+        }
+        SddmmArgs a;
+        a.n_brows = A->n_brows;
+        a.prow_ptr = A->prow_ptr;
+        a.row_off = A->d_row_off;
+        a.row_b = A->d_row_b;
+        a.fl_xrow = A->fl_xrow;
+        a.fl_w = A->fl_w;
+        a.fl_uoff = A->fl_uoff;
+        a.k = cnt * k;
+        a.alpha = 1.0;
+        a.beta = first ? 0.0 : 1.0;
+        a.A = L;
+        a.lda = wide;
+        a.B = T;
+        a.ldb = wide;
+        a.D = dvalues;
+        if (A->nnz) CUDA_TRY(launch_sddmm(true, a, s), "sddmm");
+        first = false;
+    }
+    return VBCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inspection and control
+
+extern "C" int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out) {
+    if (!A || !out) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
+    out->n_brows = A->n_brows;
+    out->n_bcols = A->n_bcols;
+    out->n_rows = A->n_rows;
+    out->n_cols = A->n_cols;
+    out->nblk = A->nblk;
+    out->nnz = A->nnz;
+    out->panel_elems = A->panel_elems;
+    out->device_bytes = A->device_bytes;
+    out->dtype = A->dtype;
+    out->n_shape_classes = (int32_t)A->cls_bi.size();
+    out->n_row_classes = (int32_t)A->fwd_buckets.size();
+    out->n_structs = A->n_structs;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, int64_t *count, int32_t cap) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (cap < 0 || (cap > 0 && (!bi || !bj || !count))) return fail(VBCSR_ERR_INVALID_ARG, "output arrays");
+    const int32_t n = (int32_t)A->cls_bi.size();
+    for (int32_t c = 0; c < n && c < cap; ++c) {
+        bi[c] = A->cls_bi[c];
+        bj[c] = A->cls_bj[c];
+        count[c] = A->cls_count[c];
+    }
+    return n;
+}
+
+extern "C" int vbcsr_set_tuning(vbcsr_t *A, int32_t kc, int32_t warps) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(kc == 0 || kc == 1 || kc == 2 || kc == 4 || kc == 8 || kc == 16 || kc == 32))
+        return fail(VBCSR_ERR_INVALID_ARG, "kc = %d", kc);
+    if (!(warps == 0 || warps == 1 || warps == 2 || warps == 4 || warps == 8))
+        return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", warps);
+    A->kc = kc;
+    A->warps = warps;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_check(vbcsr_t *A, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+    int h = 0;
+    CUDA_TRY(cudaMemcpy(&h, A->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (h != 0) {
+        CUDA_TRY(cudaMemset(A->err, 0, sizeof(int)), "clear error word");
+        return fail(VBCSR_ERR_DEVICE_CHECK, "device self-check code %d", h);
+    }
+    return VBCSR_OK;
+}

@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device data layout of a handle (built once by the planner in api.cu):
+//
+//  * Value pages. Block row i is stored as one dense row-major "panel"
+//    P_i of b_i rows and Kp_i columns: its stored blocks side by side in
+//    increasing column order (K_i = sum_{j in J(i)} b_j columns, zero-padded
+//    to Kp_i = roundup(K_i, 8) so that every panel row starts 64-byte aligned
+//    in FP64 and 32-byte aligned in FP32). Panels are laid out grouped by row
+//    height b_i, so each row class is one contiguous page (the shape-grouped
+//    pages of Sec. III.B). Then Y_i = P_i * X[g_i, :], where g_i lists the X
+//    row of every panel column.
+//  * Plan block list ("fl_*", one entry per stored block, row-major order with
+//    columns sorted): X row c_j of its first column, its first panel column,
+//    b_j, the user (packed-order) value offset, the panel element of its
+//    (0, 0) entry, the panel stride and b_i.
+//  * Transposed list ("tl_*", one entry per stored block, grouped by block
+//    column, rows increasing): what the adjoint needs to walk column j.
+//  * Work items: one warp task = up to 16 consecutive output rows of one block
+//    row (forward) or block column (adjoint); items are bucketed by their row
+//    count B so that each bucket runs as one launch of a kernel specialised
+//    for B.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vbcsr {
+
+constexpr int kMaxB = 16;        // rows per work item
+constexpr int kPadK = 8;         // panel width padding (elements)
+constexpr int kKMax = 512;       // virtual columns staged in shared memory per pass
+constexpr int kPartialsCap = 1 << 16;
+
+// One warp task.
+struct WorkItem {
+    int64_t vbase;   // forward: panel element of (first row of the item, column 0)
+    int64_t yrow;    // first scalar output row
+    int64_t lbegin;  // first entry in the plan block list (forward) / transposed list (adjoint)
+    int32_t nlist;   // entries in that list
+    int32_t K;       // virtual columns: K_i (forward) / sum of b_i over the column's blocks (adjoint)
+    int32_t Kp;      // forward: panel row stride; adjoint: first row q0 inside the block column
+    int32_t B;       // output rows of the item (1..16)
+};
+
+struct FwdList {
+    const int32_t *xrow;   // c_j
+    const int32_t *pcol;   // first panel column of the block
+    const int32_t *w;      // b_j
+};
+
+struct AdjList {
+    const int64_t *pbase;  // panel element of H_ij[0, 0]
+    const int32_t *kp;     // panel stride of row i
+    const int32_t *bi;     // b_i
+    const int32_t *xrow;   // r_i
+    const int32_t *vcol;   // first virtual column of the entry inside its block column
+};
+
+// Arguments of one product launch (one bucket of work items).
+struct ProdArgs {
+    const WorkItem *items;
+    int64_t n_items;
+    const void *values;     // panel values (FP64 or FP32 copy)
+    FwdList fl;
+    AdjList tl;
+    int64_t k;
+    int kc;                 // output columns per warp pass (power of two <= 32)
+    double alpha, beta, gamma;
+    const void *X; int64_t ldx;
+    void *Y; int64_t ldy;
+    const void *Z; int64_t ldz;
+    const void *R; int64_t ldr;
+    double *partials;       // per-CTA dot partials (NULL: no dot)
+    int64_t x_rows;         // rows of X (bounds check)
+    int *err;               // device error word
+    int debug_checks;
+    int grid;               // CTAs
+    int warps;              // warps per CTA
+};
+
+// Kernel families (defined in spmm_fma_*.cu and spmm_mma.cu).
+// value/accumulate/X types: f64 = <double,double,double>; f32 = <float,float,float>;
+// f32_on_f64 = <float,float,double> (FP32 arithmetic on an FP64 operator).
+cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+cudaError_t launch_fma_f32(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+// mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
+cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
+
+// Occupancy-derived CTA count cap for a kernel family (computed once).
+int max_resident_ctas(const void *kernel, int threads, size_t smem);
+
+size_t fma_smem_bytes(bool trans, int warps);
+size_t mma_smem_bytes(bool trans, int warps);
+
+// Misc kernels (misc.cu).
+struct SddmmArgs {
+    int64_t n_brows;
+    const int64_t *prow_ptr;    // plan block range of every block row
+    const int64_t *row_off;     // r_i
+    const int32_t *row_b;       // b_i
+    const int32_t *fl_xrow;     // c_j
+    const int32_t *fl_w;        // b_j
+    const int64_t *fl_uoff;     // packed-order offset of the block
+    int64_t k;
+    double alpha, beta;
+    const void *A; int64_t lda;
+    const void *B; int64_t ldb;
+    void *D;
+};
+cudaError_t launch_sddmm(bool f64, const SddmmArgs &a, cudaStream_t s);
+
+// scatter (to_panel = true) or gather packed-order values <-> panels
+cudaError_t launch_permute_values(bool f64, bool to_panel, int64_t nblk, const int64_t *uoff,
+                                  const int64_t *pbase, const int32_t *kp, const int32_t *bi,
+                                  const int32_t *bj, const void *user, void *panel, cudaStream_t s);
+cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
+// out[0] = scale * sum(partials[0..n)) in a fixed order
+cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out,
+                                cudaStream_t s);
+// partials[b] = sum over CTA b of A .* B ([rows, k] panels); returns CTAs used in *n_used
+cudaError_t launch_dot_panels(bool f64, int64_t rows, int64_t k, const void *A, int64_t lda,
+                              const void *B, int64_t ldb, double *partials, int64_t cap,
+                              int64_t *n_used, cudaStream_t s);
+// Y = alpha X + beta Y on [rows, k] FP64 panels (beta == 0: Y not read)
+cudaError_t launch_axpby(int64_t rows, int64_t k, double alpha, const double *X, int64_t ldx, double beta,
+                         double *Y, int64_t ldy, cudaStream_t s);
+// dst[rows, k] (ld ldd) = src (ld lds), FP64
+cudaError_t launch_copy_panel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst,
+                              int64_t ldd, cudaStream_t s);
+
+}  // namespace vbcsr

@@ -1,0 +1,213 @@
+// Pattern-sampled product (SDDMM), value permutation between packed order and
+// panels, and the fixed-order FP64 reductions used by the Chebyshev moments.
+#include "internal.cuh"
+
+namespace vbcsr {
+
+size_t fma_smem_bytes(bool trans, int warps) {
+    return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0));
+}
+
+int max_resident_ctas(const void *kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+// ---------------------------------------------------------------------------
+// SDDMM: D_ij[p, q] = alpha * <A[r_i + p, :], B[c_j + q, :]> + beta * D_ij[p, q].
+// One warp per block row; lanes own output entries of the current block, so
+// the block's packed-order output is written contiguously.
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
+__global__ void sddmm_kernel(SddmmArgs a, int warps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *__restrict__ A = static_cast<const T *>(a.A);
+    const T *__restrict__ Bm = static_cast<const T *>(a.B);
+    T *__restrict__ D = static_cast<T *>(a.D);
+    const T alpha = (T)a.alpha, beta = (T)a.beta;
+    for (int64_t i = (int64_t)blockIdx.x * warps + warp; i < a.n_brows; i += (int64_t)gridDim.x * warps) {
+        const int64_t ri = a.row_off[i];
+        const int bi = a.row_b[i];
+        for (int64_t l = a.prow_ptr[i]; l < a.prow_ptr[i + 1]; ++l) {
+            const int bj = a.fl_w[l];
+            const int64_t cj = a.fl_xrow[l];
+            T *d = D + a.fl_uoff[l];
+            const int ne = bi * bj;
+            for (int e = lane; e < ne; e += 32) {
+                const int p = e / bj, q = e - (e / bj) * bj;
+                const T *ar = A + (ri + p) * a.lda;
+                const T *br = Bm + (cj + q) * a.ldb;
+                T s = (T)0;
+                for (int64_t c = 0; c < a.k; ++c) s = fma_t(__ldg(ar + c), __ldg(br + c), s);
+                T r = alpha * s;
+                if (a.beta != 0.0) r += beta * d[e];
+                d[e] = r;
+            }
+        }
+    }
+}
+
+cudaError_t launch_sddmm(bool f64, const SddmmArgs &a, cudaStream_t s) {
+    if (a.n_brows == 0) return cudaSuccess;
+    const int warps = 8, threads = warps * 32;
+    static int cap64 = 0, cap32 = 0;
+    int &cap = f64 ? cap64 : cap32;
+    if (!cap)
+        cap = max_resident_ctas(f64 ? (const void *)sddmm_kernel<double> : (const void *)sddmm_kernel<float>,
+                                threads, 0);
+    int64_t need = (a.n_brows + warps - 1) / warps;
+    int grid = (int)(need < cap ? need : cap);
+    if (f64) sddmm_kernel<double><<<grid, threads, 0, s>>>(a, warps);
+    else sddmm_kernel<float><<<grid, threads, 0, s>>>(a, warps);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// packed order <-> panels (one warp per block)
+
+template <typename T>
+__global__ void permute_kernel(bool to_panel, int64_t nblk, const int64_t *uoff, const int64_t *pbase,
+                               const int32_t *kp, const int32_t *bi, const int32_t *bj, const T *user,
+                               T *panel, int warps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t l = (int64_t)blockIdx.x * warps + warp; l < nblk; l += (int64_t)gridDim.x * warps) {
+        const int w = bj[l], h = bi[l];
+        const int64_t u = uoff[l], pb = pbase[l], stride = kp[l];
+        for (int e = lane; e < h * w; e += 32) {
+            const int p = e / w, q = e - p * w;
+            if (to_panel) panel[pb + p * stride + q] = user[u + e];
+            else ((T *)user)[u + e] = panel[pb + p * stride + q];
+        }
+    }
+}
+
+cudaError_t launch_permute_values(bool f64, bool to_panel, int64_t nblk, const int64_t *uoff,
+                                  const int64_t *pbase, const int32_t *kp, const int32_t *bi,
+                                  const int32_t *bj, const void *user, void *panel, cudaStream_t s) {
+    if (nblk == 0) return cudaSuccess;
+    const int warps = 8;
+    int64_t need = (nblk + warps - 1) / warps;
+    int grid = (int)(need < 65536 ? need : 65536);
+    if (f64)
+        permute_kernel<double><<<grid, warps * 32, 0, s>>>(to_panel, nblk, uoff, pbase, kp, bi, bj,
+                                                           (const double *)user, (double *)panel, warps);
+    else
+        permute_kernel<float><<<grid, warps * 32, 0, s>>>(to_panel, nblk, uoff, pbase, kp, bi, bj,
+                                                          (const float *)user, (float *)panel, warps);
+    return cudaGetLastError();
+}
+
+__global__ void convert_kernel(const double *in, float *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t need = (n + 255) / 256;
+    convert_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fixed-order reductions
+
+__global__ void finalize_dot_kernel(const double *partials, int64_t n, double scale, double *out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += partials[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int m = blockDim.x / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) sh[threadIdx.x] += sh[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = scale * sh[0];
+}
+
+cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out, cudaStream_t s) {
+    finalize_dot_kernel<<<1, 256, 0, s>>>(partials, n, scale, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void dot_panels_kernel(int64_t rows, int64_t k, const T *A, int64_t lda, const T *B, int64_t ldb,
+                                  double *partials) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        s += (double)A[r * lda + c] * (double)B[r * ldb + c];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int m = blockDim.x / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) sh[threadIdx.x] += sh[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_dot_panels(bool f64, int64_t rows, int64_t k, const void *A, int64_t lda, const void *B,
+                              int64_t ldb, double *partials, int64_t cap, int64_t *n_used, cudaStream_t s) {
+    int64_t need = (rows * k + 255) / 256;
+    int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+    if (grid > 4096) grid = 4096;
+    if (f64)
+        dot_panels_kernel<double><<<grid, 256, 0, s>>>(rows, k, (const double *)A, lda, (const double *)B, ldb,
+                                                       partials);
+    else
+        dot_panels_kernel<float><<<grid, 256, 0, s>>>(rows, k, (const float *)A, lda, (const float *)B, ldb,
+                                                      partials);
+    *n_used = grid;
+    return cudaGetLastError();
+}
+
+__global__ void copy_panel_kernel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst,
+                                  int64_t ldd) {
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        dst[r * ldd + c] = src[r * lds + c];
+    }
+}
+
+cudaError_t launch_copy_panel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst, int64_t ldd,
+                              cudaStream_t s) {
+    int64_t need = (rows * k + 255) / 256;
+    if (need == 0) return cudaSuccess;
+    copy_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, src, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+__global__ void axpby_kernel(int64_t rows, int64_t k, double alpha, const double *X, int64_t ldx, double beta,
+                             double *Y, int64_t ldy) {
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        double v = alpha * X[r * ldx + c];
+        if (beta != 0.0) v += beta * Y[r * ldy + c];
+        Y[r * ldy + c] = v;
+    }
+}
+
+cudaError_t launch_axpby(int64_t rows, int64_t k, double alpha, const double *X, int64_t ldx, double beta,
+                         double *Y, int64_t ldy, cudaStream_t s) {
+    int64_t need = (rows * k + 255) / 256;
+    if (need == 0) return cudaSuccess;
+    axpby_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, alpha, X, ldx, beta, Y, ldy);
+    return cudaGetLastError();
+}
+
+}  // namespace vbcsr

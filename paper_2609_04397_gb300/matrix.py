@@ -1,0 +1,257 @@
+"""The VBCSR operator object: a thin PyTorch-facing wrapper of the C ABI.
+
+PyTorch only provides device memory and the current CUDA stream; every
+product, permutation and reduction runs in libvbcsr.so.
+"""
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import F32, F64, PRECISION, check, lib
+
+_TORCH_DTYPE = {F64: torch.float64, F32: torch.float32}
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(np.asarray(a), dtype=dt)
+
+
+def _prec(precision) -> int:
+    if isinstance(precision, int):
+        return precision
+    return PRECISION[precision.lower()]
+
+
+class VBCSR:
+    """A variable-block sparse operator resident on one GPU (Sec. II.A)."""
+
+    def __init__(self, handle: ctypes.c_void_p, dtype: int, device: torch.device, pattern):
+        self._h = handle
+        self._dtype = dtype
+        self.device = device
+        self.pattern = pattern           # (row_bsize, col_bsize, block_row_ptr, block_col_idx) as numpy
+        info = _lib.Info()
+        check(lib().vbcsr_get_info(self._h, ctypes.byref(info)), "vbcsr_get_info")
+        self.info = info
+
+    # ---- construction ---------------------------------------------------
+
+    @classmethod
+    def from_arrays(cls, row_bsize, col_bsize, block_row_ptr, block_col_idx, values,
+                    dtype: torch.dtype = torch.float64, device=None) -> "VBCSR":
+        """Build from host pattern arrays and packed values (numpy array or
+        torch tensor, host or device), blocks row-major in pattern order."""
+        device = torch.device(device or "cuda")
+        dt = F64 if dtype == torch.float64 else F32
+        rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
+        rp, ci = _np(block_row_ptr, np.int64), _np(block_col_idx, np.int32)
+        on_dev, vptr, keep = cls._values_arg(values, dtype, device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            check(lib().vbcsr_create(ctypes.byref(h), len(rb), len(cb), rb.ctypes.data, cb.ctypes.data,
+                                     rp.ctypes.data, ci.ctypes.data, vptr, dt, on_dev, _stream(device)),
+                  "vbcsr_create")
+        del keep
+        return cls(h, dt, device, (rb, cb, rp, ci))
+
+    @classmethod
+    def from_pattern(cls, pattern, values, dtype=torch.float64, device=None) -> "VBCSR":
+        return cls.from_arrays(pattern.row_bsize, pattern.col_bsize, pattern.block_row_ptr,
+                               pattern.block_col_idx, values, dtype, device)
+
+    @classmethod
+    def from_batched(cls, struct_brow_offsets, struct_bcol_offsets, row_bsize, col_bsize,
+                     block_row_ptr, local_block_col_idx, values, dtype=torch.float64, device=None) -> "VBCSR":
+        """One operator over independent structures; column indices local to
+        each structure (see vbcsr_create_batched)."""
+        device = torch.device(device or "cuda")
+        dt = F64 if dtype == torch.float64 else F32
+        so, co = _np(struct_brow_offsets, np.int64), _np(struct_bcol_offsets, np.int64)
+        rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
+        rp, ci = _np(block_row_ptr, np.int64), _np(local_block_col_idx, np.int32)
+        on_dev, vptr, keep = cls._values_arg(values, dtype, device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            check(lib().vbcsr_create_batched(ctypes.byref(h), len(so) - 1, so.ctypes.data, co.ctypes.data,
+                                             rb.ctypes.data, cb.ctypes.data, rp.ctypes.data, ci.ctypes.data,
+                                             vptr, dt, on_dev, _stream(device)), "vbcsr_create_batched")
+        del keep
+        gcol = ci.astype(np.int64).copy()
+        rows = np.repeat(np.arange(len(rb)), np.diff(rp))
+        s_of_row = np.searchsorted(so, rows, side="right") - 1
+        gcol += co[s_of_row]
+        return cls(h, dt, device, (rb, cb, rp, gcol.astype(np.int32)))
+
+    @staticmethod
+    def _values_arg(values, dtype, device):
+        if isinstance(values, torch.Tensor):
+            if values.dtype != dtype:
+                raise TypeError(f"values dtype {values.dtype} != {dtype}")
+            v = values.contiguous()
+            if v.is_cuda:
+                return 1, v.data_ptr(), v
+            return 0, v.data_ptr(), v
+        v = np.ascontiguousarray(values, dtype=np.float64 if dtype == torch.float64 else np.float32)
+        return 0, v.ctypes.data, v
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vbcsr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- properties -----------------------------------------------------
+
+    @property
+    def dtype(self) -> torch.dtype:
+        return _TORCH_DTYPE[self._dtype]
+
+    @property
+    def shape(self):
+        return (int(self.info.n_rows), int(self.info.n_cols))
+
+    @property
+    def nnz(self) -> int:
+        return int(self.info.nnz)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def shape_classes(self):
+        """[(b_i, b_j, count)] from the shape-class registry."""
+        n = check(lib().vbcsr_shape_classes(self._h, None, None, None, 0), "vbcsr_shape_classes")
+        bi = np.zeros(n, np.int32)
+        bj = np.zeros(n, np.int32)
+        cnt = np.zeros(n, np.int64)
+        check(lib().vbcsr_shape_classes(self._h, bi.ctypes.data, bj.ctypes.data, cnt.ctypes.data, n),
+              "vbcsr_shape_classes")
+        return list(zip(bi.tolist(), bj.tolist(), cnt.tolist()))
+
+    def set_tuning(self, kc: int = 0, warps: int = 0):
+        check(lib().vbcsr_set_tuning(self._h, kc, warps), "vbcsr_set_tuning")
+
+    def check(self):
+        check(lib().vbcsr_check(self._h, _stream(self.device)), "vbcsr_check")
+
+    # ---- values ----------------------------------------------------------
+
+    def set_values(self, values):
+        on_dev, vptr, keep = self._values_arg(values, self.dtype, self.device)
+        check(lib().vbcsr_set_values(self._h, vptr, on_dev, _stream(self.device)), "vbcsr_set_values")
+        if on_dev:
+            # the tensor must stay alive until the scatter has run on the stream
+            keep.record_stream(torch.cuda.current_stream(self.device))
+
+    def get_values(self) -> torch.Tensor:
+        out = torch.empty(self.nnz, dtype=self.dtype, device=self.device)
+        check(lib().vbcsr_get_values(self._h, ctypes.c_void_p(out.data_ptr()), 1, _stream(self.device)),
+              "vbcsr_get_values")
+        return out
+
+    # ---- products --------------------------------------------------------
+
+    def _panel(self, T: torch.Tensor, rows: int, name: str):
+        if not isinstance(T, torch.Tensor) or T.device != self.device or T.dtype != self.dtype:
+            raise TypeError(f"{name} must be a {self.dtype} tensor on {self.device}")
+        if T.dim() == 1:
+            T = T.view(-1, 1)
+        if T.dim() != 2 or T.shape[0] != rows or (T.shape[1] > 1 and T.stride(1) != 1):
+            raise ValueError(f"{name} must be a row-major [{rows}, k] panel, got {tuple(T.shape)} "
+                             f"strides {T.stride()}")
+        ld = T.stride(0) if T.shape[1] > 1 or T.shape[0] > 1 else 1
+        return T, max(ld, T.shape[1])
+
+    def _prod(self, transpose: bool, X, alpha, beta, Y, precision, epilogue=None):
+        n_out, n_in = (self.shape[1], self.shape[0]) if transpose else self.shape
+        squeeze = X.dim() == 1
+        X, ldx = self._panel(X, n_in, "X")
+        k = X.shape[1]
+        if Y is None:
+            Y = torch.empty((n_out, k), dtype=self.dtype, device=self.device)
+            beta = 0.0
+        Y2, ldy = self._panel(Y, n_out, "Y")
+        if Y2.shape[1] != k:
+            raise ValueError("X and Y have different column counts")
+        if epilogue is None:
+            fn = lib().vbcsr_spmm_adjoint if transpose else lib().vbcsr_spmm
+            check(fn(self._h, k, float(alpha), ctypes.c_void_p(X.data_ptr()), ldx, float(beta),
+                     ctypes.c_void_p(Y2.data_ptr()), ldy, _prec(precision), _stream(self.device)),
+                  "vbcsr_spmm_adjoint" if transpose else "vbcsr_spmm")
+        else:
+            check(lib().vbcsr_spmm_ex(self._h, int(transpose), k, float(alpha), ctypes.c_void_p(X.data_ptr()),
+                                      ldx, float(beta), ctypes.c_void_p(Y2.data_ptr()), ldy,
+                                      ctypes.byref(epilogue), _prec(precision), _stream(self.device)),
+                  "vbcsr_spmm_ex")
+        return Y.view(-1) if squeeze and Y.dim() == 1 else Y
+
+    def spmm(self, X, alpha=1.0, beta=0.0, Y=None, precision="native"):
+        """Y = alpha H X + beta Y (a new Y when Y is None)."""
+        return self._prod(False, X, alpha, beta, Y, precision)
+
+    def spmm_adjoint(self, X, alpha=1.0, beta=0.0, Y=None, precision="native"):
+        """Y = alpha H^T X + beta Y (Eq. 1)."""
+        return self._prod(True, X, alpha, beta, Y, precision)
+
+    def spmm_ex(self, X, alpha, beta, Y, transpose=False, gamma=0.0, Z=None, R=None,
+                dot_out: Optional[torch.Tensor] = None, precision="native"):
+        """Y = alpha op(H) X + beta Y + gamma Z; dot_out[0] = sum(R * Y)."""
+        epi = _lib.Epilogue()
+        epi.gamma = float(gamma)
+        if gamma != 0.0:
+            Zp, epi.ldz = self._panel(Z, Y.shape[0], "Z")
+            epi.Z = Zp.data_ptr()
+        if dot_out is not None:
+            Rp, epi.ldr = self._panel(R, Y.shape[0], "R")
+            epi.R = Rp.data_ptr()
+            assert dot_out.dtype == torch.float64 and dot_out.is_cuda
+            epi.dot_out = dot_out.data_ptr()
+        return self._prod(transpose, X, alpha, beta, Y, precision, epi)
+
+    def sddmm(self, A, B, alpha=1.0, beta=0.0, D=None):
+        """D_ij = alpha A[rows_i] B[cols_j]^T + beta D_ij on the stored blocks,
+        packed order (the gradient of <A, H B> with respect to the values)."""
+        A, lda = self._panel(A, self.shape[0], "A")
+        B, ldb = self._panel(B, self.shape[1], "B")
+        if A.shape[1] != B.shape[1]:
+            raise ValueError("A and B have different column counts")
+        if D is None:
+            D = torch.empty(self.nnz, dtype=self.dtype, device=self.device)
+            beta = 0.0
+        check(lib().vbcsr_sddmm(self._h, A.shape[1], float(alpha), ctypes.c_void_p(A.data_ptr()), lda,
+                                ctypes.c_void_p(B.data_ptr()), ldb, float(beta), ctypes.c_void_p(D.data_ptr()),
+                                _stream(self.device)), "vbcsr_sddmm")
+        return D
+
+    def chebyshev(self, R, n_moments: int, ckpt_every: int = 0, precision="native"):
+        """Moments mu_n = <R, T_n(H) R> / (N k) of an operator already scaled to
+        [-1, 1]; returns (moments, checkpoints or None)."""
+        R, ldr = self._panel(R, self.shape[0], "R")
+        k = R.shape[1]
+        N = self.shape[0]
+        mom = torch.empty(n_moments, dtype=torch.float64, device=self.device)
+        work = torch.empty(2 * N * k, dtype=torch.float64, device=self.device)
+        ck = None
+        if ckpt_every:
+            npairs = max(0, -(-(n_moments - 1) // ckpt_every))
+            ck = torch.empty((npairs, 2, N, k), dtype=torch.float64, device=self.device)
+        check(lib().vbcsr_chebyshev(self._h, k, ctypes.c_void_p(R.data_ptr()), ldr, n_moments,
+                                    ctypes.c_void_p(mom.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                    ctypes.c_void_p(ck.data_ptr() if ck is not None else None),
+                                    ckpt_every, _prec(precision), _stream(self.device)), "vbcsr_chebyshev")
+        return mom, ck
+
+    def __matmul__(self, X):
+        return self.spmm(X)

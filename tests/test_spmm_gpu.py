@@ -1,0 +1,224 @@
+"""GPU parity of the FP64 / FP32 forward product, adjoint and pattern-sampled
+product against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+from synthetic.structures import BlockPattern
+from _parity import (TOL_F64, TOL_MIXED, adjoint_ref, check_elementwise, forward_ref, rel_fro,
+                     sddmm_ref)
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(pat, vals, dtype=torch.float64):
+    from paper_2609_04397_gb300 import VBCSR
+    return VBCSR.from_pattern(pat, vals, dtype, "cuda:0")
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dtype)
+
+
+def _run_forward(H, pat, vals, k, alpha, beta, ld_extra=0, seed=0, precision="native", tol=TOL_F64):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((pat.n_cols, k + ld_extra))
+    Y0 = rng.standard_normal((pat.n_rows, k + ld_extra))
+    Xd = _dev(X, H.dtype)[:, :k]
+    Yd = _dev(Y0, H.dtype)
+    H.spmm(Xd, alpha, beta, Yd[:, :k], precision=precision)
+    got = Yd.cpu().numpy()
+    Xc = X[:, :k].astype(np.float32).astype(np.float64) if H.dtype == torch.float32 else X[:, :k]
+    Y0c = Y0[:, :k].astype(np.float32).astype(np.float64) if H.dtype == torch.float32 else Y0[:, :k]
+    ref, scale = forward_ref(pat, vals, Xc, alpha, beta, Y0c)
+    assert rel_fro(got[:, :k], ref) <= tol
+    check_elementwise(got[:, :k], ref, scale, tol)
+    # columns beyond k (inside the leading dimension) are untouched
+    if ld_extra:
+        assert np.array_equal(got[:, k:], Y0[:, k:].astype(got.dtype))
+
+
+def test_tiny_multispecies_forward():
+    """200 atoms, b in {4, 9}, X 1300 x 8 N(0,1), seed 0."""
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    X = syn.normal_panel(w.pattern.n_cols, 8, 0)
+    Y = H.spmm(_dev(X)).cpu().numpy()
+    ref, scale = forward_ref(w.pattern, w.values, X, 1.0, 0.0, None)
+    assert rel_fro(Y, ref) <= TOL_F64
+    check_elementwise(Y, ref, scale, TOL_F64)
+    for alpha, beta in ((2.0, -1.0), (-1.0, 1.0), (0.0, 1.0), (1.0, 0.0)):
+        _run_forward(H, w.pattern, w.values, 8, alpha, beta)
+    H.check()
+
+
+SIZES = [(1, 2, 3), (4, 9, 13), (1, 5, 16), (17, 3, 20), (7, 8, 9, 10, 11, 12)]
+
+
+@pytest.mark.parametrize("sizes", SIZES)
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 8, 16, 32, 33])
+def test_random_patterns_forward_adjoint(sizes, k):
+    seed = hash((sizes, k)) % 1000
+    pat = syn.random_pattern(37, 29, sizes, 0.15, seed, empty_rows=3, unsorted=True)
+    vals = syn.random_values(pat, seed)
+    H = _handle(pat, vals)
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0), (2.0, -1.0), (0.0, -1.0), (0.5, 0.25)):
+        _run_forward(H, pat, vals, k, alpha, beta, ld_extra=(k % 3), seed=seed)
+        rng = np.random.default_rng(seed + 1)
+        X = rng.standard_normal((pat.n_rows, k))
+        Y0 = rng.standard_normal((pat.n_cols, k))
+        Yd = _dev(Y0)
+        H.spmm_adjoint(_dev(X), alpha, beta, Yd)
+        ref, scale = adjoint_ref(pat, vals, X, alpha, beta, Y0)
+        got = Yd.cpu().numpy()
+        assert rel_fro(got, ref) <= TOL_F64
+        check_elementwise(got, ref, scale, TOL_F64)
+    H.check()
+
+
+@pytest.mark.parametrize("k", [1, 5, 8, 40])
+def test_sddmm_random(k):
+    pat = syn.random_pattern(31, 23, (1, 4, 9, 13, 17), 0.2, 5 + k, empty_rows=2, unsorted=True)
+    H = _handle(pat, syn.random_values(pat, 5))
+    rng = np.random.default_rng(k)
+    A = rng.standard_normal((pat.n_rows, k))
+    B = rng.standard_normal((pat.n_cols, k))
+    D0 = rng.standard_normal(pat.nnz)
+    for alpha, beta in ((1.0, 0.0), (2.0, -1.0), (0.0, 0.5)):
+        Dd = _dev(D0)
+        H.sddmm(_dev(A), _dev(B), alpha, beta, Dd)
+        ref, scale = sddmm_ref(pat, A, B, alpha, beta, D0)
+        got = Dd.cpu().numpy()
+        assert rel_fro(got, ref) <= TOL_F64
+        check_elementwise(got, ref, scale, TOL_F64)
+
+
+def test_wide_rows_and_tall_blocks():
+    """Block sizes above 16 (row chunking) and panels wider than the staged
+    shared-memory window (K > 512) in both directions."""
+    pat = syn.random_pattern(9, 11, (33, 60, 150), 0.6, 3)
+    vals = syn.random_values(pat, 3)
+    H = _handle(pat, vals)
+    for k in (1, 8, 33):
+        _run_forward(H, pat, vals, k, 1.0, 0.5, seed=k)
+        X = np.random.default_rng(k).standard_normal((pat.n_rows, k))
+        got = H.spmm_adjoint(_dev(X)).cpu().numpy()
+        ref, scale = adjoint_ref(pat, vals, X, 1.0, 0.0, None)
+        check_elementwise(got, ref, scale, TOL_F64)
+
+
+def test_beta_zero_and_alpha_zero_do_not_read():
+    pat = syn.random_pattern(20, 20, (3, 9), 0.3, 4)
+    vals = syn.random_values(pat, 4)
+    H = _handle(pat, vals)
+    X = _dev(np.random.default_rng(0).standard_normal((pat.n_cols, 4)))
+    Y = torch.full((pat.n_rows, 4), float("nan"), dtype=torch.float64, device="cuda:0")
+    H.spmm(X, 1.0, 0.0, Y)
+    assert torch.isfinite(Y).all()
+    Xn = torch.full_like(X, float("nan"))
+    Y2 = torch.ones((pat.n_rows, 4), dtype=torch.float64, device="cuda:0")
+    H.spmm(Xn, 0.0, 3.0, Y2)
+    assert torch.equal(Y2, torch.full_like(Y2, 3.0))
+
+
+def test_degenerate_sizes():
+    from paper_2609_04397_gb300 import VBCSR
+    # no blocks at all
+    pat = BlockPattern(np.array([2, 3]), np.array([4]), np.array([0, 0, 0]), np.zeros(0))
+    H = VBCSR.from_pattern(pat, np.zeros(0), torch.float64, "cuda:0")
+    Y = torch.full((5, 3), 7.0, dtype=torch.float64, device="cuda:0")
+    H.spmm(torch.ones((4, 3), dtype=torch.float64, device="cuda:0"), 1.0, 0.5, Y)
+    assert torch.equal(Y, torch.full_like(Y, 3.5))
+    # k = 0 launches nothing
+    H.spmm(torch.ones((4, 0), dtype=torch.float64, device="cuda:0"), 1.0, 0.0,
+           torch.ones((5, 0), dtype=torch.float64, device="cuda:0"))
+    # zero block rows
+    pat0 = BlockPattern(np.zeros(0), np.array([2]), np.array([0]), np.zeros(0))
+    H0 = VBCSR.from_pattern(pat0, np.zeros(0), torch.float64, "cuda:0")
+    assert H0.shape == (0, 2)
+    H.check()
+
+
+def test_alias_rejected():
+    from paper_2609_04397_gb300 import VBCSRError
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    X = torch.ones((1300, 4), dtype=torch.float64, device="cuda:0")
+    with pytest.raises(VBCSRError) as ei:
+        H.spmm(X, 1.0, 0.0, X)
+    assert ei.value.status == -7
+
+
+def test_values_roundtrip_and_update():
+    pat = syn.random_pattern(25, 25, (4, 9, 13), 0.2, 6, unsorted=True)
+    vals = syn.random_values(pat, 6)
+    H = _handle(pat, vals)
+    assert np.array_equal(H.get_values().cpu().numpy(), vals)
+    v2 = syn.random_values(pat, 7)
+    H.set_values(_dev(v2))
+    assert np.array_equal(H.get_values().cpu().numpy(), v2)
+    H.set_values(v2 * 2.0)       # host path
+    assert np.array_equal(H.get_values().cpu().numpy(), v2 * 2.0)
+    _run_forward(H, pat, v2 * 2.0, 5, 1.0, 0.0)
+
+
+def test_shape_class_registry():
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    cls = H.shape_classes()
+    pat = w.pattern
+    rows = pat.block_rows()
+    expect = {}
+    for bi, bj in zip(pat.row_bsize[rows], pat.col_bsize[pat.block_col_idx]):
+        expect[(int(bi), int(bj))] = expect.get((int(bi), int(bj)), 0) + 1
+    assert {(a, b): c for a, b, c in cls} == expect
+    assert len(cls) == 4
+
+
+def test_fp32_operator():
+    pat = syn.random_pattern(40, 40, (4, 9, 13), 0.15, 8)
+    vals = syn.random_values(pat, 8)
+    v32 = vals.astype(np.float32)
+    H = _handle(pat, v32, torch.float32)
+    _run_forward(H, pat, v32.astype(np.float64), 8, 1.0, 0.0, tol=TOL_MIXED)
+    _run_forward(H, pat, v32.astype(np.float64), 3, 2.0, -1.0, tol=TOL_MIXED)
+
+
+def test_f32_mode_on_fp64_operator():
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    _run_forward(H, w.pattern, w.values, 8, 1.0, 0.0, precision="f32", tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("kc,warps", [(1, 1), (4, 2), (8, 8), (32, 4), (16, 1)])
+def test_tuning_variants_agree(kc, warps):
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    H.set_tuning(kc, warps)
+    _run_forward(H, w.pattern, w.values, 11, 1.0, 0.0)
+
+
+def test_zincblende_full_size_sampled_rows():
+    """~50k-atom zinc-blende cluster (549,607 rows, 1.67e8 entries) at k = 1, 8
+    and 32: every output of 64 sampled block rows against the oracle."""
+    w = syn.zincblende(50_000)
+    pat = w.pattern
+    H = _handle(pat, w.values)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(pat.n_brows, 64, replace=False))
+    roff = np.concatenate([[0], np.cumsum(pat.row_bsize.astype(np.int64))])
+    for k in (1, 8, 32):
+        X = syn.normal_panel(pat.n_cols, k, 0)
+        Y = H.spmm(_dev(X)).cpu().numpy()
+        ref = np.zeros_like(Y)
+        scale = np.zeros_like(Y)
+        absv, absx = np.abs(w.values), np.abs(X)
+        for i in rows:
+            ref = oracle.spmm(pat, w.values, X, row_range=(i, i + 1), Y=ref, beta=1.0)
+            scale = oracle.spmm(pat, absv, absx, row_range=(i, i + 1), Y=scale, beta=1.0)
+        sel = np.concatenate([np.arange(roff[i], roff[i + 1]) for i in rows])
+        check_elementwise(Y[sel], ref[sel], scale[sel], TOL_F64)
+        assert rel_fro(Y[sel], ref[sel]) <= TOL_F64
+    H.check()
