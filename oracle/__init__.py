@@ -172,20 +172,24 @@ def gershgorin_bounds(pat, values):
     r = np.concatenate([[0], np.cumsum(rb)])
     c = np.concatenate([[0], np.cumsum(cb)])
     N = int(r[-1])
-    absrow = np.zeros(N)
+    rows = np.repeat(np.arange(len(rb)), np.diff(pat.block_row_ptr))
+    cols = np.asarray(pat.block_col_idx, np.int64)
+    off = np.concatenate([[0], np.cumsum(rb[rows] * cb[cols])])
+    values = np.asarray(values, np.float64)
+    # absolute row sums: every stored entry adds |h| to its scalar row
+    ent_block = np.repeat(np.arange(len(rows)), rb[rows] * cb[cols])
+    local = np.arange(off[-1]) - off[ent_block]
+    ent_row = r[rows[ent_block]] + local // cb[cols[ent_block]]
+    absrow = np.bincount(ent_row, weights=np.abs(values), minlength=N)
+    # diagonal entries: only blocks whose scalar row and column ranges overlap
     diag = np.zeros(N)
-    off = 0
-    for i in range(len(rb)):
-        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
-            j = int(pat.block_col_idx[b])
-            blk = np.asarray(values[off:off + rb[i] * cb[j]]).reshape(rb[i], cb[j])
-            off += rb[i] * cb[j]
-            absrow[r[i]:r[i + 1]] += np.abs(blk).sum(axis=1)
-            for p in range(rb[i]):
-                col = c[j] + np.arange(cb[j])
-                hit = np.nonzero(col == r[i] + p)[0]
-                if len(hit):
-                    diag[r[i] + p] += blk[p, hit[0]]
+    for b in np.nonzero((r[rows] < c[cols] + cb[cols]) & (c[cols] < r[rows] + rb[rows]))[0]:
+        i, j = rows[b], cols[b]
+        blk = values[off[b]:off[b + 1]].reshape(rb[i], cb[j])
+        for p in range(rb[i]):
+            q = r[i] + p - c[j]
+            if 0 <= q < cb[j]:
+                diag[r[i] + p] += blk[p, q]
     radius = absrow - np.abs(diag)
     return float((diag - radius).min()), float((diag + radius).max())
 
@@ -203,16 +207,16 @@ def shift_scale_values(pat, values, c, d) -> np.ndarray:
     cb = np.asarray(pat.col_bsize, np.int64)
     r = np.concatenate([[0], np.cumsum(rb)])
     cc = np.concatenate([[0], np.cumsum(cb)])
+    rows = np.repeat(np.arange(len(rb)), np.diff(pat.block_row_ptr))
+    cols = np.asarray(pat.block_col_idx, np.int64)
+    off = np.concatenate([[0], np.cumsum(rb[rows] * cb[cols])])
     out = np.array(values, dtype=np.float64, copy=True)
-    off = 0
-    for i in range(len(rb)):
-        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
-            j = int(pat.block_col_idx[b])
-            for p in range(rb[i]):
-                for q in range(cb[j]):
-                    if r[i] + p == cc[j] + q:
-                        out[off + p * cb[j] + q] -= c
-            off += rb[i] * cb[j]
+    for b in np.nonzero((r[rows] < cc[cols] + cb[cols]) & (cc[cols] < r[rows] + rb[rows]))[0]:
+        i, j = rows[b], cols[b]
+        for p in range(rb[i]):
+            q = r[i] + p - cc[j]
+            if 0 <= q < cb[j]:
+                out[off[b] + p * cb[j] + q] -= c
     return out / d
 
 

@@ -10,3 +10,4 @@ from ._lib import VBCSRError, lib  # noqa: F401
 from .matrix import VBCSR  # noqa: F401
 
 __all__ = ["VBCSR", "VBCSRError", "lib"]
+from .autograd import chebyshev_moments, diagonal_mask, shift_scale, vbcsr_matmul  # noqa: F401,E402

@@ -596,8 +596,11 @@ static int cached_cap(const void *kernel, int warps, size_t smem) {
     return c;
 }
 
+// dot_scale multiplies the fused dot product before it is stored (1 for the
+// public epilogue, 1 / (N k) for the Chebyshev moments).
 static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const void *X, int64_t ldx, double beta,
-                       void *Y, int64_t ldy, const vbcsr_epilogue_t *epi, int precision, cudaStream_t s) {
+                       void *Y, int64_t ldy, const vbcsr_epilogue_t *epi, int precision, cudaStream_t s,
+                       double dot_scale = 1.0) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
     if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_BF16X2)
@@ -685,7 +688,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             e = launch_mma(mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
     }
-    if (want_dot) CUDA_TRY(launch_finalize_dot(A->partials, used, 1.0, epi->dot_out, s), "dot finalize");
+    if (want_dot) CUDA_TRY(launch_finalize_dot(A->partials, used, dot_scale, epi->dot_out, s), "dot finalize");
     return VBCSR_OK;
 }
 
@@ -764,7 +767,7 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     epi.ldr = ldr;
     // t_1 = H~ R  -> buf[1];  t_0 (a copy of R) -> buf[0]
     epi.dot_out = moments + 1;
-    int rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s);
+    int rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale);
     if (rc) return rc;
     auto store_pair = [&](int64_t m, const double *tm, int64_t ldm, const double *tm1) -> int {
         if (!ckpt || m % ckpt_every) return VBCSR_OK;
@@ -780,7 +783,7 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     for (int64_t n = 1; n + 1 < n_moments; ++n) {
         double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
         epi.dot_out = moments + n + 1;
-        rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s);
+        rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale);
         if (rc) return rc;
         if ((rc = store_pair(n, tn, k, tprev))) return rc;
     }

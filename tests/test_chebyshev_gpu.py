@@ -1,0 +1,165 @@
+"""GPU parity of the Chebyshev recurrence (kernel polynomial method, Sec. V),
+its checkpoints, its mixed-precision form and its reverse-mode gradient."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(w):
+    from paper_2609_04397_gb300 import VBCSR
+    c, d = oracle.cheb_scale(w.pattern, w.values)
+    vt = oracle.shift_scale_values(w.pattern, w.values, c, d)
+    H = VBCSR.from_pattern(w.pattern, vt, torch.float64, "cuda:0")
+    return H, vt, c, d
+
+
+def test_moments_and_checkpoints_tiny():
+    w = syn.tiny_multispecies(0)
+    H, vt, c, d = _setup(w)
+    R = syn.rademacher_panel(w.pattern.n_rows, 16, 0)
+    M, E = 30, 10
+    mom, ck = H.chebyshev(torch.from_numpy(R).cuda(), M, ckpt_every=E)
+    ref = oracle.chebyshev_moments(w.pattern, vt, R, M)
+    assert np.abs(mom.cpu().numpy() - ref).max() <= 1e-12
+    t = oracle.chebyshev_vectors(w.pattern, vt, R, M)
+    ck = ck.cpu().numpy()
+    assert ck.shape[0] == 3
+    for s in range(ck.shape[0]):
+        for j in range(2):
+            ref_t = t[s * E + j]
+            assert np.linalg.norm(ck[s, j] - ref_t) <= 1e-12 * np.linalg.norm(ref_t)
+
+
+@pytest.mark.parametrize("mode", ["f32", "tf32x3", "bf16x2"])
+def test_mixed_precision_moments(mode):
+    """Block products in reduced precision, recurrence and moments in FP64:
+    every moment within 1e-5 of the FP64 oracle (relative to mu_0 = 1)."""
+    w = syn.tiny_multispecies(0)
+    H, vt, c, d = _setup(w)
+    R = syn.rademacher_panel(w.pattern.n_rows, 16, 0)
+    mom, _ = H.chebyshev(torch.from_numpy(R).cuda(), 51, precision=mode)
+    ref = oracle.chebyshev_moments(w.pattern, vt, R, 51)
+    err = np.abs(mom.cpu().numpy() - ref) / abs(ref[0])
+    assert err.max() <= 1e-5, err.max()
+
+
+def _grad_case(n_atoms, k, M, E, seed=0):
+    side = 60.0 * (n_atoms / 20000) ** (1 / 3)
+    w = syn.amorphous(n=n_atoms, side=side, seed=seed)
+    H, vt, c, d = _setup(w)
+    R = syn.rademacher_panel(w.pattern.n_rows, k, seed)
+    return w, H, vt, c, d, R
+
+
+@pytest.mark.parametrize("E", [1, 4, 10, 40])
+def test_moment_loss_gradient_matches_oracle(E):
+    from paper_2609_04397_gb300 import chebyshev_moments
+    w, H, vt, c, d, R = _grad_case(600, 4, 30, E)
+    v = torch.from_numpy(vt).cuda().requires_grad_(True)
+    mu = chebyshev_moments(H, v, torch.from_numpy(R).cuda(), 30, ckpt_every=E)
+    loss = (mu ** 2).sum()
+    loss.backward()
+    ref = oracle.moment_loss_grad(w.pattern, vt, R, 30)
+    g = v.grad.cpu().numpy()
+    assert np.linalg.norm(g - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert np.abs(g - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_gradient_through_shift_scale_and_fd():
+    """dL/dH (original values) = dL/dH~ / d, checked against central finite
+    differences (h = 1e-6) of the oracle's loss on 50 sampled entries."""
+    from paper_2609_04397_gb300 import chebyshev_moments, diagonal_mask, shift_scale
+    w, H, vt, c, d, R = _grad_case(300, 4, 30, 10)
+    mask = diagonal_mask(H)
+    v = torch.from_numpy(w.values).cuda().requires_grad_(True)
+    mu = chebyshev_moments(H, shift_scale(v, mask, c, d), torch.from_numpy(R).cuda(), 30, ckpt_every=10)
+    (mu ** 2).sum().backward()
+    g = v.grad.cpu().numpy()
+
+    def loss(vals):
+        return oracle.moment_loss(w.pattern, oracle.shift_scale_values(w.pattern, vals, c, d), R, 30)
+
+    h = 1e-6
+    idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
+    fd = []
+    for i in idx:
+        vp, vm = w.values.copy(), w.values.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd.append((loss(vp) - loss(vm)) / (2 * h))
+    fd = np.array(fd)
+    # max-norm relative deviation over the sampled entries
+    assert np.abs(fd - g[idx]).max() <= 1e-6 * np.abs(g[idx]).max()
+
+
+def test_f32_products_gradient_close_to_fp64():
+    from paper_2609_04397_gb300 import chebyshev_moments
+    w, H, vt, c, d, R = _grad_case(600, 4, 30, 10)
+    Rd = torch.from_numpy(R).cuda()
+    grads = {}
+    for mode in ("native", "f32"):
+        v = torch.from_numpy(vt).cuda().requires_grad_(True)
+        (chebyshev_moments(H, v, Rd, 30, 10, precision=mode) ** 2).sum().backward()
+        grads[mode] = v.grad.cpu().numpy()
+    rel = np.linalg.norm(grads["f32"] - grads["native"]) / np.linalg.norm(grads["native"])
+    assert rel <= 1e-4, rel
+
+
+def test_matmul_autograd():
+    from paper_2609_04397_gb300 import VBCSR, vbcsr_matmul
+    pat = syn.random_pattern(30, 25, (4, 9, 13), 0.2, 2)
+    vals = syn.random_values(pat, 2)
+    H = VBCSR.from_pattern(pat, vals, torch.float64, "cuda:0")
+    X = np.random.default_rng(1).standard_normal((pat.n_cols, 6))
+    G = np.random.default_rng(2).standard_normal((pat.n_rows, 6))
+    v = torch.from_numpy(vals).cuda().requires_grad_(True)
+    Xd = torch.from_numpy(X).cuda().requires_grad_(True)
+    Y = vbcsr_matmul(H, v, Xd)
+    (Y * torch.from_numpy(G).cuda()).sum().backward()
+    ref_dx = oracle.spmm_adjoint(pat, vals, G)
+    ref_dv = oracle.sddmm(pat, G, X)
+    assert np.linalg.norm(Xd.grad.cpu().numpy() - ref_dx) <= 1e-12 * np.linalg.norm(ref_dx)
+    assert np.linalg.norm(v.grad.cpu().numpy() - ref_dv) <= 1e-12 * np.linalg.norm(ref_dv)
+
+
+@pytest.mark.skipif(os.environ.get("VBCSR_FULL_FD") != "1", reason="set VBCSR_FULL_FD=1 (minutes of CPU time)")
+def test_amorphous_20k_gradient_fd_50_entries():
+    """Full differentiation workload: 20k amorphous atoms, 30 moments, k = 16,
+    checkpoints every 10 steps; GPU gradient of L = sum mu_n^2 against central
+    differences (h = 1e-6) of the oracle on 50 sampled stored entries."""
+    from paper_2609_04397_gb300 import chebyshev_moments
+    w, H, vt, c, d, R = _grad_case(20000, 16, 30, 10)
+    v = torch.from_numpy(vt).cuda().requires_grad_(True)
+    (chebyshev_moments(H, v, torch.from_numpy(R).cuda(), 30, ckpt_every=10) ** 2).sum().backward()
+    g = v.grad.cpu().numpy()
+    nthreads = os.cpu_count() or 1
+    pat = w.pattern
+
+    def loss(vals):
+        t0 = R
+        t1 = oracle.spmm(pat, vals, t0, nthreads=nthreads)
+        mu = [np.sum(R * t0) / R.size, np.sum(R * t1) / R.size]
+        for n in range(1, 29):
+            t0, t1 = t1, oracle.spmm(pat, vals, t1, 2.0, -1.0, t0, nthreads=nthreads)
+            mu.append(np.sum(R * t1) / R.size)
+        return float(np.sum(np.square(mu)))
+
+    h = 1e-6
+    idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
+    fd = []
+    for i in idx:
+        vp, vm = vt.copy(), vt.copy()
+        vp[i] += h
+        vm[i] -= h
+        fd.append((loss(vp) - loss(vm)) / (2 * h))
+    fd = np.array(fd)
+    worst = np.abs(fd - g[idx]).max() / np.abs(g[idx]).max()
+    print(f"amorphous 20k: max-norm relative FD deviation over 50 entries = {worst:.3e}")
+    assert worst <= 1e-6

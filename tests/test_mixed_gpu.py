@@ -1,0 +1,98 @@
+"""GPU parity of the mixed-precision block products against the FP64 oracle.
+
+Per result (Frobenius) the split modes TF32X3 and BF16X2 and the FP32 mode
+must stay within 1e-5 of the FP64 oracle. Element by element the bound is
+1e-4 * (|H| |X|): a single product of a bf16 hi+lo pair can be off by about
+2^-16 of |h x| and FP32 accumulation over a ~300-term row adds up to
+~300 * 2^-24 in the worst case, so 1e-5 per element is not guaranteed.
+Single-pass TF32 (11-bit values) is expected to exceed 1e-5 and is only
+checked against its own 2^-10-scale bound.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from _parity import TOL_MIXED, adjoint_ref, check_elementwise, forward_ref, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["f32", "tf32x3", "bf16x2"]
+
+
+def _handle(pat, vals, dtype=torch.float64):
+    from paper_2609_04397_gb300 import VBCSR
+    return VBCSR.from_pattern(pat, vals, dtype, "cuda:0")
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0", dtype)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k", [1, 3, 8, 16, 33])
+def test_mixed_forward_tiny_multispecies(mode, k):
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    X = syn.normal_panel(w.pattern.n_cols, k, 0)
+    Y0 = syn.normal_panel(w.pattern.n_rows, k, 1)
+    for alpha, beta in ((1.0, 0.0), (2.0, -1.0)):
+        Yd = _dev(Y0)
+        H.spmm(_dev(X), alpha, beta, Yd, precision=mode)
+        ref, scale = forward_ref(w.pattern, w.values, X, alpha, beta, Y0)
+        got = Yd.cpu().numpy()
+        assert rel_fro(got, ref) <= TOL_MIXED, rel_fro(got, ref)
+        check_elementwise(got, ref, scale, 1e-4)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_adjoint_and_shapes(mode):
+    pat = syn.random_pattern(41, 37, (1, 4, 9, 13, 16, 20), 0.2, 12, empty_rows=2, unsorted=True)
+    vals = syn.random_values(pat, 12)
+    H = _handle(pat, vals)
+    for k in (1, 8, 17):
+        X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
+        got = H.spmm(_dev(X), precision=mode).cpu().numpy()
+        ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
+        assert rel_fro(got, ref) <= TOL_MIXED
+        check_elementwise(got, ref, scale, 1e-4)
+        Xa = np.random.default_rng(k + 1).standard_normal((pat.n_rows, k))
+        got = H.spmm_adjoint(_dev(Xa), precision=mode).cpu().numpy()
+        ref, scale = adjoint_ref(pat, vals, Xa, 1.0, 0.0, None)
+        assert rel_fro(got, ref) <= TOL_MIXED
+        check_elementwise(got, ref, scale, 1e-4)
+
+
+def test_single_tf32_within_its_own_bound():
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    X = syn.normal_panel(w.pattern.n_cols, 8, 0)
+    got = H.spmm(_dev(X), precision="tf32").cpu().numpy()
+    ref, scale = forward_ref(w.pattern, w.values, X, 1.0, 0.0, None)
+    check_elementwise(got, ref, scale, 2.0 ** -9)
+    assert rel_fro(got, ref) > 1e-6   # really ran in reduced precision
+
+
+@pytest.mark.parametrize("mode", ["native", "tf32x3", "bf16x2"])
+def test_fp32_operator_modes(mode):
+    pat = syn.random_pattern(30, 30, (4, 9, 13), 0.2, 9)
+    vals = syn.random_values(pat, 9).astype(np.float32)
+    H = _handle(pat, vals, torch.float32)
+    X = np.random.default_rng(2).standard_normal((pat.n_cols, 8)).astype(np.float32)
+    got = H.spmm(_dev(X, torch.float32), precision=mode).cpu().numpy().astype(np.float64)
+    ref, scale = forward_ref(pat, vals.astype(np.float64), X.astype(np.float64), 1.0, 0.0, None)
+    assert rel_fro(got, ref) <= TOL_MIXED
+    check_elementwise(got, ref, scale, 1e-4)
+
+
+def test_mixed_copy_follows_set_values():
+    pat = syn.random_pattern(20, 20, (4, 9), 0.3, 3)
+    v1 = syn.random_values(pat, 3)
+    H = _handle(pat, v1)
+    X = np.random.default_rng(0).standard_normal((pat.n_cols, 4))
+    H.spmm(_dev(X), precision="bf16x2")            # builds the FP32 copy
+    v2 = syn.random_values(pat, 4)
+    H.set_values(_dev(v2))
+    got = H.spmm(_dev(X), precision="bf16x2").cpu().numpy()
+    ref, _ = forward_ref(pat, v2, X, 1.0, 0.0, None)
+    assert rel_fro(got, ref) <= TOL_MIXED
