@@ -158,6 +158,76 @@ def cpu_baseline(pat, values, ks, budget_s=12.0):
                       f"{secs:.1f} s of CPU work per pass"}
 
 
+def batched_section(dev, steps):
+    """256 independent structures (50-2000 atoms, log-uniform; b in {4, 9, 13};
+    FP32; k = 8): 256 separate handles launched one after another, against one
+    batched handle (autotuned tiles and schedule), plain and replayed from a
+    captured CUDA graph. Same X / Y memory for all three."""
+    import torch
+    import synthetic as syn
+    from paper_2609_04397_gb300 import VBCSR
+    w = syn.batched_uneven(n_structs=256, n_min=50, n_max=2000, seed=0)
+    pat = w.pattern
+    vals = w.values.astype(np.float32)
+    offs = w.struct_brow_offsets
+    rows = pat.block_rows()
+    local = pat.block_col_idx.astype(np.int64) - offs[np.searchsorted(offs, rows, side="right") - 1]
+    k = 8
+    Hb = VBCSR.from_batched(offs, offs, pat.row_bsize, pat.col_bsize, pat.block_row_ptr, local, vals,
+                            torch.float32, dev)
+    voff = pat.value_offset()
+    coff = np.concatenate([[0], np.cumsum(pat.col_bsize.astype(np.int64))])
+    X = torch.randn(pat.n_cols, k, dtype=torch.float32, device=dev)
+    Y = torch.empty(pat.n_rows, k, dtype=torch.float32, device=dev)
+    parts = []
+    for s_, part in enumerate(w.parts):
+        b0, b1 = offs[s_], offs[s_ + 1]
+        Hs = VBCSR.from_pattern(part, vals[voff[pat.block_row_ptr[b0]]:voff[pat.block_row_ptr[b1]]],
+                                torch.float32, dev)
+        parts.append((Hs, X[coff[b0]:coff[b1]], Y[coff[b0]:coff[b1]]))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    def separate():
+        for Hs, Xs, Ys in parts:
+            Hs.spmm(Xs, 1.0, 0.0, Ys)
+
+    reps = max(10, steps)
+    t_sep = timed(separate, reps)
+    Y_sep = Y.clone()
+    t_plain = timed(lambda: Hb.spmm(X, 1.0, 0.0, Y), reps)
+    tune = Hb.autotune(k)
+    t_tuned = timed(lambda: Hb.spmm(X, 1.0, 0.0, Y), reps)
+    same = bool(torch.allclose(Y, Y_sep, rtol=1e-5, atol=1e-5))
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        Hb.spmm(X, 1.0, 0.0, Y)
+    stream.wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        Hb.spmm(X, 1.0, 0.0, Y)
+    t_graph = timed(g.replay, reps)
+    flops = 2.0 * pat.nnz * k
+    return {"workload": f"batched_{len(w.parts)}_structures_{pat.n_brows}_atoms", "dtype": "f32", "k": k,
+            "nnz": pat.nnz, "ms_256_separate": t_sep, "ms_one_handle_default": t_plain,
+            "ms_one_handle_autotuned": t_tuned, "ms_graph_replay": t_graph,
+            "schedule": tune["schedule"], "speedup_vs_separate": t_sep / min(t_tuned, t_graph),
+            "gflops_graph": flops / (t_graph / 1e3) / 1e9, "matches_separate": same}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
     world, rank, _ = _dist()
@@ -320,6 +390,7 @@ def run_ours(args):
            "h2d_bytes_per_step": int(sum(8 * pat.n_cols * k for k in KS)),
            "d2h_bytes_per_step": int(sum(8 * pat.n_rows * k for k in KS)), "ms_per_step": e2e_ms}
 
+    batched = batched_section(dev, args.steps) if not args.no_batched else None
     H.check()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -328,7 +399,7 @@ def run_ours(args):
                        "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk, "ks": list(KS),
                        "alpha": 1.0, "beta": 0.0, "parallelism": f"replicas x{world}",
                        "l2": "no flush: inputs larger than L2 (1.33 GB of values per product)"},
-            "roofline": roofline, "per_k": per_k, "mixed": mixed, "e2e": e2e,
+            "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
             "gpu_launches": n_buckets * len(KS) * args.steps, "clocks": clocks}
     if rank == 0:
         if not args.no_cpu_baseline:
@@ -347,6 +418,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -73,6 +73,16 @@ typedef enum {
     VBCSR_PREC_BF16X2 = 4
 } vbcsr_precision;
 
+/* Launch schedules of the CUDA-core products (vbcsr_set_schedule). */
+typedef enum {
+    VBCSR_SCHED_BUCKETED = 0,     /* one launch per work-item row count (default)      */
+    VBCSR_SCHED_PERSISTENT = 1    /* one launch over all items, costliest first, warps
+                                     taking items from a device work counter           */
+} vbcsr_schedule;
+
+/* Flags of vbcsr_autotune. */
+#define VBCSR_TUNE_NO_PERSISTENT 1   /* keep the bucketed schedule */
+
 typedef struct {
     int64_t n_brows, n_bcols;     /* block rows / block columns                      */
     int64_t n_rows, n_cols;       /* scalar rows / columns                           */
@@ -259,11 +269,37 @@ int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out);
 int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, int64_t *count, int32_t cap);
 
 /*
- * Tuning of the forward kernel: KC output columns per warp pass (1, 2, 4, 8,
- * 16 or 32; 0 = automatic from k) and warps per CTA (1, 2, 4 or 8; 0 =
- * automatic). Applies to later calls on this handle.
+ * Tuning of the CUDA-core products. Work items are bucketed by their row
+ * count B (1..16); each bucket has a column tile kc (output columns per warp
+ * pass: 1, 2, 4, 8, 16 or 32; 0 = the smallest power of two >= k, capped at
+ * 32) and a CTA width (warps per CTA: 1, 2, 4 or 8; 0 = 4). A tile larger than
+ * k's automatic choice is clamped to it.
+ *  vbcsr_set_tuning         the same kc and warps for every bucket
+ *  vbcsr_set_bucket_tuning  one bucket (B = 0: every bucket)
+ *  vbcsr_set_schedule       VBCSR_SCHED_BUCKETED or VBCSR_SCHED_PERSISTENT and the
+ *                           CTA width of the persistent launch (0 = 4)
+ *  vbcsr_get_tuning         reads them back: kc_by_b[17], warps_by_b[17] (index = B;
+ *                           any pointer may be NULL)
+ * They apply to later calls on this handle. The tensor-core modes ignore them.
  */
 int vbcsr_set_tuning(vbcsr_t *A, int32_t kc, int32_t warps_per_cta);
+int vbcsr_set_bucket_tuning(vbcsr_t *A, int32_t B, int32_t kc, int32_t warps_per_cta);
+int vbcsr_set_schedule(vbcsr_t *A, int32_t schedule, int32_t persist_warps);
+int vbcsr_get_tuning(const vbcsr_t *A, int32_t *kc_by_b, int32_t *warps_by_b, int32_t *schedule,
+                     int32_t *persist_warps);
+
+/*
+ * Autotuner: times the product (transpose = 0 forward, 1 adjoint) at width k
+ * for every bucket's candidate (kc, warps) pairs, keeps the fastest per
+ * bucket, then times the persistent schedule at each CTA width and keeps
+ * whichever schedule is faster (unless flags has VBCSR_TUNE_NO_PERSISTENT).
+ * X and Y are device panels of the product's shapes; Y is overwritten. The
+ * call synchronises `stream` repeatedly (a set-up step: do not capture it in
+ * a CUDA graph). Tensor-core precisions return at once (nothing to tune).
+ * (The per-shape-group tuning of tiles has no counterpart in the paper.)
+ */
+int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                   int precision, int32_t flags, void *stream);
 
 /* Synchronises `stream`, then reads and clears the handle's device error
    word: VBCSR_OK, or VBCSR_ERR_DEVICE_CHECK with the recorded code in the

@@ -46,6 +46,10 @@ SIGNATURES = {
     "vbcsr_get_info": ([_p, ctypes.POINTER(Info)], _int),
     "vbcsr_shape_classes": ([_p, _p, _p, _p, _i32], _int),
     "vbcsr_set_tuning": ([_p, _i32, _i32], _int),
+    "vbcsr_set_bucket_tuning": ([_p, _i32, _i32, _i32], _int),
+    "vbcsr_set_schedule": ([_p, _i32, _i32], _int),
+    "vbcsr_get_tuning": ([_p, _p, _p, _p, _p], _int),
+    "vbcsr_autotune": ([_p, _int, _i64, _p, _i64, _p, _i64, _int, _i32, _p], _int),
     "vbcsr_check": ([_p, _p], _int),
 }
 

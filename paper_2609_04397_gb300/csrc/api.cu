@@ -84,7 +84,10 @@ struct vbcsr_matrix {
     size_t esize = 8;
     int64_t n_brows = 0, n_bcols = 0, n_rows = 0, n_cols = 0, nblk = 0, nnz = 0, panel_elems = 0;
     int32_t n_structs = 1;
-    int kc = 0, warps = 0;
+    int kc_b[kMaxB + 1] = {0};      // column tile per row count (0: from k)
+    int warps_b[kMaxB + 1] = {0};   // warps per CTA per row count (0: 4)
+    int schedule = 0;               // 0: one launch per row count, 1: one persistent launch
+    int persist_warps = 0;          // warps per CTA of the persistent launch (0: 4)
     int debug_checks = 0;
 
     // host copies
@@ -101,7 +104,10 @@ struct vbcsr_matrix {
     void *panel = nullptr;        // values in panels (dtype)
     float *panel32 = nullptr;     // FP32 copy for the mixed modes (FP64 operators), lazily built
     bool panel32_valid = false;
-    WorkItem *fwd_items = nullptr, *adj_items = nullptr;
+    WorkItem *fwd_items = nullptr, *adj_items = nullptr;   // bucketed by row count
+    WorkItem *fwd_lpt = nullptr, *adj_lpt = nullptr;       // all items, descending cost
+    int64_t n_fwd_items = 0, n_adj_items = 0;
+    long long *queue = nullptr;                            // work counter of the persistent launch
     int32_t *fl_xrow = nullptr, *fl_pcol = nullptr, *fl_w = nullptr, *fl_kp = nullptr, *fl_bi = nullptr;
     int64_t *fl_uoff = nullptr, *fl_pbase = nullptr;
     int64_t *tl_pbase = nullptr;
@@ -196,6 +202,14 @@ static int validate_pattern(int64_t n_brows, int64_t n_bcols, const int32_t *row
 }
 
 static int ceil_to(int64_t v, int m) { return (int)((v + m - 1) / m * m); }
+
+// Longest-processing-time order for the persistent launch: the costliest
+// items (rows x virtual columns) first, so that the queue ends with small ones.
+static void sort_by_cost(std::vector<WorkItem> &items) {
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem &x, const WorkItem &y) {
+        return (int64_t)x.B * (x.K + 8) > (int64_t)y.B * (y.K + 8);
+    });
+}
 
 static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
                  const int32_t *col_bsize, const int64_t *block_row_ptr, const int32_t *block_col_idx,
@@ -304,6 +318,9 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
             items.insert(items.end(), bk[b].begin(), bk[b].end());
         }
         CUDA_TRY(upload(A, &A->fwd_items, items, s), "upload forward items");
+        A->n_fwd_items = (int64_t)items.size();
+        sort_by_cost(items);
+        CUDA_TRY(upload(A, &A->fwd_lpt, items, s), "upload forward items");
     }
 
     // transposed list and adjoint work items
@@ -359,6 +376,9 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
             items.insert(items.end(), bk[b].begin(), bk[b].end());
         }
         CUDA_TRY(upload(A, &A->adj_items, items, s), "upload adjoint items");
+        A->n_adj_items = (int64_t)items.size();
+        sort_by_cost(items);
+        CUDA_TRY(upload(A, &A->adj_lpt, items, s), "upload adjoint items");
         CUDA_TRY(upload(A, &A->tl_pbase, tl_pbase, s), "upload");
         CUDA_TRY(upload(A, &A->tl_kp, tl_kp, s), "upload");
         CUDA_TRY(upload(A, &A->tl_bi, tl_bi, s), "upload");
@@ -378,6 +398,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     CUDA_TRY(upload(A, &A->d_row_b, A->row_b, s), "upload");
     CUDA_TRY(A->alloc(&A->partials, kPartialsCap), "alloc partials");
     CUDA_TRY(A->alloc(&A->err, 1), "alloc error word");
+    CUDA_TRY(A->alloc(&A->queue, 1), "alloc work counter");
     CUDA_TRY(cudaMemsetAsync(A->err, 0, sizeof(int), s), "memset");
 
     // value pages
@@ -555,9 +576,9 @@ extern "C" int vbcsr_get_values(const vbcsr_t *Ac, void *values, int on_device, 
 // products
 
 namespace vbcsr {
-const void *fma_f64_kernel(bool trans);
-const void *fma_f32_kernel(bool trans);
-const void *fma_f32_on_f64_kernel(bool trans);
+const void *fma_f64_kernel(bool trans, bool persistent);
+const void *fma_f32_kernel(bool trans, bool persistent);
+const void *fma_f32_on_f64_kernel(bool trans, bool persistent);
 const void *mma_kernel_ptr(int mode, bool xdouble, bool trans);
 }  // namespace vbcsr
 
@@ -635,7 +656,6 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.fl = {A->fl_xrow, A->fl_pcol, A->fl_w};
     a.tl = {A->tl_pbase, A->tl_kp, A->tl_bi, A->tl_xrow, A->tl_vcol};
     a.k = k;
-    a.kc = A->kc ? A->kc : auto_kc(k);
     a.alpha = alpha;
     a.beta = beta;
     a.gamma = gamma;
@@ -650,30 +670,20 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.x_rows = xrows;
     a.err = A->err;
     a.debug_checks = A->debug_checks;
-    a.warps = A->warps ? A->warps : 4;
+    const int kc_auto = auto_kc(k);
+    auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
-    const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
-    const WorkItem *items = trans ? A->adj_items : A->fwd_items;
-    const void *kern = nullptr;
-    size_t smem = 0;
-    if (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32) {
-        kern = (mode == VBCSR_PREC_NATIVE) ? (f64 ? fma_f64_kernel(trans) : fma_f32_kernel(trans))
-                                           : fma_f32_on_f64_kernel(trans);
-        smem = fma_smem_bytes(trans, a.warps);
-    } else {
-        kern = mma_kernel_ptr(mode, f64, trans);
-        if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
-        a.warps = 4;
-        smem = mma_smem_bytes(trans, a.warps);
-    }
-    const int cap = cached_cap(kern, a.warps, smem);
-
+    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32);
     int64_t used = 0;
-    for (const Bucket &b : buckets) {
-        a.items = items + b.begin;
-        a.n_items = b.count;
-        const int64_t need = (b.count + a.warps - 1) / a.warps;
-        a.grid = (int)std::min<int64_t>(need, cap);
+    // one launch of `kern` over items[0..n) with `warps` warps per CTA
+    auto launch = [&](int B, const WorkItem *items, int64_t n, int warps, const void *kern, size_t smem) -> int {
+        a.items = items;
+        a.n_items = n;
+        a.warps = warps;
+        const int cap = cached_cap(kern, warps, smem);
+        const int64_t need = (n + warps - 1) / warps;
+        a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
+        a.partials = nullptr;
         if (want_dot) {
             if (used + a.grid > kPartialsCap) return fail(VBCSR_ERR_UNSUPPORTED, "too many CTAs for the dot");
             a.partials = A->partials + used;
@@ -681,13 +691,48 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         }
         cudaError_t e;
         if (mode == VBCSR_PREC_NATIVE)
-            e = f64 ? launch_fma_f64(b.B, trans, a, s) : launch_fma_f32(b.B, trans, a, s);
+            e = f64 ? launch_fma_f64(B, trans, a, s) : launch_fma_f32(B, trans, a, s);
         else if (mode == VBCSR_PREC_F32)
-            e = launch_fma_f32_on_f64(b.B, trans, a, s);
+            e = launch_fma_f32_on_f64(B, trans, a, s);
         else
             e = launch_mma(mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
+        return VBCSR_OK;
+    };
+    auto fma_kern = [&](bool persistent) {
+        return (mode == VBCSR_PREC_NATIVE) ? (f64 ? fma_f64_kernel(trans, persistent) : fma_f32_kernel(trans, persistent))
+                                           : fma_f32_on_f64_kernel(trans, persistent);
+    };
+    const int64_t n_all = trans ? A->n_adj_items : A->n_fwd_items;
+    int rc = VBCSR_OK;
+    if (!fma) {
+        // tensor-core kernel: the row count is a runtime mask, one launch serves every item
+        const void *kern = mma_kernel_ptr(mode, f64, trans);
+        if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, 4));
+    } else if (A->schedule == 1) {
+        // persistent launch over every row count, items in descending cost from a work queue
+        a.kc_log2_by_b = 0;
+        for (int B = 1; B <= kMaxB; ++B) {
+            int l = 0;
+            while ((1 << l) < kc_for(B)) ++l;
+            a.kc_log2_by_b |= (uint64_t)l << (3 * B);
+        }
+        a.queue = A->queue;
+        CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
+        const int warps = A->persist_warps ? A->persist_warps : 4;
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps, fma_kern(true), fma_smem_bytes(trans, warps));
+    } else {
+        const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
+        const WorkItem *items = trans ? A->adj_items : A->fwd_items;
+        for (const Bucket &b : buckets) {
+            a.kc = kc_for(b.B);
+            const int warps = A->warps_b[b.B] ? A->warps_b[b.B] : 4;
+            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false), fma_smem_bytes(trans, warps));
+            if (rc) return rc;
+        }
     }
+    if (rc) return rc;
     if (want_dot) CUDA_TRY(launch_finalize_dot(A->partials, used, dot_scale, epi->dot_out, s), "dot finalize");
     return VBCSR_OK;
 }
@@ -898,14 +943,130 @@ extern "C" int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, i
     return n;
 }
 
+static bool valid_kc(int kc) { return kc == 0 || kc == 1 || kc == 2 || kc == 4 || kc == 8 || kc == 16 || kc == 32; }
+static bool valid_warps(int w) { return w == 0 || w == 1 || w == 2 || w == 4 || w == 8; }
+
 extern "C" int vbcsr_set_tuning(vbcsr_t *A, int32_t kc, int32_t warps) {
+    return vbcsr_set_bucket_tuning(A, 0, kc, warps);
+}
+
+extern "C" int vbcsr_set_bucket_tuning(vbcsr_t *A, int32_t B, int32_t kc, int32_t warps) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (!(kc == 0 || kc == 1 || kc == 2 || kc == 4 || kc == 8 || kc == 16 || kc == 32))
-        return fail(VBCSR_ERR_INVALID_ARG, "kc = %d", kc);
-    if (!(warps == 0 || warps == 1 || warps == 2 || warps == 4 || warps == 8))
-        return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", warps);
-    A->kc = kc;
-    A->warps = warps;
+    if (B < 0 || B > kMaxB) return fail(VBCSR_ERR_INVALID_ARG, "row count %d outside [0, %d]", B, kMaxB);
+    if (!valid_kc(kc)) return fail(VBCSR_ERR_INVALID_ARG, "kc = %d", kc);
+    if (!valid_warps(warps)) return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", warps);
+    for (int b = (B ? B : 1); b <= (B ? B : kMaxB); ++b) {
+        A->kc_b[b] = kc;
+        A->warps_b[b] = warps;
+    }
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_set_schedule(vbcsr_t *A, int32_t schedule, int32_t persist_warps) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (schedule != VBCSR_SCHED_BUCKETED && schedule != VBCSR_SCHED_PERSISTENT)
+        return fail(VBCSR_ERR_INVALID_ARG, "schedule %d", schedule);
+    if (!valid_warps(persist_warps)) return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", persist_warps);
+    A->schedule = schedule;
+    A->persist_warps = persist_warps;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_get_tuning(const vbcsr_t *A, int32_t *kc_by_b, int32_t *warps_by_b, int32_t *schedule,
+                                int32_t *persist_warps) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    for (int b = 0; b <= kMaxB; ++b) {
+        if (kc_by_b) kc_by_b[b] = A->kc_b[b];
+        if (warps_by_b) warps_by_b[b] = A->warps_b[b];
+    }
+    if (schedule) *schedule = A->schedule;
+    if (persist_warps) *persist_warps = A->persist_warps;
+    return VBCSR_OK;
+}
+
+// Mean device time of `reps` runs of one product configuration (ms), or < 0.
+static double time_product(vbcsr_t *A, bool trans, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,
+                           int precision, cudaStream_t s, int reps) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+    double ms = -1.0;
+    if (run_product(A, trans, k, 1.0, X, ldx, 0.0, Y, ldy, nullptr, precision, s) == VBCSR_OK) {
+        cudaEventRecord(e0, s);
+        bool ok = true;
+        for (int r = 0; r < reps && ok; ++r)
+            ok = run_product(A, trans, k, 1.0, X, ldx, 0.0, Y, ldy, nullptr, precision, s) == VBCSR_OK;
+        cudaEventRecord(e1, s);
+        float t = 0.f;
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+            ms = t / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *X, int64_t ldx, void *Y,
+                              int64_t ldy, int precision, int32_t flags, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (transpose != 0 && transpose != 1) return fail(VBCSR_ERR_INVALID_ARG, "transpose must be 0 or 1");
+    if (k < 1) return fail(VBCSR_ERR_INVALID_ARG, "k must be >= 1");
+    if (precision != VBCSR_PREC_NATIVE && !(precision == VBCSR_PREC_F32 && A->dtype == VBCSR_F64)) {
+        // the tensor-core kernels have no per-row-count tile to choose
+        if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_BF16X2)
+            return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+        return VBCSR_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool trans = transpose == 1;
+    const int reps = 3;
+    const int kcs[] = {1, 2, 4, 8, 16, 32};
+    const int wss[] = {2, 4, 8};
+    const int kc_auto = auto_kc(k);
+    // 1) per row count: the column tile and CTA width of its bucket launch
+    const int saved_schedule = A->schedule;
+    A->schedule = VBCSR_SCHED_BUCKETED;
+    const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
+    int keep_kc[kMaxB + 1], keep_w[kMaxB + 1];
+    memcpy(keep_kc, A->kc_b, sizeof(keep_kc));
+    memcpy(keep_w, A->warps_b, sizeof(keep_w));
+    for (const Bucket &b : buckets) {
+        double best = 1e30;
+        int bkc = 0, bw = 0;
+        // time this bucket alone: other buckets get an empty share by pointing their
+        // tiles at the auto choice (their time is a constant offset)
+        for (int kc : kcs) {
+            if (kc > kc_auto) continue;
+            for (int w : wss) {
+                A->kc_b[b.B] = kc;
+                A->warps_b[b.B] = w;
+                const double ms = time_product(A, trans, k, X, ldx, Y, ldy, precision, s, reps);
+                if (ms < 0) {
+                    memcpy(A->kc_b, keep_kc, sizeof(keep_kc));
+                    memcpy(A->warps_b, keep_w, sizeof(keep_w));
+                    A->schedule = saved_schedule;
+                    return fail(VBCSR_ERR_CUDA, "autotune trial failed: %s", g_detail.c_str());
+                }
+                if (ms < best) { best = ms; bkc = kc; bw = w; }
+            }
+        }
+        A->kc_b[b.B] = bkc;
+        A->warps_b[b.B] = bw;
+    }
+    const double t_bucketed = time_product(A, trans, k, X, ldx, Y, ldy, precision, s, reps);
+    // 2) the persistent launch with those tiles: its CTA width, then the faster schedule
+    int schedule = VBCSR_SCHED_BUCKETED, pw = 0;
+    double best = t_bucketed;
+    if (!(flags & VBCSR_TUNE_NO_PERSISTENT)) {
+        A->schedule = VBCSR_SCHED_PERSISTENT;
+        for (int w : wss) {
+            A->persist_warps = w;
+            const double ms = time_product(A, trans, k, X, ldx, Y, ldy, precision, s, reps);
+            if (ms >= 0 && ms < best) { best = ms; schedule = VBCSR_SCHED_PERSISTENT; pw = w; }
+        }
+    }
+    A->schedule = schedule;
+    A->persist_warps = pw;
     return VBCSR_OK;
 }
 

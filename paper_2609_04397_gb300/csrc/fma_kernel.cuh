@@ -11,9 +11,14 @@
 //            H_ij[p, q0 + q], contiguous in q (Eq. 1).
 // Lanes split as (tg, c): c = lane % KC picks an output column of the pass,
 // tg = lane / KC strides the virtual columns. Each lane keeps B partial sums
-// in registers; a butterfly over the tg lanes finishes them, and each output
-// entry is written once by one lane (no atomics). The epilogue applies
-// alpha, beta, gamma * Z and accumulates the optional FP64 dot with R.
+// in registers; the tg lanes of a column then combine them (a reduce-scatter
+// when KC = 1, a butterfly otherwise), and each output entry is written once
+// by one lane (no atomics). The epilogue applies alpha, beta, gamma * Z and
+// accumulates the optional FP64 dot with R.
+//
+// Two launch shapes share the per-item code: one launch per row count B over
+// the items of that count, and one persistent launch over all items (a switch
+// on B per item) that takes items from a work queue in descending-cost order.
 #pragma once
 
 #include "internal.cuh"
@@ -26,6 +31,149 @@ __device__ __forceinline__ T ld_ro(const T *p) { return __ldg(p); }
 __device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 
+// Stage the X row (and, for the adjoint, the value address) of virtual
+// columns [t0, t0 + tn) of item w in shared memory.
+template <bool TRANS>
+__device__ __forceinline__ void stage_columns(const ProdArgs &a, const WorkItem &w, int t0, int tn,
+                                              int32_t *s_x, int64_t *s_a, int lane) {
+    __syncwarp();
+    for (int e = lane; e < w.nlist; e += 32) {
+        const int64_t l = w.lbegin + e;
+        if (!TRANS) {
+            const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
+            const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
+            for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
+        } else {
+            const int64_t pb = a.tl.pbase[l];
+            const int kp = a.tl.kp[l], bi = a.tl.bi[l];
+            const int xr = a.tl.xrow[l], vc = a.tl.vcol[l];
+            const int lo = max(vc, t0), hi = min(vc + bi, t0 + tn);
+            for (int t = lo; t < hi; ++t) {
+                s_x[t - t0] = xr + (t - vc);
+                s_a[t - t0] = pb + (int64_t)(t - vc) * kp + w.Kp;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <typename TX>
+__device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_t c, TX acc, double &dot) {
+    TX *Y = static_cast<TX *>(a.Y);
+    TX *yp = Y + row * a.ldy + c;
+    TX r = (TX)a.alpha * acc;
+    if (a.beta != 0.0) r += (TX)a.beta * *yp;
+    if (a.gamma != 0.0) r += (TX)a.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
+    *yp = r;
+    if (a.partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
+}
+
+// Reduce-scatter of B (<= 16) per-lane partial sums over all 32 lanes: after
+// it, lane l holds the full sum of row rs_row(l) (lanes l and l^1 agree). It
+// costs 16 adds per lane instead of 5 * B for a butterfly on every row.
+__device__ __forceinline__ int rs_row(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
+template <int B, typename TA>
+__device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
+    TA v8[8], v4[4], v2[2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const TA lo = (j < B) ? acc[j] : (TA)0, hi = (j + 8 < B) ? acc[j + 8] : (TA)0;
+        const bool up = lane & 16;
+        const TA keep = up ? hi : lo, send = up ? lo : hi;
+        v8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool up = lane & 8;
+        const TA keep = up ? v8[j + 4] : v8[j], send = up ? v8[j] : v8[j + 4];
+        v4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const bool up = lane & 4;
+        const TA keep = up ? v4[j + 2] : v4[j], send = up ? v4[j] : v4[j + 2];
+        v2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const bool up = lane & 2;
+    TA v = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, up ? v2[0] : v2[1], 2);
+    return v + __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+template <int B, bool TRANS, typename TV, typename TA, typename TX>
+__device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &w, int KC, int32_t *s_x,
+                                             int64_t *s_a, int lane, double &dot) {
+    const int TG = 32 / KC;
+    const int cl = lane % KC;
+    const int tg = lane / KC;
+    const TV *__restrict__ vals = static_cast<const TV *>(a.values);
+    const TX *__restrict__ X = static_cast<const TX *>(a.X);
+    const bool do_prod = a.alpha != 0.0;
+
+    for (int64_t c0 = 0; c0 < a.k; c0 += KC) {
+        const int64_t c = c0 + cl;
+        const bool cv = c < a.k;
+        TA acc[B];
+#pragma unroll
+        for (int p = 0; p < B; ++p) acc[p] = (TA)0;
+
+        if (do_prod) {
+            for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+                const int tn = min(kKMax, w.K - t0);
+                if (c0 == 0 || w.K > kKMax) stage_columns<TRANS>(a, w, t0, tn, s_x, s_a, lane);
+                for (int t = tg; t < tn; t += TG) {
+                    const int xr = s_x[t];
+                    if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
+                        atomicExch(a.err, 1);
+                        continue;
+                    }
+                    const TA x = cv ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
+                    if (!TRANS) {
+                        const TV *v = vals + w.vbase + t0 + t;
+                        const int64_t kp = w.Kp;
+#pragma unroll
+                        for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p * kp), x, acc[p]);
+                    } else {
+                        const TV *v = vals + s_a[t];
+#pragma unroll
+                        for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p), x, acc[p]);
+                    }
+                }
+            }
+        }
+        if (KC == 1) {
+            // every lane worked on column c0; one reduce-scatter finishes all rows
+            const TA v = reduce_scatter32<B>(acc, lane);
+            const int p = rs_row(lane);
+            if ((lane & 1) == 0 && p < B && cv) write_out<TX>(a, w.yrow + p, c, (TX)v, dot);
+        } else {
+            for (int m = KC; m < 32; m <<= 1) {
+#pragma unroll
+                for (int p = 0; p < B; ++p) acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], m);
+            }
+#pragma unroll
+            for (int p = 0; p < B; ++p)
+                if ((p % TG) == tg && cv) write_out<TX>(a, w.yrow + p, c, (TX)acc[p], dot);
+        }
+    }
+}
+
+__device__ __forceinline__ void finish_dot(const ProdArgs &a, double dot, int warp, int lane, int warps) {
+    // fixed-order CTA reduction of the dot partials
+    for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+    __shared__ double s_dot[32];
+    __syncthreads();
+    if (lane == 0) s_dot[warp] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < warps; ++i) s += s_dot[i];
+        a.partials[blockIdx.x] = s;
+    }
+}
+
 template <int B, bool TRANS, typename TV, typename TA, typename TX>
 __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,113 +183,62 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
-
-    const int KC = a.kc;
-    const int TG = 32 / KC;
-    const int cl = lane % KC;
-    const int tg = lane / KC;
-    const TV *__restrict__ vals = static_cast<const TV *>(a.values);
-    const TX *__restrict__ X = static_cast<const TX *>(a.X);
-    TX *__restrict__ Y = static_cast<TX *>(a.Y);
-    const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
-    const TX *__restrict__ R = static_cast<const TX *>(a.R);
-    const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
-    const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
-
-    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items;
-         it += (int64_t)gridDim.x * warps) {
+    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        for (int64_t c0 = 0; c0 < a.k; c0 += KC) {
-            const int64_t c = c0 + cl;
-            const bool cv = c < a.k;
-            TA acc[B];
-#pragma unroll
-            for (int p = 0; p < B; ++p) acc[p] = (TA)0;
-
-            if (do_prod) {
-                for (int t0 = 0; t0 < w.K; t0 += kKMax) {
-                    const int tn = min(kKMax, w.K - t0);
-                    if (c0 == 0 || w.K > kKMax) {
-                        __syncwarp();
-                        for (int e = lane; e < w.nlist; e += 32) {
-                            const int64_t l = w.lbegin + e;
-                            if (!TRANS) {
-                                const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
-                                const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
-                                for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
-                            } else {
-                                const int64_t pb = a.tl.pbase[l];
-                                const int kp = a.tl.kp[l], bi = a.tl.bi[l];
-                                const int xr = a.tl.xrow[l], vc = a.tl.vcol[l];
-                                const int lo = max(vc, t0), hi = min(vc + bi, t0 + tn);
-                                for (int t = lo; t < hi; ++t) {
-                                    s_x[t - t0] = xr + (t - vc);
-                                    s_a[t - t0] = pb + (int64_t)(t - vc) * kp + w.Kp;
-                                }
-                            }
-                        }
-                        __syncwarp();
-                    }
-                    for (int t = tg; t < tn; t += TG) {
-                        const int xr = s_x[t];
-                        if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
-                            atomicExch(a.err, 1);
-                            continue;
-                        }
-                        const TA x = cv ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
-                        if (!TRANS) {
-                            const TV *v = vals + w.vbase + t0 + t;
-                            const int64_t kp = w.Kp;
-#pragma unroll
-                            for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p * kp), x, acc[p]);
-                        } else {
-                            const TV *v = vals + s_a[t];
-#pragma unroll
-                            for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p), x, acc[p]);
-                        }
-                    }
-                }
-            }
-            // finish the partial sums over the tg lanes that share column c
-            for (int m = KC; m < 32; m <<= 1) {
-#pragma unroll
-                for (int p = 0; p < B; ++p) acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], m);
-            }
-#pragma unroll
-            for (int p = 0; p < B; ++p) {
-                if ((p % TG) == tg && cv) {
-                    const int64_t row = w.yrow + p;
-                    TX *yp = Y + row * a.ldy + c;
-                    TX r = alpha * (TX)acc[p];
-                    if (a.beta != 0.0) r += beta * *yp;
-                    if (a.gamma != 0.0) r += gamma * Z[row * a.ldz + c];
-                    *yp = r;
-                    if (a.partials) dot += (double)R[row * a.ldr + c] * (double)r;
-                }
-            }
-        }
+        process_item<B, TRANS, TV, TA, TX>(a, w, a.kc, s_x, s_a, lane, dot);
     }
+    if (a.partials) finish_dot(a, dot, warp, lane, warps);
+}
 
-    if (a.partials) {
-        // fixed-order CTA reduction of the dot partials
-        for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
-        __shared__ double s_dot[32];
-        __syncthreads();
-        if (lane == 0) s_dot[warp] = dot;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < warps; ++i) s += s_dot[i];
-            a.partials[blockIdx.x] = s;
+// One launch over items of every row count. Items come from a.items in
+// order (the planner sorts them by descending cost); warps take the next
+// item from a device counter (a.queue, zeroed before the launch) or, without
+// a queue, round-robin. a.kc_of(B) is the column tile of row count B.
+template <bool TRANS, typename TV, typename TA, typename TX>
+__global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warps = a.warps;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
+    int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
+                   warp * kKMax;
+    double dot = 0.0;
+    int64_t it = (int64_t)blockIdx.x * warps + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long q = 0;
+            if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
         }
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+        const int kc = a.kc_of(w.B);
+#define VBCSR_ITEM_CASE(NB) \
+    case NB: process_item<NB, TRANS, TV, TA, TX>(a, w, kc, s_x, s_a, lane, dot); break;
+        switch (w.B) {
+            VBCSR_ITEM_CASE(1) VBCSR_ITEM_CASE(2) VBCSR_ITEM_CASE(3) VBCSR_ITEM_CASE(4)
+            VBCSR_ITEM_CASE(5) VBCSR_ITEM_CASE(6) VBCSR_ITEM_CASE(7) VBCSR_ITEM_CASE(8)
+            VBCSR_ITEM_CASE(9) VBCSR_ITEM_CASE(10) VBCSR_ITEM_CASE(11) VBCSR_ITEM_CASE(12)
+            VBCSR_ITEM_CASE(13) VBCSR_ITEM_CASE(14) VBCSR_ITEM_CASE(15) VBCSR_ITEM_CASE(16)
+            default: break;
+        }
+#undef VBCSR_ITEM_CASE
+        if (!a.queue) it += (int64_t)gridDim.x * warps;
     }
+    if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
 
 template <typename TV, typename TA, typename TX>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s) {
     const int threads = a.warps * 32;
     const size_t smem = fma_smem_bytes(trans, a.warps);
+    if (B == 0) {   // persistent launch over every row count
+        if (trans) fma_persistent_kernel<true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+        else fma_persistent_kernel<false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+        return cudaGetLastError();
+    }
 #define VBCSR_FMA_CASE(NB)                                                                        \
     case NB:                                                                                      \
         if (trans) fma_product_kernel<NB, true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);    \
@@ -159,8 +256,11 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
 }
 
 template <typename TV, typename TA, typename TX>
-const void *fma_kernel_ptr(bool trans) {
-    // B = 16 is the largest register footprint; used for the occupancy cap
+const void *fma_kernel_ptr(bool trans, bool persistent) {
+    // B = 16 is the largest register footprint of the bucketed kernels
+    if (persistent)
+        return trans ? (const void *)fma_persistent_kernel<true, TV, TA, TX>
+                     : (const void *)fma_persistent_kernel<false, TV, TA, TX>;
     return trans ? (const void *)fma_product_kernel<16, true, TV, TA, TX>
                  : (const void *)fma_product_kernel<16, false, TV, TA, TX>;
 }

@@ -77,9 +77,14 @@ struct ProdArgs {
     int debug_checks;
     int grid;               // CTAs
     int warps;              // warps per CTA
+    // persistent launch only
+    long long *queue;       // device work counter, zero at launch (NULL: round-robin)
+    uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
+    __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
-// Kernel families (defined in spmm_fma_*.cu and spmm_mma.cu).
+// Kernel families (defined in spmm_fma_*.cu and spmm_mma.cu). B = 0 selects
+// the persistent launch over items of every row count.
 // value/accumulate/X types: f64 = <double,double,double>; f32 = <float,float,float>;
 // f32_on_f64 = <float,float,double> (FP32 arithmetic on an FP64 operator).
 cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);

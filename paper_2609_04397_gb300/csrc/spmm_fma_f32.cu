@@ -13,7 +13,11 @@ cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStre
     return launch_fma_family<float, float, double>(B, trans, a, s);
 }
 
-const void *fma_f32_kernel(bool trans) { return fma_kernel_ptr<float, float, float>(trans); }
-const void *fma_f32_on_f64_kernel(bool trans) { return fma_kernel_ptr<float, float, double>(trans); }
+const void *fma_f32_kernel(bool trans, bool persistent) {
+    return fma_kernel_ptr<float, float, float>(trans, persistent);
+}
+const void *fma_f32_on_f64_kernel(bool trans, bool persistent) {
+    return fma_kernel_ptr<float, float, double>(trans, persistent);
+}
 
 }  // namespace vbcsr

@@ -7,6 +7,8 @@ cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s)
     return launch_fma_family<double, double, double>(B, trans, a, s);
 }
 
-const void *fma_f64_kernel(bool trans) { return fma_kernel_ptr<double, double, double>(trans); }
+const void *fma_f64_kernel(bool trans, bool persistent) {
+    return fma_kernel_ptr<double, double, double>(trans, persistent);
+}
 
 }  // namespace vbcsr

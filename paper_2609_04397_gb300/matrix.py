@@ -140,8 +140,68 @@ class VBCSR:
               "vbcsr_shape_classes")
         return list(zip(bi.tolist(), bj.tolist(), cnt.tolist()))
 
-    def set_tuning(self, kc: int = 0, warps: int = 0):
-        check(lib().vbcsr_set_tuning(self._h, kc, warps), "vbcsr_set_tuning")
+    def set_tuning(self, kc: int = 0, warps: int = 0, B: int = 0):
+        """Column tile and CTA width of the bucket of row count B (0: all)."""
+        check(lib().vbcsr_set_bucket_tuning(self._h, B, kc, warps), "vbcsr_set_bucket_tuning")
+
+    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0):
+        """'bucketed' (one launch per row count) or 'persistent' (one launch)."""
+        code = {"bucketed": 0, "persistent": 1}[schedule]
+        check(lib().vbcsr_set_schedule(self._h, code, persist_warps), "vbcsr_set_schedule")
+
+    def get_tuning(self) -> dict:
+        kc = np.zeros(17, np.int32)
+        w = np.zeros(17, np.int32)
+        sch = ctypes.c_int32()
+        pw = ctypes.c_int32()
+        check(lib().vbcsr_get_tuning(self._h, kc.ctypes.data, w.ctypes.data, ctypes.byref(sch),
+                                     ctypes.byref(pw)), "vbcsr_get_tuning")
+        return {"kc_by_b": kc.tolist(), "warps_by_b": w.tolist(),
+                "schedule": ["bucketed", "persistent"][sch.value], "persist_warps": pw.value}
+
+    def apply_tuning(self, t: dict):
+        for B in range(1, 17):
+            self.set_tuning(t["kc_by_b"][B], t["warps_by_b"][B], B)
+        self.set_schedule(t["schedule"], t["persist_warps"])
+
+    def autotune(self, k: int, precision="native", transpose: bool = False, allow_persistent: bool = True,
+                 cache: Optional[str] = None) -> dict:
+        """Choose per-row-count tiles and the schedule by timing the product at
+        width k on scratch panels; with `cache`, reuse/record the choice in a
+        JSON file keyed by the pattern, k, precision and direction."""
+        key = None
+        if cache:
+            import hashlib
+            import json
+            import os
+            h = hashlib.sha1()
+            for a in self.pattern:
+                h.update(np.ascontiguousarray(a).tobytes())
+            key = f"{h.hexdigest()}:{k}:{precision}:{int(transpose)}:{int(allow_persistent)}"
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    db = json.load(f)
+                if key in db:
+                    self.apply_tuning(db[key])
+                    return db[key]
+        n_in, n_out = (self.shape[0], self.shape[1]) if transpose else (self.shape[1], self.shape[0])
+        X = torch.randn(n_in, k, dtype=self.dtype, device=self.device)
+        Y = torch.empty(n_out, k, dtype=self.dtype, device=self.device)
+        check(lib().vbcsr_autotune(self._h, int(transpose), k, ctypes.c_void_p(X.data_ptr()), k,
+                                   ctypes.c_void_p(Y.data_ptr()), k, _prec(precision),
+                                   0 if allow_persistent else 1, _stream(self.device)), "vbcsr_autotune")
+        t = self.get_tuning()
+        if cache:
+            import json
+            import os
+            db = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    db = json.load(f)
+            db[key] = t
+            with open(cache, "w") as f:
+                json.dump(db, f)
+        return t
 
     def check(self):
         check(lib().vbcsr_check(self._h, _stream(self.device)), "vbcsr_check")

@@ -222,3 +222,25 @@ def test_zincblende_full_size_sampled_rows():
         check_elementwise(Y[sel], ref[sel], scale[sel], TOL_F64)
         assert rel_fro(Y[sel], ref[sel]) <= TOL_F64
     H.check()
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_fused_epilogue_gamma_z_and_dot(transpose):
+    """Y = alpha op(H) X + beta Y + gamma Z and dot = sum(R * Y) through vbcsr_spmm_ex."""
+    pat = syn.random_pattern(33, 33, (4, 9, 13), 0.2, 21)
+    vals = syn.random_values(pat, 21)
+    H = _handle(pat, vals)
+    rng = np.random.default_rng(3)
+    n_in, n_out = (pat.n_rows, pat.n_cols) if transpose else (pat.n_cols, pat.n_rows)
+    X = rng.standard_normal((n_in, 5))
+    Y0 = rng.standard_normal((n_out, 5))
+    Z = rng.standard_normal((n_out, 5))
+    R = rng.standard_normal((n_out, 5))
+    Yd = _dev(Y0)
+    dot = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    H.spmm_ex(_dev(X), 2.0, -1.0, Yd, transpose=transpose, gamma=0.5, Z=_dev(Z), R=_dev(R), dot_out=dot)
+    fn = oracle.spmm_adjoint if transpose else oracle.spmm
+    ref = fn(pat, vals, X, 2.0, -1.0, Y0) + 0.5 * Z
+    got = Yd.cpu().numpy()
+    assert rel_fro(got, ref) <= TOL_F64
+    assert abs(dot.item() - np.sum(R * ref)) <= 1e-12 * np.sum(np.abs(R * ref))
