@@ -613,7 +613,7 @@ static int cached_cap(const void *kernel, int warps, size_t smem) {
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int c = max_resident_ctas(kernel, warps * 32, smem);
-    cache[key] = c;
+    if (c > 0) cache[key] = c;
     return c;
 }
 
@@ -680,7 +680,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         a.items = items;
         a.n_items = n;
         a.warps = warps;
+        cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) return cuda_fail(pending, "error pending before the product launch");
         const int cap = cached_cap(kern, warps, smem);
+        if (cap < 0) return cuda_fail(cudaGetLastError(), "occupancy query of the product kernel");
         const int64_t need = (n + warps - 1) / warps;
         a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
         a.partials = nullptr;

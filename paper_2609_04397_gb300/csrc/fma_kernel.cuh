@@ -230,19 +230,40 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
 
+// Kernels whose dynamic shared memory plus the static dot buffer would pass
+// the default 48 KB per CTA need the larger carve-out requested first.
+template <typename K>
+inline cudaError_t launch_smem_opt_in(K kernel, size_t smem) {
+    if (smem + 1024 <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 1024);
+}
+
 template <typename TV, typename TA, typename TX>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s) {
     const int threads = a.warps * 32;
     const size_t smem = fma_smem_bytes(trans, a.warps);
+    cudaError_t e;
     if (B == 0) {   // persistent launch over every row count
-        if (trans) fma_persistent_kernel<true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
-        else fma_persistent_kernel<false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+        if (trans) {
+            if ((e = launch_smem_opt_in(fma_persistent_kernel<true, TV, TA, TX>, smem)) != cudaSuccess) return e;
+            fma_persistent_kernel<true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+        } else {
+            if ((e = launch_smem_opt_in(fma_persistent_kernel<false, TV, TA, TX>, smem)) != cudaSuccess) return e;
+            fma_persistent_kernel<false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+        }
         return cudaGetLastError();
     }
-#define VBCSR_FMA_CASE(NB)                                                                        \
-    case NB:                                                                                      \
-        if (trans) fma_product_kernel<NB, true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);    \
-        else fma_product_kernel<NB, false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);         \
+#define VBCSR_FMA_CASE(NB)                                                                               \
+    case NB:                                                                                             \
+        if (trans) {                                                                                     \
+            if ((e = launch_smem_opt_in(fma_product_kernel<NB, true, TV, TA, TX>, smem)) != cudaSuccess) \
+                return e;                                                                                \
+            fma_product_kernel<NB, true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);                   \
+        } else {                                                                                         \
+            if ((e = launch_smem_opt_in(fma_product_kernel<NB, false, TV, TA, TX>, smem)) != cudaSuccess) \
+                return e;                                                                                \
+            fma_product_kernel<NB, false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);                  \
+        }                                                                                                \
         break;
     switch (B) {
         VBCSR_FMA_CASE(1) VBCSR_FMA_CASE(2) VBCSR_FMA_CASE(3) VBCSR_FMA_CASE(4)

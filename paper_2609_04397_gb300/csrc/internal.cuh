@@ -93,7 +93,8 @@ cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStre
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
 
-// Occupancy-derived CTA count cap for a kernel family (computed once).
+// Occupancy-derived CTA count cap (SMs x resident CTAs per SM); -1 when a CUDA
+// query failed (the error stays pending for the caller to read).
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
 
 size_t fma_smem_bytes(bool trans, int warps);

@@ -10,14 +10,14 @@ size_t fma_smem_bytes(bool trans, int warps) {
 
 int max_resident_ctas(const void *kernel, int threads, size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    return sms * per_sm;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    if (smem + 1024 > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 1024) != cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) return -1;
+    return sms * (per_sm < 1 ? 1 : per_sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -62,9 +62,14 @@ cudaError_t launch_sddmm(bool f64, const SddmmArgs &a, cudaStream_t s) {
     const int warps = 8, threads = warps * 32;
     static int cap64 = 0, cap32 = 0;
     int &cap = f64 ? cap64 : cap32;
-    if (!cap)
+    if (!cap) {
         cap = max_resident_ctas(f64 ? (const void *)sddmm_kernel<double> : (const void *)sddmm_kernel<float>,
                                 threads, 0);
+        if (cap < 0) {
+            cap = 0;
+            return cudaGetLastError();
+        }
+    }
     int64_t need = (a.n_brows + warps - 1) / warps;
     int grid = (int)(need < cap ? need : cap);
     if (f64) sddmm_kernel<double><<<grid, threads, 0, s>>>(a, warps);
