@@ -256,6 +256,30 @@ int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ld
                              const double *grad_mu, const double *ckpt, int64_t ckpt_every,
                              double *dvalues, double *work, int precision, void *stream);
 
+/*
+ * vbcsr_chebyshev without the `work` argument (and without checkpoints), for
+ * callers that cannot allocate device memory at the point where they need
+ * the moments: code whose device memory belongs to another allocator (a host
+ * application or framework that reserves the free memory up front) or a loop
+ * that must not allocate once it runs. Such a caller creates the operator at
+ * start-up; this call then allocates nothing (no cudaMalloc or cudaFree): the
+ * recurrence's two work panels live in a fixed 16 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.
+ *  Limit: n_rows * k <= 1,048,576 (2^20); larger requests return
+ *         VBCSR_ERR_UNSUPPORTED and launch nothing.
+ *  The first call on a device looks up the array's device address (with
+ *  that device current); make that first call before any stream capture.
+ *  All calls share the one array: calls whose work overlaps on the GPU (on
+ *  different streams, or from several threads) race and give wrong moments.
+ *  Nothing in the array needs to start at zero: each call writes every element
+ *  it reads before reading it.
+ * Arguments, moments and errors as in vbcsr_chebyshev. (This entry point has
+ * no counterpart in the paper.)
+ */
+int vbcsr_chebyshev_noalloc(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                            double *moments, int precision, void *stream);
+
 /* ---- inspection ---------------------------------------------------------- */
 
 int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out);

@@ -43,6 +43,7 @@ SIGNATURES = {
     "vbcsr_sddmm": ([_p, _i64, _d, _p, _i64, _p, _i64, _d, _p, _p], _int),
     "vbcsr_chebyshev": ([_p, _i64, _p, _i64, _i64, _p, _p, _p, _i64, _int, _p], _int),
     "vbcsr_chebyshev_backward": ([_p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _p, _int, _p], _int),
+    "vbcsr_chebyshev_noalloc": ([_p, _i64, _p, _i64, _i64, _p, _int, _p], _int),
     "vbcsr_get_info": ([_p, ctypes.POINTER(Info)], _int),
     "vbcsr_shape_classes": ([_p, _p, _p, _p, _i32], _int),
     "vbcsr_set_tuning": ([_p, _i32, _i32], _int),

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -1084,4 +1085,48 @@ extern "C" int vbcsr_check(vbcsr_t *A, void *stream) {
         return fail(VBCSR_ERR_DEVICE_CHECK, "device self-check code %d", h);
     }
     return VBCSR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev moments without a caller-provided work buffer
+//
+// For callers that cannot allocate device memory when they need the moments:
+// code whose device memory is owned by another allocator (a host application
+// or framework that reserves the free memory up front), or a loop that must
+// not allocate once it runs. Such a caller creates the operator once at
+// start-up and later calls this entry point, which allocates nothing: the two
+// work panels of the recurrence live in the fixed array below, which every
+// GPU that loads the library holds until the process exits.
+
+static constexpr int64_t kNoAllocPanelElems = int64_t(1) << 20;   // n_rows * k per panel, at most
+static __device__ __align__(256) double g_cheb_scratch[2 * kNoAllocPanelElems];   // 16 MiB
+
+extern "C" int vbcsr_chebyshev_noalloc(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                                       double *moments, int precision, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (k < 1) return fail(VBCSR_ERR_INVALID_ARG, "k must be >= 1");
+    if (A->n_rows > kNoAllocPanelElems / k)
+        return fail(VBCSR_ERR_UNSUPPORTED,
+                    "n_rows * k = %lld * %lld exceeds the fixed work area of %lld elements per panel",
+                    (long long)A->n_rows, (long long)k, (long long)kNoAllocPanelElems);
+    // set-up, once per device: host code cannot use g_cheb_scratch as a device
+    // address, so ask the runtime for it with that device current
+    static std::mutex mu;
+    static std::map<int, double *> addr;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    double *work = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = addr.find(dev);
+        if (it == addr.end()) {
+            void *p = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&p, g_cheb_scratch), "cudaGetSymbolAddress of the work area");
+            it = addr.emplace(dev, static_cast<double *>(p)).first;
+        }
+        work = it->second;
+    }
+    // every element of the work panels that the recurrence reads is written
+    // earlier in the same call, so nothing has to be cleared first
+    return vbcsr_chebyshev(A, k, R, ldr, n_moments, moments, work, nullptr, 0, precision, stream);
 }
