@@ -346,7 +346,10 @@ def run_ours(args):
     # ---- mixed precision vs FP64 on the same workload (separately timed) ----
     mixed = {}
     ref = {k: Ys[k].clone() for k in KS}
-    for mode in ("bf16x2", "tf32x3", "f32"):
+    variants = [("df32", False), ("bf16x2", False), ("bf16x2", True), ("tf32x3", False), ("tf32x3", True),
+                ("f32", False)]
+    for mode, staged in variants:
+        H.set_schedule("bucketed", mma_staged=staged)
         for k in KS:
             H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
         torch.cuda.synchronize(dev)
@@ -361,8 +364,10 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / reps
-        mixed[mode] = {"ms_per_step": ms, "speedup_vs_f64": (total_ms / args.steps) / ms,
-                       "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9}
+        mixed[mode + ("_staged" if staged else "")] = {
+            "ms_per_step": ms, "speedup_vs_f64": (total_ms / args.steps) / ms,
+            "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9}
+    H.set_schedule("bucketed")
 
     # ---- end to end through the public API: pinned host X in, Y out, every step ----
     hX = {k: torch.randn(pat.n_cols, k, dtype=torch.float64).pin_memory() for k in KS}

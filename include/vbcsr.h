@@ -57,27 +57,40 @@ typedef enum {
 /*
  * Arithmetic of the block products. X, Y, alpha, beta and the epilogue stay in
  * the matrix dtype in every mode; the mixed modes keep an FP32 copy of the
- * values (built on first use, refreshed by vbcsr_set_values).
+ * values (built on first use, refreshed by vbcsr_set_values) and, for an FP64
+ * operator, convert X to FP32 once per call into a buffer the handle owns
+ * (allocated on first use and grown when a call needs more; growing it
+ * synchronises the stream). Mixed-mode calls on one handle therefore must not
+ * overlap on the GPU.
  *  NATIVE  products and accumulation in the matrix dtype (FP64 FMA / FP32 FMA)
  *  F32     values and X rounded to FP32, FP32 FMA, FP32 accumulation
  *  TF32    one TF32 tensor-core product per block product, FP32 accumulation
  *  TF32X3  v = hi + lo with hi = tf32(v), lo = tf32(v - hi) for values and X;
  *          hi*hi + hi*lo + lo*hi on the tensor cores, FP32 accumulation
  *  BF16X2  the same split with bf16 pieces, FP32 accumulation
+ *  DF32    FP64-accurate: values and X carried as pairs hi + lo of FP32
+ *          numbers (48 significand bits), products with an exact leading
+ *          part (fused multiply-add) and TwoSum accumulation on the FP32
+ *          units; relative error a few 2^-48 of sum |h x|. FP64 operators
+ *          only; operands must lie inside the FP32 exponent range
+ *          (|v| in about [1e-30, 1e38]) for that accuracy.
  */
 typedef enum {
     VBCSR_PREC_NATIVE = 0,
     VBCSR_PREC_F32 = 1,
     VBCSR_PREC_TF32 = 2,
     VBCSR_PREC_TF32X3 = 3,
-    VBCSR_PREC_BF16X2 = 4
+    VBCSR_PREC_BF16X2 = 4,
+    VBCSR_PREC_DF32 = 5
 } vbcsr_precision;
 
 /* Launch schedules of the CUDA-core products (vbcsr_set_schedule). */
 typedef enum {
     VBCSR_SCHED_BUCKETED = 0,     /* one launch per work-item row count (default)      */
-    VBCSR_SCHED_PERSISTENT = 1    /* one launch over all items, costliest first, warps
+    VBCSR_SCHED_PERSISTENT = 1,   /* one launch over all items, costliest first, warps
                                      taking items from a device work counter           */
+    VBCSR_SCHED_MMA_STAGED = 2    /* flag: the tensor-core forward kernel stages value
+                                     panels in shared memory with bulk async copies   */
 } vbcsr_schedule;
 
 /* Flags of vbcsr_autotune. */
@@ -257,6 +270,24 @@ int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ld
                              double *dvalues, double *work, int precision, void *stream);
 
 /*
+ * Spectral bounds for the kernel polynomial method (Sec. V needs H scaled so
+ * that its spectrum lies in [-1, 1]): Gershgorin discs over scalar rows,
+ *   bounds[0] = min_r (H_rr - sum_{c != r} |H_rc|),
+ *   bounds[1] = max_r (H_rr + sum_{c != r} |H_rc|),
+ * written to the device array `bounds` (2 doubles). Square FP64 operator.
+ */
+int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream);
+
+/*
+ * Replaces the stored values by those of H~ = (H - c I) / d (c subtracted on
+ * the scalar diagonal, every entry divided by d), in place, for the Chebyshev
+ * recurrence; with c = (E+ + E-)/2 and d slightly above (E+ - E-)/2 from
+ * vbcsr_gershgorin the spectrum of H~ lies inside [-1, 1]. Square FP64
+ * operator; d must be nonzero and finite.
+ */
+int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream);
+
+/*
  * vbcsr_chebyshev without the `work` argument (and without checkpoints), for
  * callers that cannot allocate device memory at the point where they need
  * the moments: code whose device memory belongs to another allocator (a host
@@ -300,8 +331,9 @@ int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, int64_t *cou
  * k's automatic choice is clamped to it.
  *  vbcsr_set_tuning         the same kc and warps for every bucket
  *  vbcsr_set_bucket_tuning  one bucket (B = 0: every bucket)
- *  vbcsr_set_schedule       VBCSR_SCHED_BUCKETED or VBCSR_SCHED_PERSISTENT and the
- *                           CTA width of the persistent launch (0 = 4)
+ *  vbcsr_set_schedule       VBCSR_SCHED_BUCKETED or VBCSR_SCHED_PERSISTENT, optionally
+ *                           OR VBCSR_SCHED_MMA_STAGED, and the CTA width of the
+ *                           persistent launch (0 = 4)
  *  vbcsr_get_tuning         reads them back: kc_by_b[17], warps_by_b[17] (index = B;
  *                           any pointer may be NULL)
  * They apply to later calls on this handle. The tensor-core modes ignore them.
@@ -319,7 +351,8 @@ int vbcsr_get_tuning(const vbcsr_t *A, int32_t *kc_by_b, int32_t *warps_by_b, in
  * whichever schedule is faster (unless flags has VBCSR_TUNE_NO_PERSISTENT).
  * X and Y are device panels of the product's shapes; Y is overwritten. The
  * call synchronises `stream` repeatedly (a set-up step: do not capture it in
- * a CUDA graph). Tensor-core precisions return at once (nothing to tune).
+ * a CUDA graph). For the tensor-core precisions it only chooses, for the
+ * forward product, between the plain and the shared-memory-staged kernel.
  * (The per-shape-group tuning of tiles has no counterpart in the paper.)
  */
 int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *X, int64_t ldx, void *Y, int64_t ldy,

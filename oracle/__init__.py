@@ -56,7 +56,8 @@ def _load():
         L.oracle_spmm.argtypes = [i64, i64, p, p, p, p, p, i64, d, p, i64, d, p, i64, i64, i64, i32]
         L.oracle_spmm_adjoint.argtypes = [i64, i64, p, p, p, p, p, i64, d, p, i64, d, p, i64]
         L.oracle_sddmm.argtypes = [i64, i64, p, p, p, p, i64, d, p, i64, p, i64, d, p, i32]
-        for f in (L.oracle_spmm, L.oracle_spmm_adjoint, L.oracle_sddmm):
+        L.oracle_gershgorin.argtypes = [i64, i64, p, p, p, p, p, p]
+        for f in (L.oracle_spmm, L.oracle_spmm_adjoint, L.oracle_sddmm, L.oracle_gershgorin):
             f.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -166,32 +167,13 @@ def to_dense(pat, values) -> np.ndarray:
 def gershgorin_bounds(pat, values):
     """(E_min, E_max) from Gershgorin discs over scalar rows: every eigenvalue
     of a square H lies in [min_p (H_pp - R_p), max_p (H_pp + R_p)], R_p the
-    off-diagonal absolute row sum."""
-    rb = np.asarray(pat.row_bsize, np.int64)
-    cb = np.asarray(pat.col_bsize, np.int64)
-    r = np.concatenate([[0], np.cumsum(rb)])
-    c = np.concatenate([[0], np.cumsum(cb)])
-    N = int(r[-1])
-    rows = np.repeat(np.arange(len(rb)), np.diff(pat.block_row_ptr))
-    cols = np.asarray(pat.block_col_idx, np.int64)
-    off = np.concatenate([[0], np.cumsum(rb[rows] * cb[cols])])
-    values = np.asarray(values, np.float64)
-    # absolute row sums: every stored entry adds |h| to its scalar row
-    ent_block = np.repeat(np.arange(len(rows)), rb[rows] * cb[cols])
-    local = np.arange(off[-1]) - off[ent_block]
-    ent_row = r[rows[ent_block]] + local // cb[cols[ent_block]]
-    absrow = np.bincount(ent_row, weights=np.abs(values), minlength=N)
-    # diagonal entries: only blocks whose scalar row and column ranges overlap
-    diag = np.zeros(N)
-    for b in np.nonzero((r[rows] < c[cols] + cb[cols]) & (c[cols] < r[rows] + rb[rows]))[0]:
-        i, j = rows[b], cols[b]
-        blk = values[off[b]:off[b + 1]].reshape(rb[i], cb[j])
-        for p in range(rb[i]):
-            q = r[i] + p - c[j]
-            if 0 <= q < cb[j]:
-                diag[r[i] + p] += blk[p, q]
-    radius = absrow - np.abs(diag)
-    return float((diag - radius).min()), float((diag + radius).max())
+    off-diagonal absolute row sum (C loop, O(n_rows) memory)."""
+    keep, args = _pat(pat)
+    v, pv = _c(values, np.float64)
+    out = np.zeros(2)
+    if _load().oracle_gershgorin(*args, pv, out.ctypes.data):
+        raise MemoryError("oracle_gershgorin")
+    return float(out[0]), float(out[1])
 
 
 def cheb_scale(pat, values, pad: float = 1.01):
@@ -201,8 +183,9 @@ def cheb_scale(pat, values, pad: float = 1.01):
     return 0.5 * (hi + lo), pad * 0.5 * (hi - lo)
 
 
-def shift_scale_values(pat, values, c, d) -> np.ndarray:
-    """Packed values of H~ = (H - c I) / d (c subtracted on the scalar diagonal)."""
+def shift_scale_values(pat, values, c, d, inplace: bool = False) -> np.ndarray:
+    """Packed values of H~ = (H - c I) / d (c subtracted on the scalar diagonal);
+    with inplace=True the float64 array `values` itself is overwritten."""
     rb = np.asarray(pat.row_bsize, np.int64)
     cb = np.asarray(pat.col_bsize, np.int64)
     r = np.concatenate([[0], np.cumsum(rb)])
@@ -210,14 +193,15 @@ def shift_scale_values(pat, values, c, d) -> np.ndarray:
     rows = np.repeat(np.arange(len(rb)), np.diff(pat.block_row_ptr))
     cols = np.asarray(pat.block_col_idx, np.int64)
     off = np.concatenate([[0], np.cumsum(rb[rows] * cb[cols])])
-    out = np.array(values, dtype=np.float64, copy=True)
+    out = values if inplace else np.array(values, dtype=np.float64, copy=True)
     for b in np.nonzero((r[rows] < cc[cols] + cb[cols]) & (cc[cols] < r[rows] + rb[rows]))[0]:
         i, j = rows[b], cols[b]
         for p in range(rb[i]):
             q = r[i] + p - cc[j]
             if 0 <= q < cb[j]:
                 out[off[b] + p * cb[j] + q] -= c
-    return out / d
+    np.divide(out, d, out=out)
+    return out
 
 
 def chebyshev_vectors(pat, values_t, R, n_moments):
@@ -230,12 +214,19 @@ def chebyshev_vectors(pat, values_t, R, n_moments):
     return t
 
 
-def chebyshev_moments(pat, values_t, R, n_moments) -> np.ndarray:
+def chebyshev_moments(pat, values_t, R, n_moments, nthreads=1) -> np.ndarray:
     """mu_n = <R, t_n> / (N * n_vec) for n = 0 .. n_moments - 1 (stochastic
-    trace estimate of T_n(H~) / N, kernel polynomial method)."""
+    trace estimate of T_n(H~) / N, kernel polynomial method). Keeps only the
+    last two vectors of the recurrence."""
     R = np.asarray(R, dtype=np.float64)
-    t = chebyshev_vectors(pat, values_t, R, n_moments)
-    return np.array([float(np.sum(R * tn)) for tn in t]) / R.size
+    mu = [float(np.sum(R * R))]
+    if n_moments > 1:
+        prev, cur = R, spmm(pat, values_t, R, nthreads=nthreads)
+        mu.append(float(np.sum(R * cur)))
+        for n in range(1, n_moments - 1):
+            prev, cur = cur, spmm(pat, values_t, cur, alpha=2.0, beta=-1.0, Y=prev, nthreads=nthreads)
+            mu.append(float(np.sum(R * cur)))
+    return np.array(mu) / R.size
 
 
 def moment_loss(pat, values_t, R, n_moments) -> float:

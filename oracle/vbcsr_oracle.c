@@ -158,3 +158,45 @@ int oracle_sddmm(int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize, con
     free(r); free(cj); free(voff);
     return 0;
 }
+
+/*
+ * Gershgorin bounds over scalar rows of a square operator: every eigenvalue
+ * lies in [min_r (H_rr - R_r), max_r (H_rr + R_r)], R_r = sum_{c != r} |H_rc|.
+ * Writes out[0] = lower bound, out[1] = upper bound. Plain loops, O(nnz) time
+ * and O(n_rows) memory.
+ */
+int oracle_gershgorin(int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize, const int32_t *col_bsize,
+                      const int64_t *block_row_ptr, const int32_t *block_col_idx, const double *values,
+                      double *out) {
+    int64_t *r = prefix_sizes(n_brows, row_bsize);
+    int64_t *cj = prefix_sizes(n_bcols, col_bsize);
+    int64_t *voff = value_offsets(n_brows, row_bsize, col_bsize, block_row_ptr, block_col_idx);
+    if (!r || !cj || !voff) { free(r); free(cj); free(voff); return -1; }
+    double lo = 0.0, hi = 0.0;
+    int first = 1;
+    for (int64_t i = 0; i < n_brows; ++i) {
+        const int bi = row_bsize[i];
+        for (int p = 0; p < bi; ++p) {
+            const int64_t row = r[i] + p;
+            double diag = 0.0, off = 0.0;
+            for (int64_t b = block_row_ptr[i]; b < block_row_ptr[i + 1]; ++b) {
+                const int64_t j = block_col_idx[b];
+                const int bj = col_bsize[j];
+                const double *h = values + voff[b];
+                for (int q = 0; q < bj; ++q) {
+                    const double v = h[p * bj + q];
+                    if (cj[j] + q == row) diag += v;
+                    else off += v < 0 ? -v : v;
+                }
+            }
+            const double a = diag - off, c = diag + off;
+            if (first || a < lo) lo = a;
+            if (first || c > hi) hi = c;
+            first = 0;
+        }
+    }
+    out[0] = lo;
+    out[1] = hi;
+    free(r); free(cj); free(voff);
+    return 0;
+}

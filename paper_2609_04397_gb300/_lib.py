@@ -13,7 +13,7 @@ VBCSR_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "PATTERN", -3: "CUDA", -4: "NO_MEMORY",
           -5: "UNSUPPORTED", -6: "DEVICE_CHECK", -7: "ALIAS"}
 F64, F32 = 0, 1
-PRECISION = {"native": 0, "f32": 1, "tf32": 2, "tf32x3": 3, "bf16x2": 4}
+PRECISION = {"native": 0, "f32": 1, "tf32": 2, "tf32x3": 3, "bf16x2": 4, "df32": 5}
 
 # every function that include/vbcsr.h declares, with its ctypes signature
 _i64, _i32, _d, _p, _int = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
@@ -44,6 +44,8 @@ SIGNATURES = {
     "vbcsr_chebyshev": ([_p, _i64, _p, _i64, _i64, _p, _p, _p, _i64, _int, _p], _int),
     "vbcsr_chebyshev_backward": ([_p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _p, _int, _p], _int),
     "vbcsr_chebyshev_noalloc": ([_p, _i64, _p, _i64, _i64, _p, _int, _p], _int),
+    "vbcsr_gershgorin": ([_p, _p, _p], _int),
+    "vbcsr_shift_scale": ([_p, _d, _d, _p], _int),
     "vbcsr_get_info": ([_p, ctypes.POINTER(Info)], _int),
     "vbcsr_shape_classes": ([_p, _p, _p, _p, _i32], _int),
     "vbcsr_set_tuning": ([_p, _i32, _i32], _int),

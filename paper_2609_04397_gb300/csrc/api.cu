@@ -105,6 +105,12 @@ struct vbcsr_matrix {
     void *panel = nullptr;        // values in panels (dtype)
     float *panel32 = nullptr;     // FP32 copy for the mixed modes (FP64 operators), lazily built
     bool panel32_valid = false;
+    float *xconv = nullptr;       // FP32 copy of the current X for the mixed modes (grown on demand)
+    size_t xconv_elems = 0;
+    float2 *paneldf = nullptr;    // (hi, lo) FP32 pairs of the values for the double-FP32 mode
+    bool paneldf_valid = false;
+    float2 *xdf = nullptr;        // (hi, lo) pairs of the current X for the double-FP32 mode
+    size_t xdf_elems = 0;
     WorkItem *fwd_items = nullptr, *adj_items = nullptr;   // bucketed by row count
     WorkItem *fwd_lpt = nullptr, *adj_lpt = nullptr;       // all items, descending cost
     int64_t n_fwd_items = 0, n_adj_items = 0;
@@ -521,6 +527,33 @@ static int refresh_panel32(vbcsr_t *A, cudaStream_t s) {
     return VBCSR_OK;
 }
 
+static int refresh_paneldf(vbcsr_t *A, cudaStream_t s) {
+    if (!A->paneldf) CUDA_TRY(A->alloc(&A->paneldf, (size_t)A->panel_elems), "alloc double-FP32 value copy");
+    CUDA_TRY(launch_split_df(A->panel_elems, 1, (const double *)A->panel, 1, A->paneldf, s), "split values");
+    A->paneldf_valid = true;
+    return VBCSR_OK;
+}
+
+// Grow a handle-owned scratch buffer to at least `need` elements.
+template <typename T>
+static int grow(vbcsr_t *A, T **buf, size_t *have, size_t need, cudaStream_t s, const char *what) {
+    if (need <= *have) return VBCSR_OK;
+    if (*buf) {
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        for (auto &b : A->bufs)
+            if (b.p == (void *)*buf) {
+                cudaFree(b.p);
+                A->device_bytes -= (int64_t)b.bytes;
+                b.p = nullptr;
+            }
+        *buf = nullptr;
+        *have = 0;
+    }
+    CUDA_TRY(A->alloc(buf, need), what);
+    *have = need;
+    return VBCSR_OK;
+}
+
 extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (on_device != 0 && on_device != 1) return fail(VBCSR_ERR_INVALID_ARG, "on_device must be 0 or 1");
@@ -543,7 +576,11 @@ extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, v
         if (e2 != cudaSuccess) return cuda_fail(e2, "set_values");
     }
     if (e != cudaSuccess) return cuda_fail(e, "set_values");
-    if (A->panel32) return refresh_panel32(A, s);
+    if (A->panel32) {
+        int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+    if (A->paneldf) return refresh_paneldf(A, s);
     return VBCSR_OK;
 }
 
@@ -580,7 +617,8 @@ namespace vbcsr {
 const void *fma_f64_kernel(bool trans, bool persistent);
 const void *fma_f32_kernel(bool trans, bool persistent);
 const void *fma_f32_on_f64_kernel(bool trans, bool persistent);
-const void *mma_kernel_ptr(int mode, bool xdouble, bool trans);
+const void *fma_df_kernel(bool trans, bool persistent);
+const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int64_t k);
 }  // namespace vbcsr
 
 // True when the [rows, k] windows of two row-major panels share an element.
@@ -625,8 +663,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
                        double dot_scale = 1.0) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
-    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_BF16X2)
+    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
         return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+    if (precision == VBCSR_PREC_DF32 && A->dtype != VBCSR_F64)
+        return fail(VBCSR_ERR_UNSUPPORTED, "the double-FP32 mode needs an FP64 operator");
     const int64_t xrows = trans ? A->n_rows : A->n_cols;
     const int64_t yrows = trans ? A->n_cols : A->n_rows;
     const bool want_dot = epi && epi->dot_out;
@@ -646,14 +686,38 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const bool f64 = A->dtype == VBCSR_F64;
     int mode = precision;
     if (!f64 && mode == VBCSR_PREC_F32) mode = VBCSR_PREC_NATIVE;
-    if (f64 && mode != VBCSR_PREC_NATIVE && !A->panel32_valid) {
+    if (f64 && mode != VBCSR_PREC_NATIVE && mode != VBCSR_PREC_DF32 && !A->panel32_valid) {
         int rc = refresh_panel32(A, s);
         if (rc) return rc;
+    }
+    if (mode == VBCSR_PREC_DF32 && !A->paneldf_valid) {
+        int rc = refresh_paneldf(A, s);
+        if (rc) return rc;
+    }
+
+    // The mixed modes read X as FP32 (the double-FP32 mode as hi/lo pairs):
+    // convert an FP64 X once here rather than at every gather inside the
+    // kernel (each X row is gathered by ~30 work items).
+    if (f64 && mode != VBCSR_PREC_NATIVE && alpha != 0.0 && xrows > 0) {
+        const size_t need = (size_t)xrows * (size_t)k;
+        if (mode == VBCSR_PREC_DF32) {
+            int rc = grow(A, &A->xdf, &A->xdf_elems, need, s, "alloc double-FP32 copy of X");
+            if (rc) return rc;
+            CUDA_TRY(launch_split_df(xrows, k, (const double *)X, ldx, A->xdf, s), "split X");
+            X = A->xdf;
+        } else {
+            int rc = grow(A, &A->xconv, &A->xconv_elems, need, s, "alloc FP32 copy of X");
+            if (rc) return rc;
+            CUDA_TRY(launch_convert_panel_f64_to_f32(xrows, k, (const double *)X, ldx, A->xconv, s), "convert X");
+            X = A->xconv;
+        }
+        ldx = k;
     }
 
     ProdArgs a;
     memset(&a, 0, sizeof(a));
-    a.values = (f64 && mode != VBCSR_PREC_NATIVE) ? (const void *)A->panel32 : A->panel;
+    a.values = mode == VBCSR_PREC_DF32 ? (const void *)A->paneldf
+             : (f64 && mode != VBCSR_PREC_NATIVE) ? (const void *)A->panel32 : A->panel;
     a.fl = {A->fl_xrow, A->fl_pcol, A->fl_w};
     a.tl = {A->tl_pbase, A->tl_kp, A->tl_bi, A->tl_xrow, A->tl_vcol};
     a.k = k;
@@ -674,7 +738,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const int kc_auto = auto_kc(k);
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
-    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32);
+    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32 || mode == VBCSR_PREC_DF32);
     int64_t used = 0;
     // one launch of `kern` over items[0..n) with `warps` warps per CTA
     auto launch = [&](int B, const WorkItem *items, int64_t n, int warps, const void *kern, size_t smem) -> int {
@@ -698,12 +762,15 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             e = f64 ? launch_fma_f64(B, trans, a, s) : launch_fma_f32(B, trans, a, s);
         else if (mode == VBCSR_PREC_F32)
             e = launch_fma_f32_on_f64(B, trans, a, s);
+        else if (mode == VBCSR_PREC_DF32)
+            e = launch_fma_df(B, trans, a, s);
         else
             e = launch_mma(mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
         return VBCSR_OK;
     };
     auto fma_kern = [&](bool persistent) {
+        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent);
         return (mode == VBCSR_PREC_NATIVE) ? (f64 ? fma_f64_kernel(trans, persistent) : fma_f32_kernel(trans, persistent))
                                            : fma_f32_on_f64_kernel(trans, persistent);
     };
@@ -711,10 +778,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     int rc = VBCSR_OK;
     if (!fma) {
         // tensor-core kernel: the row count is a runtime mask, one launch serves every item
-        const void *kern = mma_kernel_ptr(mode, f64, trans);
+        const bool staged = !trans && (A->schedule & VBCSR_SCHED_MMA_STAGED);
+        a.mma_staged = staged ? 1 : 0;
+        const void *kern = mma_kernel_ptr(mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
-        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, 4));
-    } else if (A->schedule == 1) {
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
+    } else if (A->schedule & VBCSR_SCHED_PERSISTENT) {
         // persistent launch over every row count, items in descending cost from a work queue
         a.kc_log2_by_b = 0;
         for (int B = 1; B <= kMaxB; ++B) {
@@ -915,6 +984,34 @@ extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, 
     return VBCSR_OK;
 }
 
+extern "C" int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream) {
+    if (!A || !bounds) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
+    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "Gershgorin bounds need an FP64 operator");
+    if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
+    if (A->n_rows == 0) return fail(VBCSR_ERR_INVALID_ARG, "empty operator");
+    CUDA_TRY(launch_gershgorin(A->fwd_items, A->n_fwd_items, (const double *)A->panel, A->fl_xrow, A->fl_pcol,
+                               A->fl_w, A->partials, kPartialsCap, bounds, (cudaStream_t)stream),
+             "gershgorin");
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "shift/scale needs an FP64 operator");
+    if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
+    if (!(d != 0.0) || d != d || c != c) return fail(VBCSR_ERR_INVALID_ARG, "c = %g, d = %g", c, d);
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(launch_shift_scale(A->fwd_items, A->n_fwd_items, (double *)A->panel, A->fl_xrow, A->fl_pcol, A->fl_w, c,
+                                d, s),
+             "shift_scale");
+    if (A->panel32) {
+        int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+    if (A->paneldf) return refresh_paneldf(A, s);
+    return VBCSR_OK;
+}
+
 // ---------------------------------------------------------------------------
 // inspection and control
 
@@ -968,7 +1065,7 @@ extern "C" int vbcsr_set_bucket_tuning(vbcsr_t *A, int32_t B, int32_t kc, int32_
 
 extern "C" int vbcsr_set_schedule(vbcsr_t *A, int32_t schedule, int32_t persist_warps) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (schedule != VBCSR_SCHED_BUCKETED && schedule != VBCSR_SCHED_PERSISTENT)
+    if (schedule < 0 || schedule > (VBCSR_SCHED_PERSISTENT | VBCSR_SCHED_MMA_STAGED))
         return fail(VBCSR_ERR_INVALID_ARG, "schedule %d", schedule);
     if (!valid_warps(persist_warps)) return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", persist_warps);
     A->schedule = schedule;
@@ -1015,10 +1112,23 @@ extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (transpose != 0 && transpose != 1) return fail(VBCSR_ERR_INVALID_ARG, "transpose must be 0 or 1");
     if (k < 1) return fail(VBCSR_ERR_INVALID_ARG, "k must be >= 1");
-    if (precision != VBCSR_PREC_NATIVE && !(precision == VBCSR_PREC_F32 && A->dtype == VBCSR_F64)) {
-        // the tensor-core kernels have no per-row-count tile to choose
-        if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_BF16X2)
+    if (precision != VBCSR_PREC_NATIVE &&
+        !((precision == VBCSR_PREC_F32 || precision == VBCSR_PREC_DF32) && A->dtype == VBCSR_F64)) {
+        // tensor-core kernels: no per-row-count tile; choose the forward variant
+        if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
             return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+        if (transpose) return VBCSR_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int keep = A->schedule;
+        A->schedule = keep & ~VBCSR_SCHED_MMA_STAGED;
+        const double t_plain = time_product(A, false, k, X, ldx, Y, ldy, precision, s, 3);
+        A->schedule = keep | VBCSR_SCHED_MMA_STAGED;
+        const double t_staged = time_product(A, false, k, X, ldx, Y, ldy, precision, s, 3);
+        if (t_plain < 0 || t_staged < 0) {
+            A->schedule = keep;
+            return fail(VBCSR_ERR_CUDA, "autotune trial failed: %s", g_detail.c_str());
+        }
+        A->schedule = t_staged < t_plain ? (keep | VBCSR_SCHED_MMA_STAGED) : (keep & ~VBCSR_SCHED_MMA_STAGED);
         return VBCSR_OK;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -1029,7 +1139,8 @@ extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *
     const int kc_auto = auto_kc(k);
     // 1) per row count: the column tile and CTA width of its bucket launch
     const int saved_schedule = A->schedule;
-    A->schedule = VBCSR_SCHED_BUCKETED;
+    const int mma_bit = saved_schedule & VBCSR_SCHED_MMA_STAGED;
+    A->schedule = VBCSR_SCHED_BUCKETED | mma_bit;
     const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
     int keep_kc[kMaxB + 1], keep_w[kMaxB + 1];
     memcpy(keep_kc, A->kc_b, sizeof(keep_kc));
@@ -1062,14 +1173,14 @@ extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *
     int schedule = VBCSR_SCHED_BUCKETED, pw = 0;
     double best = t_bucketed;
     if (!(flags & VBCSR_TUNE_NO_PERSISTENT)) {
-        A->schedule = VBCSR_SCHED_PERSISTENT;
+        A->schedule = VBCSR_SCHED_PERSISTENT | mma_bit;
         for (int w : wss) {
             A->persist_warps = w;
             const double ms = time_product(A, trans, k, X, ldx, Y, ldy, precision, s, reps);
             if (ms >= 0 && ms < best) { best = ms; schedule = VBCSR_SCHED_PERSISTENT; pw = w; }
         }
     }
-    A->schedule = schedule;
+    A->schedule = schedule | mma_bit;
     A->persist_warps = pw;
     return VBCSR_OK;
 }

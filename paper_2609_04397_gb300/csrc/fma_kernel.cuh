@@ -102,14 +102,14 @@ __device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
     return v + __shfl_xor_sync(0xffffffffu, v, 1);
 }
 
-template <int B, bool TRANS, typename TV, typename TA, typename TX>
+template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI>
 __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &w, int KC, int32_t *s_x,
                                              int64_t *s_a, int lane, double &dot) {
     const int TG = 32 / KC;
     const int cl = lane % KC;
     const int tg = lane / KC;
     const TV *__restrict__ vals = static_cast<const TV *>(a.values);
-    const TX *__restrict__ X = static_cast<const TX *>(a.X);
+    const TXI *__restrict__ X = static_cast<const TXI *>(a.X);
     const bool do_prod = a.alpha != 0.0;
 
     for (int64_t c0 = 0; c0 < a.k; c0 += KC) {
@@ -123,6 +123,30 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
             for (int t0 = 0; t0 < w.K; t0 += kKMax) {
                 const int tn = min(kKMax, w.K - t0);
                 if (c0 == 0 || w.K > kKMax) stage_columns<TRANS>(a, w, t0, tn, s_x, s_a, lane);
+                if (!TRANS && sizeof(TV) == 4) {
+                    // FP32 values: four consecutive panel columns per lane and step, one
+                    // 16-byte load per row (rows start 32-byte aligned; Kp is a multiple
+                    // of 8, so the four columns never leave the row)
+                    for (int t = 4 * tg; t < tn; t += 4 * TG) {
+                        TA x[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int xr = (t + j < tn) ? s_x[t + j] : -1;
+                            x[j] = (cv && xr >= 0) ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
+                        }
+                        const TV *v = vals + w.vbase + t0 + t;
+                        const int64_t kp = w.Kp;
+#pragma unroll
+                        for (int p = 0; p < B; ++p) {
+                            const float4 q = __ldg(reinterpret_cast<const float4 *>(v + p * kp));
+                            acc[p] = fmat((TA)q.x, x[0], acc[p]);
+                            acc[p] = fmat((TA)q.y, x[1], acc[p]);
+                            acc[p] = fmat((TA)q.z, x[2], acc[p]);
+                            acc[p] = fmat((TA)q.w, x[3], acc[p]);
+                        }
+                    }
+                    continue;
+                }
                 for (int t = tg; t < tn; t += TG) {
                     const int xr = s_x[t];
                     if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
@@ -174,7 +198,7 @@ __device__ __forceinline__ void finish_dot(const ProdArgs &a, double dot, int wa
     }
 }
 
-template <int B, bool TRANS, typename TV, typename TA, typename TX>
+template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI>
 __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
@@ -186,7 +210,7 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     double dot = 0.0;
     for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        process_item<B, TRANS, TV, TA, TX>(a, w, a.kc, s_x, s_a, lane, dot);
+        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, lane, dot);
     }
     if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
@@ -195,7 +219,7 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
 // order (the planner sorts them by descending cost); warps take the next
 // item from a device counter (a.queue, zeroed before the launch) or, without
 // a queue, round-robin. a.kc_of(B) is the column tile of row count B.
-template <bool TRANS, typename TV, typename TA, typename TX>
+template <bool TRANS, typename TV, typename TA, typename TX, typename TXI>
 __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
         const WorkItem w = a.items[it];
         const int kc = a.kc_of(w.B);
 #define VBCSR_ITEM_CASE(NB) \
-    case NB: process_item<NB, TRANS, TV, TA, TX>(a, w, kc, s_x, s_a, lane, dot); break;
+    case NB: process_item<NB, TRANS, TV, TA, TX, TXI>(a, w, kc, s_x, s_a, lane, dot); break;
         switch (w.B) {
             VBCSR_ITEM_CASE(1) VBCSR_ITEM_CASE(2) VBCSR_ITEM_CASE(3) VBCSR_ITEM_CASE(4)
             VBCSR_ITEM_CASE(5) VBCSR_ITEM_CASE(6) VBCSR_ITEM_CASE(7) VBCSR_ITEM_CASE(8)
@@ -238,31 +262,31 @@ inline cudaError_t launch_smem_opt_in(K kernel, size_t smem) {
     return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 1024);
 }
 
-template <typename TV, typename TA, typename TX>
+template <typename TV, typename TA, typename TX, typename TXI>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s) {
     const int threads = a.warps * 32;
     const size_t smem = fma_smem_bytes(trans, a.warps);
     cudaError_t e;
     if (B == 0) {   // persistent launch over every row count
         if (trans) {
-            if ((e = launch_smem_opt_in(fma_persistent_kernel<true, TV, TA, TX>, smem)) != cudaSuccess) return e;
-            fma_persistent_kernel<true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+            if ((e = launch_smem_opt_in(fma_persistent_kernel<true, TV, TA, TX, TXI>, smem)) != cudaSuccess) return e;
+            fma_persistent_kernel<true, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);
         } else {
-            if ((e = launch_smem_opt_in(fma_persistent_kernel<false, TV, TA, TX>, smem)) != cudaSuccess) return e;
-            fma_persistent_kernel<false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);
+            if ((e = launch_smem_opt_in(fma_persistent_kernel<false, TV, TA, TX, TXI>, smem)) != cudaSuccess) return e;
+            fma_persistent_kernel<false, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);
         }
         return cudaGetLastError();
     }
 #define VBCSR_FMA_CASE(NB)                                                                               \
     case NB:                                                                                             \
         if (trans) {                                                                                     \
-            if ((e = launch_smem_opt_in(fma_product_kernel<NB, true, TV, TA, TX>, smem)) != cudaSuccess) \
+            if ((e = launch_smem_opt_in(fma_product_kernel<NB, true, TV, TA, TX, TXI>, smem)) != cudaSuccess) \
                 return e;                                                                                \
-            fma_product_kernel<NB, true, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);                   \
+            fma_product_kernel<NB, true, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);                   \
         } else {                                                                                         \
-            if ((e = launch_smem_opt_in(fma_product_kernel<NB, false, TV, TA, TX>, smem)) != cudaSuccess) \
+            if ((e = launch_smem_opt_in(fma_product_kernel<NB, false, TV, TA, TX, TXI>, smem)) != cudaSuccess) \
                 return e;                                                                                \
-            fma_product_kernel<NB, false, TV, TA, TX><<<a.grid, threads, smem, s>>>(a);                  \
+            fma_product_kernel<NB, false, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);                  \
         }                                                                                                \
         break;
     switch (B) {
@@ -276,14 +300,14 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
     return cudaGetLastError();
 }
 
-template <typename TV, typename TA, typename TX>
+template <typename TV, typename TA, typename TX, typename TXI>
 const void *fma_kernel_ptr(bool trans, bool persistent) {
     // B = 16 is the largest register footprint of the bucketed kernels
     if (persistent)
-        return trans ? (const void *)fma_persistent_kernel<true, TV, TA, TX>
-                     : (const void *)fma_persistent_kernel<false, TV, TA, TX>;
-    return trans ? (const void *)fma_product_kernel<16, true, TV, TA, TX>
-                 : (const void *)fma_product_kernel<16, false, TV, TA, TX>;
+        return trans ? (const void *)fma_persistent_kernel<true, TV, TA, TX, TXI>
+                     : (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;
+    return trans ? (const void *)fma_product_kernel<16, true, TV, TA, TX, TXI>
+                 : (const void *)fma_product_kernel<16, false, TV, TA, TX, TXI>;
 }
 
 }  // namespace vbcsr

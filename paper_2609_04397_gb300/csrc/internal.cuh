@@ -80,6 +80,7 @@ struct ProdArgs {
     // persistent launch only
     long long *queue;       // device work counter, zero at launch (NULL: round-robin)
     uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
+    int mma_staged;         // tensor-core forward: 1 = value panels staged in shared memory
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
@@ -90,6 +91,9 @@ struct ProdArgs {
 cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);
 cudaError_t launch_fma_f32(int B, bool trans, const ProdArgs &a, cudaStream_t s);
 cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+// double-FP32 arithmetic on (hi, lo) FP32 pairs of an FP64 operator and X, FP64 epilogue
+cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t ld, float2 *out, cudaStream_t s);
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
 
@@ -98,7 +102,7 @@ cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cu
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
 
 size_t fma_smem_bytes(bool trans, int warps);
-size_t mma_smem_bytes(bool trans, int warps);
+size_t mma_smem_bytes(bool trans, bool staged, int warps);
 
 // Misc kernels (misc.cu).
 struct SddmmArgs {
@@ -122,6 +126,9 @@ cudaError_t launch_permute_values(bool f64, bool to_panel, int64_t nblk, const i
                                   const int64_t *pbase, const int32_t *kp, const int32_t *bi,
                                   const int32_t *bj, const void *user, void *panel, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
+// out[rows, k] (leading dimension k) = FP32 of the FP64 panel in (leading dimension ld)
+cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
+                                            cudaStream_t s);
 // out[0] = scale * sum(partials[0..n)) in a fixed order
 cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out,
                                 cudaStream_t s);
@@ -132,6 +139,13 @@ cudaError_t launch_dot_panels(bool f64, int64_t rows, int64_t k, const void *A, 
 // Y = alpha X + beta Y on [rows, k] FP64 panels (beta == 0: Y not read)
 cudaError_t launch_axpby(int64_t rows, int64_t k, double alpha, const double *X, int64_t ldx, double beta,
                          double *Y, int64_t ldy, cudaStream_t s);
+// Gershgorin bounds over the forward items: out[0] = min, out[1] = max (device)
+cudaError_t launch_gershgorin(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
+                              const int32_t *pcol, const int32_t *wd, double *partials, int64_t cap, double *out,
+                              cudaStream_t s);
+// panel <- (panel - c I) / d in place
+cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+                               const int32_t *pcol, const int32_t *wd, double c, double d, cudaStream_t s);
 // dst[rows, k] (ld ldd) = src (ld lds), FP64
 cudaError_t launch_copy_panel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst,
                               int64_t ldd, cudaStream_t s);

@@ -124,6 +124,22 @@ cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, c
     return cudaGetLastError();
 }
 
+__global__ void convert_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, float *out) {
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        out[e] = (float)in[r * ld + c];
+    }
+}
+
+cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
+                                            cudaStream_t s) {
+    const int64_t need = (rows * k + 255) / 256;
+    if (need == 0) return cudaSuccess;
+    convert_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, in, ld, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // fixed-order reductions
 
@@ -212,6 +228,121 @@ cudaError_t launch_axpby(int64_t rows, int64_t k, double alpha, const double *X,
     int64_t need = (rows * k + 255) / 256;
     if (need == 0) return cudaSuccess;
     axpby_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, alpha, X, ldx, beta, Y, ldy);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gershgorin bounds and the shift/scale of the Chebyshev recurrence, both
+// walking the forward work items (every panel row exactly once). A panel
+// column t of a row r is on the scalar diagonal when its X row equals r.
+
+__device__ __forceinline__ void stage_x_rows(const WorkItem &w, const int32_t *xrow, const int32_t *pcol,
+                                             const int32_t *wd, int t0, int tn, int32_t *s_x, int lane) {
+    __syncwarp();
+    for (int e = lane; e < w.nlist; e += 32) {
+        const int64_t l = w.lbegin + e;
+        const int xr = xrow[l], pc = pcol[l], bw = wd[l];
+        const int lo = max(pc, t0), hi = min(pc + bw, t0 + tn);
+        for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
+    }
+    __syncwarp();
+}
+
+__global__ void gershgorin_kernel(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
+                                  const int32_t *pcol, const int32_t *wd, double *partials, int warps) {
+    extern __shared__ int32_t s_mem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *s_x = s_mem + warp * kKMax;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < n_items; it += (int64_t)gridDim.x * warps) {
+        const WorkItem w = items[it];
+        for (int p = 0; p < w.B; ++p) {
+            double off = 0.0, dg = 0.0;
+            for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+                const int tn = min(kKMax, w.K - t0);
+                if (p == 0 || w.K > kKMax) stage_x_rows(w, xrow, pcol, wd, t0, tn, s_x, lane);
+                for (int t = lane; t < tn; t += 32) {
+                    const double v = panel[w.vbase + (int64_t)p * w.Kp + t0 + t];
+                    if (s_x[t] == w.yrow + p) dg += v;
+                    else off += fabs(v);
+                }
+            }
+            for (int m = 16; m > 0; m >>= 1) {
+                off += __shfl_xor_sync(0xffffffffu, off, m);
+                dg += __shfl_xor_sync(0xffffffffu, dg, m);
+            }
+            lo = fmin(lo, dg - off);
+            hi = fmax(hi, dg + off);
+        }
+    }
+    __shared__ double s_lo[32], s_hi[32];
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < warps; ++i) {
+            lo = fmin(lo, s_lo[i]);
+            hi = fmax(hi, s_hi[i]);
+        }
+        partials[2 * blockIdx.x] = lo;
+        partials[2 * blockIdx.x + 1] = hi;
+    }
+}
+
+__global__ void minmax_finalize_kernel(const double *partials, int n, double *out) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+        lo = fmin(lo, partials[2 * i]);
+        hi = fmax(hi, partials[2 * i + 1]);
+    }
+    out[0] = lo;
+    out[1] = hi;
+}
+
+cudaError_t launch_gershgorin(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
+                              const int32_t *pcol, const int32_t *wd, double *partials, int64_t cap, double *out,
+                              cudaStream_t s) {
+    const int warps = 4;
+    int64_t need = (n_items + warps - 1) / warps;
+    int grid = (int)(need < cap / 2 ? (need > 0 ? need : 1) : cap / 2);
+    if (grid > 2048) grid = 2048;
+    gershgorin_kernel<<<grid, warps * 32, warps * kKMax * sizeof(int32_t), s>>>(items, n_items, panel, xrow, pcol,
+                                                                              wd, partials, warps);
+    minmax_finalize_kernel<<<1, 1, 0, s>>>(partials, grid, out);
+    return cudaGetLastError();
+}
+
+__global__ void shift_scale_kernel(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+                                   const int32_t *pcol, const int32_t *wd, double c, double d, int warps) {
+    extern __shared__ int32_t s_mem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *s_x = s_mem + warp * kKMax;
+    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < n_items; it += (int64_t)gridDim.x * warps) {
+        const WorkItem w = items[it];
+        for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+            const int tn = min(kKMax, w.K - t0);
+            stage_x_rows(w, xrow, pcol, wd, t0, tn, s_x, lane);
+            for (int p = 0; p < w.B; ++p)
+                for (int t = lane; t < tn; t += 32) {
+                    double *v = panel + w.vbase + (int64_t)p * w.Kp + t0 + t;
+                    double x = *v;
+                    if (s_x[t] == w.yrow + p) x -= c;
+                    *v = x / d;
+                }
+        }
+    }
+}
+
+cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+                               const int32_t *pcol, const int32_t *wd, double c, double d, cudaStream_t s) {
+    const int warps = 4;
+    int64_t need = (n_items + warps - 1) / warps;
+    if (need == 0) return cudaSuccess;
+    const int grid = (int)(need < 65536 ? need : 65536);
+    shift_scale_kernel<<<grid, warps * 32, warps * kKMax * sizeof(int32_t), s>>>(items, n_items, panel, xrow, pcol,
+                                                                               wd, c, d, warps);
     return cudaGetLastError();
 }
 

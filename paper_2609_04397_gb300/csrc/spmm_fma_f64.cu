@@ -4,11 +4,11 @@
 namespace vbcsr {
 
 cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s) {
-    return launch_fma_family<double, double, double>(B, trans, a, s);
+    return launch_fma_family<double, double, double, double>(B, trans, a, s);
 }
 
 const void *fma_f64_kernel(bool trans, bool persistent) {
-    return fma_kernel_ptr<double, double, double>(trans, persistent);
+    return fma_kernel_ptr<double, double, double, double>(trans, persistent);
 }
 
 }  // namespace vbcsr

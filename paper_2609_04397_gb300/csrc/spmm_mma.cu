@@ -1,6 +1,7 @@
 // Tensor-core block products for the mixed-precision modes (TF32, TF32X3,
 // BF16X2) on the FP32 copy of the values, with FP32 accumulation and the
-// epilogue (alpha, beta, gamma * Z, dot with R) in the panel dtype.
+// epilogue (alpha, beta, gamma * Z, dot with R) in the panel dtype. X is read
+// as FP32: an FP64 X is converted once per call before the launch.
 //
 // Work decomposition is that of the CUDA-core kernel (one warp per work item
 // of up to 16 output rows; virtual columns staged in shared memory). The item
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
     const float *__restrict__ vals = static_cast<const float *>(a.values);
-    const TX *__restrict__ X = static_cast<const TX *>(a.X);
+    const float *__restrict__ X = static_cast<const float *>(a.X);   // FP32 (converted before the launch)
     TX *__restrict__ Y = static_cast<TX *>(a.Y);
     const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
     const TX *__restrict__ R = static_cast<const TX *>(a.R);
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
                             float xv[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                xv[j] = (xr[j] >= 0 && col < a.k) ? (float)__ldg(X + (int64_t)xr[j] * a.ldx + col)
+                                xv[j] = (xr[j] >= 0 && col < a.k) ? __ldg(X + (int64_t)xr[j] * a.ldx + col)
                                                                  : 0.f;
                             Pieces px;
                             split4<MODE>(xv, px);
@@ -236,9 +237,304 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Forward product with the value panel staged in shared memory.
+//
+// The plain kernel above keeps about one 16-column step of loads in flight per
+// warp, which leaves the HBM pipe mostly idle. Here each warp copies its
+// item's panel in chunks of kStageCols columns (B row segments of up to
+// 512 bytes) into shared memory with bulk asynchronous copies that complete
+// on an mbarrier, two buffers deep: while one chunk feeds the tensor cores
+// the next chunk (of the same item, the next column pass, or the warp's next
+// item) is already on its way. Panel rows start 32-byte aligned and chunk
+// widths are multiples of 8 columns, so every copy is a multiple of 16 bytes
+// from a 16-byte aligned address. Waits are bounded: on timeout the kernel
+// records error code 2 in the handle's error word and the warp stops.
+
+constexpr int kStageCols = 64;
+constexpr int kStageLd = kStageCols + 16;      // padded row: rows g and g+1 fall on disjoint bank halves
+constexpr int kStageBuf = 16 * kStageLd;       // floats per buffer
+constexpr long long kWaitLimit = 1ll << 26;    // try_wait polls before a wait is declared failed
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int MODE, typename TX, int NT>
+__global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warps = a.warps;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    float *bufs = reinterpret_cast<float *>(smem_raw) + (size_t)warp * 2 * kStageBuf;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw + (size_t)warps * 2 * kStageBuf * sizeof(float)) +
+                   warp * kKMax;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)warps * 2 * kStageBuf * sizeof(float) +
+                                                  (size_t)warps * kKMax * sizeof(int32_t)) +
+                     warp * 2;
+    const float *__restrict__ vals = static_cast<const float *>(a.values);
+    const float *__restrict__ X = static_cast<const float *>(a.X);
+    TX *__restrict__ Y = static_cast<TX *>(a.Y);
+    const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
+    const TX *__restrict__ R = static_cast<const TX *>(a.R);
+    const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
+    const bool do_prod = a.alpha != 0.0;
+    const int64_t stride = (int64_t)gridDim.x * warps;
+    const int64_t npass = (a.k + 8 * NT - 1) / (8 * NT);
+    double dot = 0.0;
+
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
+    // a stage is (item, column pass, chunk); the warp walks its stages in order
+    struct Stage {
+        int64_t it, pass;
+        int c;
+    };
+    auto nchunks = [](const WorkItem &w) { return w.Kp > 0 ? (w.Kp + kStageCols - 1) / kStageCols : 1; };
+    auto issue = [&](const Stage &st, const WorkItem &w, int b) {
+        const int col0 = st.c * kStageCols;
+        const int ncol = max(0, min(kStageCols, w.Kp - col0));
+        float *dst = bufs + b * kStageBuf;
+        if (lane == 0) {
+            if (ncol > 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive_expect(&bars[b], (uint32_t)(w.B * ncol * sizeof(float)));
+            } else {
+                mbar_arrive(&bars[b]);
+            }
+        }
+        __syncwarp();
+        if (ncol > 0 && lane < w.B)
+            bulk_copy_g2s(dst + lane * kStageLd, vals + w.vbase + (int64_t)lane * w.Kp + col0,
+                          (uint32_t)(ncol * sizeof(float)), &bars[b]);
+    };
+
+    uint32_t phase[2] = {0u, 0u};
+    Stage cur{(int64_t)blockIdx.x * warps + warp, 0, 0};
+    if (!do_prod) {
+        // alpha == 0: no product, only Y = beta Y (+ gamma Z)
+        for (int64_t it = cur.it; it < a.n_items; it += stride) {
+            const WorkItem w = a.items[it];
+            for (int64_t col = lane; col < (int64_t)w.B * a.k; col += 32) {
+                const int64_t row = w.yrow + col / a.k, c = col % a.k;
+                TX v = (TX)0;
+                if (a.beta != 0.0) v += beta * Y[row * a.ldy + c];
+                if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + c];
+                Y[row * a.ldy + c] = v;
+                if (a.partials) dot += (double)R[row * a.ldr + c] * (double)v;
+            }
+        }
+    } else if (cur.it < a.n_items) {
+        WorkItem wc = a.items[cur.it];
+        int b = 0;
+        issue(cur, wc, b);
+        float acc[NT][4];
+        bool failed = false;
+        for (;;) {
+            // successor stage
+            Stage nx = cur;
+            WorkItem wn = wc;
+            bool have_next = true;
+            if (cur.c + 1 < nchunks(wc)) {
+                nx.c = cur.c + 1;
+            } else if (cur.pass + 1 < npass) {
+                nx.pass = cur.pass + 1;
+                nx.c = 0;
+            } else {
+                nx.it = cur.it + stride;
+                nx.pass = 0;
+                nx.c = 0;
+                have_next = nx.it < a.n_items;
+                if (have_next) wn = a.items[nx.it];
+            }
+            if (have_next) issue(nx, wn, b ^ 1);
+
+            // consume the current stage
+            const int col0 = cur.c * kStageCols;
+            const int ncol = max(0, min(kStageCols, wc.Kp - col0));
+            const int64_t n0 = cur.pass * 8 * NT;
+            if (cur.c == 0) {
+#pragma unroll
+                for (int n = 0; n < NT; ++n)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[n][j] = 0.f;
+            }
+            // X rows of this chunk's columns: staged per kKMax window
+            const int win0 = (col0 / kKMax) * kKMax;
+            const int wn_cols = min(kKMax, wc.K - win0);
+            if (col0 % kKMax == 0 && wn_cols > 0) {
+                __syncwarp();
+                for (int e = lane; e < wc.nlist; e += 32) {
+                    const int64_t l = wc.lbegin + e;
+                    const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
+                    const int lo = max(pc, win0), hi = min(pc + wd, win0 + wn_cols);
+                    for (int t = lo; t < hi; ++t) s_x[t - win0] = xr + (t - pc);
+                }
+                __syncwarp();
+            }
+            if (!mbar_wait(&bars[b], phase[b])) {
+                failed = true;
+                break;
+            }
+            phase[b] ^= 1u;
+            const float *buf = bufs + b * kStageBuf;
+            // X values of a 16-column step: lane holds columns 4t..4t+3 of the step for
+            // output columns n0 + 8n + g; the next step's are loaded before this step's MMAs
+            auto load_x = [&](int c16, float (&xv)[NT][4]) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int cl = c16 + 4 * t4 + j;
+                    const int t = col0 + cl;
+                    const int xr = (cl < ncol && t < wc.K) ? s_x[t - win0] : -1;
+#pragma unroll
+                    for (int n = 0; n < NT; ++n) {
+                        const int64_t col = n0 + n * 8 + g;
+                        xv[n][j] = (xr >= 0 && col < a.k) ? __ldg(X + (int64_t)xr * a.ldx + col) : 0.f;
+                    }
+                }
+            };
+            float xnext[NT][4];
+            if (ncol > 0) load_x(0, xnext);
+            for (int c16 = 0; c16 < ncol; c16 += 16) {
+                float xcur[NT][4];
+#pragma unroll
+                for (int n = 0; n < NT; ++n)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) xcur[n][j] = xnext[n][j];
+                if (c16 + 16 < ncol) load_x(c16 + 16, xnext);
+                const int cl = c16 + 4 * t4;                 // chunk-relative first column of this lane
+                float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
+                if (cl < ncol) {                              // ncol is a multiple of 8: all four are inside
+                    if (g < wc.B) {
+                        const float4 q = *reinterpret_cast<const float4 *>(buf + g * kStageLd + cl);
+                        va[0] = q.x; va[1] = q.y; va[2] = q.z; va[3] = q.w;
+                    }
+                    if (g + 8 < wc.B) {
+                        const float4 q = *reinterpret_cast<const float4 *>(buf + (g + 8) * kStageLd + cl);
+                        vb[0] = q.x; vb[1] = q.y; vb[2] = q.z; vb[3] = q.w;
+                    }
+                }
+                Pieces pa, pb;
+                split4<MODE>(va, pa);
+                split4<MODE>(vb, pb);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    Pieces px;
+                    split4<MODE>(xcur[n], px);
+                    step<MODE>(acc[n], pa, pb, px);
+                }
+            }
+            __syncwarp();   // every lane is done with buffer b before it is refilled
+
+            if (cur.c + 1 == nchunks(wc)) {
+                // epilogue of (item, pass): acc[n] = {(g,2t),(g,2t+1),(g+8,2t),(g+8,2t+1)} of tile n
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int r = g + ((j >> 1) << 3);
+                        const int64_t col = n0 + n * 8 + 2 * t4 + (j & 1);
+                        if (r < wc.B && col < a.k) {
+                            const int64_t row = wc.yrow + r;
+                            TX *yp = Y + row * a.ldy + col;
+                            TX v = alpha * (TX)acc[n][j];
+                            if (a.beta != 0.0) v += beta * *yp;
+                            if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
+                            *yp = v;
+                            if (a.partials) dot += (double)R[row * a.ldr + col] * (double)v;
+                        }
+                    }
+                }
+            }
+            if (!have_next) break;
+            cur = nx;
+            wc = wn;
+            b ^= 1;
+        }
+        if (failed) {
+            if (lane == 0) atomicExch(a.err, 2);
+            // let copies already issued into either buffer land before the CTA exits
+            mbar_wait(&bars[0], phase[0]);
+            mbar_wait(&bars[1], phase[1]);
+        }
+    }
+
+    if (a.partials) {
+        for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+        __shared__ double s_dot[32];
+        __syncthreads();
+        if (lane == 0) s_dot[warp] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int i = 0; i < warps; ++i) sum += s_dot[i];
+            a.partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+size_t staged_smem_bytes(int warps) {
+    return (size_t)warps * (2 * kStageBuf * sizeof(float) + kKMax * sizeof(int32_t) + 2 * sizeof(uint64_t));
+}
+
+template <typename K>
+cudaError_t staged_launch(K kernel, const ProdArgs &a, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<a.grid, a.warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool TRANS, typename TX>
 cudaError_t launch_nt(const ProdArgs &a, cudaStream_t s) {
-    const size_t smem = mma_smem_bytes(TRANS, a.warps);
+    if (!TRANS && a.mma_staged) {
+        const size_t smem = staged_smem_bytes(a.warps);
+        if (a.k <= 8) return staged_launch(mma_staged_kernel<MODE, TX, 1>, a, smem, s);
+        if (a.k <= 16) return staged_launch(mma_staged_kernel<MODE, TX, 2>, a, smem, s);
+        return staged_launch(mma_staged_kernel<MODE, TX, 4>, a, smem, s);
+    }
+    const size_t smem = mma_smem_bytes(TRANS, false, a.warps);
     const int threads = a.warps * 32;
     if (a.k <= 8) mma_product_kernel<MODE, TRANS, TX, 1><<<a.grid, threads, smem, s>>>(a);
     else if (a.k <= 16) mma_product_kernel<MODE, TRANS, TX, 2><<<a.grid, threads, smem, s>>>(a);
@@ -254,22 +550,33 @@ cudaError_t launch_mode(bool xdouble, bool trans, const ProdArgs &a, cudaStream_
 
 }  // namespace
 
-size_t mma_smem_bytes(bool trans, int warps) {
+size_t mma_smem_bytes(bool trans, bool staged, int warps) {
+    if (!trans && staged) return staged_smem_bytes(warps);
     return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0));
 }
 
-const void *mma_kernel_ptr(int mode, bool xdouble, bool trans) {
-#define VBCSR_PTR(M)                                                                                  \
-    if (mode == M) {                                                                                  \
-        if (xdouble) return trans ? (const void *)mma_product_kernel<M, true, double, 4>              \
-                                  : (const void *)mma_product_kernel<M, false, double, 4>;            \
-        return trans ? (const void *)mma_product_kernel<M, true, float, 4>                            \
-                     : (const void *)mma_product_kernel<M, false, float, 4>;                          \
+// The kernel a launch of (mode, X/Y type, direction, variant, k) runs; used to size its grid.
+const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int64_t k) {
+    const int nt = k <= 8 ? 1 : (k <= 16 ? 2 : 4);
+#define VBCSR_PTR_NT(M, TX, NT)                                                                   \
+    if (nt == NT) {                                                                               \
+        if (trans) return (const void *)mma_product_kernel<M, true, TX, NT>;                      \
+        if (staged) return (const void *)mma_staged_kernel<M, TX, NT>;                            \
+        return (const void *)mma_product_kernel<M, false, TX, NT>;                                \
+    }
+#define VBCSR_PTR(M)                                                                              \
+    if (mode == M) {                                                                              \
+        if (xdouble) {                                                                            \
+            VBCSR_PTR_NT(M, double, 1) VBCSR_PTR_NT(M, double, 2) VBCSR_PTR_NT(M, double, 4)      \
+        } else {                                                                                  \
+            VBCSR_PTR_NT(M, float, 1) VBCSR_PTR_NT(M, float, 2) VBCSR_PTR_NT(M, float, 4)         \
+        }                                                                                         \
     }
     VBCSR_PTR(kTF32)
     VBCSR_PTR(kTF32X3)
     VBCSR_PTR(kBF16X2)
 #undef VBCSR_PTR
+#undef VBCSR_PTR_NT
     return nullptr;
 }
 

@@ -144,9 +144,10 @@ class VBCSR:
         """Column tile and CTA width of the bucket of row count B (0: all)."""
         check(lib().vbcsr_set_bucket_tuning(self._h, B, kc, warps), "vbcsr_set_bucket_tuning")
 
-    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0):
-        """'bucketed' (one launch per row count) or 'persistent' (one launch)."""
-        code = {"bucketed": 0, "persistent": 1}[schedule]
+    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0, mma_staged: bool = False):
+        """'bucketed' (one launch per row count) or 'persistent' (one launch);
+        mma_staged selects the shared-memory-staged tensor-core forward kernel."""
+        code = {"bucketed": 0, "persistent": 1}[schedule] | (2 if mma_staged else 0)
         check(lib().vbcsr_set_schedule(self._h, code, persist_warps), "vbcsr_set_schedule")
 
     def get_tuning(self) -> dict:
@@ -157,12 +158,13 @@ class VBCSR:
         check(lib().vbcsr_get_tuning(self._h, kc.ctypes.data, w.ctypes.data, ctypes.byref(sch),
                                      ctypes.byref(pw)), "vbcsr_get_tuning")
         return {"kc_by_b": kc.tolist(), "warps_by_b": w.tolist(),
-                "schedule": ["bucketed", "persistent"][sch.value], "persist_warps": pw.value}
+                "schedule": ["bucketed", "persistent"][sch.value & 1], "mma_staged": bool(sch.value & 2),
+                "persist_warps": pw.value}
 
     def apply_tuning(self, t: dict):
         for B in range(1, 17):
             self.set_tuning(t["kc_by_b"][B], t["warps_by_b"][B], B)
-        self.set_schedule(t["schedule"], t["persist_warps"])
+        self.set_schedule(t["schedule"], t["persist_warps"], t.get("mma_staged", False))
 
     def autotune(self, k: int, precision="native", transpose: bool = False, allow_persistent: bool = True,
                  cache: Optional[str] = None) -> dict:
@@ -312,6 +314,18 @@ class VBCSR:
                                     ctypes.c_void_p(ck.data_ptr() if ck is not None else None),
                                     ckpt_every, _prec(precision), _stream(self.device)), "vbcsr_chebyshev")
         return mom, ck
+
+    def gershgorin(self):
+        """(E_min, E_max): Gershgorin bounds of the spectrum, computed on the GPU."""
+        out = torch.empty(2, dtype=torch.float64, device=self.device)
+        check(lib().vbcsr_gershgorin(self._h, ctypes.c_void_p(out.data_ptr()), _stream(self.device)),
+              "vbcsr_gershgorin")
+        lo, hi = out.tolist()
+        return lo, hi
+
+    def shift_scale(self, c: float, d: float):
+        """Values <- (H - c I) / d in place."""
+        check(lib().vbcsr_shift_scale(self._h, float(c), float(d), _stream(self.device)), "vbcsr_shift_scale")
 
     def __matmul__(self, X):
         return self.spmm(X)

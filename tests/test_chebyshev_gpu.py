@@ -50,6 +50,17 @@ def test_mixed_precision_moments(mode):
     assert err.max() <= 1e-5, err.max()
 
 
+def test_df32_moments_fp64_accurate():
+    """Double-FP32 block products inside the FP64 recurrence: moments within
+    the FP64 moment tolerance."""
+    w = syn.tiny_multispecies(0)
+    H, vt, c, d = _setup(w)
+    R = syn.rademacher_panel(w.pattern.n_rows, 16, 0)
+    mom, _ = H.chebyshev(torch.from_numpy(R).cuda(), 51, precision="df32")
+    ref = oracle.chebyshev_moments(w.pattern, vt, R, 51)
+    assert np.abs(mom.cpu().numpy() - ref).max() <= 1e-12
+
+
 def _grad_case(n_atoms, k, M, E, seed=0):
     side = 60.0 * (n_atoms / 20000) ** (1 / 3)
     w = syn.amorphous(n=n_atoms, side=side, seed=seed)
@@ -163,3 +174,22 @@ def test_amorphous_20k_gradient_fd_50_entries():
     worst = np.abs(fd - g[idx]).max() / np.abs(g[idx]).max()
     print(f"amorphous 20k: max-norm relative FD deviation over 50 entries = {worst:.3e}")
     assert worst <= 1e-6
+
+
+def test_gershgorin_and_shift_scale_on_gpu():
+    from paper_2609_04397_gb300 import VBCSR
+    w = syn.amorphous(n=500, side=60.0 * (500 / 20000) ** (1 / 3), seed=3)
+    H = VBCSR.from_pattern(w.pattern, w.values, torch.float64, "cuda:0")
+    lo, hi = H.gershgorin()
+    rlo, rhi = oracle.gershgorin_bounds(w.pattern, w.values)
+    assert abs(lo - rlo) <= 1e-13 * abs(rlo) and abs(hi - rhi) <= 1e-13 * abs(rhi)
+    c, d = 0.5 * (hi + lo), 1.01 * 0.5 * (hi - lo)
+    H.spmm(torch.ones(w.pattern.n_cols, 2, dtype=torch.float64, device="cuda:0"), precision="bf16x2")
+    H.shift_scale(c, d)
+    ref = oracle.shift_scale_values(w.pattern, w.values, c, d)
+    assert np.array_equal(H.get_values().cpu().numpy(), ref)
+    # the mixed-precision copy follows the new values
+    X = np.random.default_rng(0).standard_normal((w.pattern.n_cols, 3))
+    got = H.spmm(torch.from_numpy(X).cuda(), precision="bf16x2").cpu().numpy()
+    refy = oracle.spmm(w.pattern, ref, X)
+    assert np.linalg.norm(got - refy) <= 1e-5 * np.linalg.norm(refy)

@@ -96,3 +96,36 @@ def test_mixed_copy_follows_set_values():
     got = H.spmm(_dev(X), precision="bf16x2").cpu().numpy()
     ref, _ = forward_ref(pat, v2, X, 1.0, 0.0, None)
     assert rel_fro(got, ref) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("mode", ["tf32", "tf32x3", "bf16x2"])
+@pytest.mark.parametrize("k", [1, 8, 16, 40])
+def test_staged_forward_kernel_matches_plain(mode, k):
+    """The shared-memory-staged tensor-core forward kernel computes the same
+    products as the plain one (same fragments, same summation order), incl.
+    wide panels that span several stages and rows of every height."""
+    pat = syn.random_pattern(45, 45, (1, 4, 9, 13, 16, 20, 70), 0.2, 40 + k, empty_rows=3, unsorted=True)
+    vals = syn.random_values(pat, 40 + k)
+    H = _handle(pat, vals)
+    X = _dev(np.random.default_rng(k).standard_normal((pat.n_cols, k)))
+    Y0 = _dev(np.random.default_rng(k + 1).standard_normal((pat.n_rows, k)))
+    Yp = Y0.clone()
+    H.spmm(X, 2.0, -1.0, Yp, precision=mode)
+    H.set_schedule("bucketed", mma_staged=True)
+    Ys = Y0.clone()
+    H.spmm(X, 2.0, -1.0, Ys, precision=mode)
+    assert torch.equal(Yp, Ys)
+    if mode != "tf32":
+        ref, scale = forward_ref(pat, vals, X.cpu().numpy(), 2.0, -1.0, Y0.cpu().numpy())
+        assert rel_fro(Ys.cpu().numpy(), ref) <= TOL_MIXED
+
+
+def test_autotune_picks_a_tensor_core_variant():
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    t = H.autotune(8, precision="bf16x2")
+    assert isinstance(t["mma_staged"], bool)
+    X = syn.normal_panel(w.pattern.n_cols, 8, 0)
+    got = H.spmm(_dev(X), precision="bf16x2").cpu().numpy()
+    ref, _ = forward_ref(w.pattern, w.values, X, 1.0, 0.0, None)
+    assert rel_fro(got, ref) <= TOL_MIXED

@@ -249,3 +249,15 @@ def test_moment_loss_gradient_central_differences():
         vm[i] -= h
         fd = (oracle.moment_loss(pat, vp, R, M) - oracle.moment_loss(pat, vm, R, M)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i]))
+
+
+def test_gershgorin_matches_dense_definition():
+    """Bounds from the dense matrix: min/max of H_rr -/+ sum_{c != r} |H_rc|."""
+    pat = syn.random_pattern(15, 15, (1, 3, 4), 0.3, 31)
+    pat = BlockPattern(pat.row_bsize, pat.row_bsize, pat.block_row_ptr, pat.block_col_idx)
+    v = syn.random_values(pat, 31)
+    H = oracle.to_dense(pat, v)
+    d = np.diag(H)
+    rad = np.abs(H).sum(axis=1) - np.abs(d)
+    lo, hi = oracle.gershgorin_bounds(pat, v)
+    assert abs(lo - (d - rad).min()) < 1e-13 and abs(hi - (d + rad).max()) < 1e-13

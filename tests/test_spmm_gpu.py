@@ -244,3 +244,34 @@ def test_fused_epilogue_gamma_z_and_dot(transpose):
     got = Yd.cpu().numpy()
     assert rel_fro(got, ref) <= TOL_F64
     assert abs(dot.item() - np.sum(R * ref)) <= 1e-12 * np.sum(np.abs(R * ref))
+
+
+@pytest.mark.parametrize("sizes", SIZES)
+@pytest.mark.parametrize("k", [1, 8, 33])
+def test_df32_mode_meets_fp64_tolerance(sizes, k):
+    """FP64 operands in double-FP32 arithmetic: held to the FP64 tolerance."""
+    seed = 7 + k
+    pat = syn.random_pattern(37, 29, sizes, 0.15, seed, empty_rows=3, unsorted=True)
+    vals = syn.random_values(pat, seed)
+    H = _handle(pat, vals)
+    for alpha, beta in ((1.0, 0.0), (2.0, -1.0)):
+        _run_forward(H, pat, vals, k, alpha, beta, ld_extra=1, seed=seed, precision="df32")
+        X = np.random.default_rng(seed).standard_normal((pat.n_rows, k))
+        got = H.spmm_adjoint(_dev(X), precision="df32").cpu().numpy()
+        ref, scale = adjoint_ref(pat, vals, X, 1.0, 0.0, None)
+        assert rel_fro(got, ref) <= TOL_F64
+        check_elementwise(got, ref, scale, TOL_F64)
+
+
+def test_df32_mode_zincblende_sampled_rows():
+    w = syn.zincblende(8000)
+    pat = w.pattern
+    H = _handle(pat, w.values)
+    X = syn.normal_panel(pat.n_cols, 16, 0)
+    got = H.spmm(_dev(X), precision="df32").cpu().numpy()
+    ref, scale = forward_ref(pat, w.values, X, 1.0, 0.0, None)
+    assert rel_fro(got, ref) <= TOL_F64
+    check_elementwise(got, ref, scale, TOL_F64)
+    # and the FP32 copy is not what it used: the plain FP32 mode is far less accurate
+    got32 = H.spmm(_dev(X), precision="f32").cpu().numpy()
+    assert rel_fro(got32, ref) > 100 * rel_fro(got, ref)
