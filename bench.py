@@ -47,6 +47,12 @@ FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_GHZ = 152, 2, 2.07
 FP64_PEAK_TFLOPS = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 
 
+# DRAM bytes (read + write) of one FP64 k = 32 product on this workload, from
+# one ncu capture of its two launches (row heights 9 and 13); see
+# profiles/fma_product_f64_zincblende50k.md. Algorithmic bytes are 1.62 GB.
+TRAFFIC_F64_K32 = 806001408 + 54032384 + 1060621568 + 76182784
+
+
 def _workload():
     import synthetic as syn
     return syn.zincblende(N_ATOMS, seed=0)
@@ -228,6 +234,60 @@ def batched_section(dev, steps):
             "gflops_graph": flops / (t_graph / 1e3) / 1e9, "matches_separate": same}
 
 
+def domains_section(dev, steps):
+    """The three structural domains of the paper's kernel benchmark (Sec. IV),
+    ~500 MiB each, FP64: SpMV (k = 1) and SpMM (k = 16) GFLOP/s and GB/s of
+    every backend (and of the block-row kernels on the scalar domain)."""
+    import torch
+    import synthetic as syn
+    from paper_2609_04397_gb300 import VBCSR
+    out = {}
+    hbm, _ = _peaks()
+    for kind in ("csr", "bsr", "vbcsr"):
+        w = syn.domain(kind)
+        pat = w.pattern
+        H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
+        res = {"atoms": pat.n_brows, "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk,
+               "value_bytes": 8 * pat.nnz, "backend": H.backend}
+        # default schedule; the block-row kernels on the scalar domain; one
+        # persistent launch and the autotuned choice on the block domains
+        variants = [("", {})]
+        if kind == "csr":
+            variants.append(("_blockrow", {"scalar_kernel": False}))
+        else:
+            variants += [("_persistent", {"schedule": "persistent"}), ("_tuned", None)]
+        for tag, sched in variants:
+            if sched is not None:
+                sched = dict(sched)
+                H.set_schedule(sched.pop("schedule", "bucketed"), **sched)
+            for k in (1, 16):
+                for prec in ("native", "df32"):
+                    X = torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev)
+                    Y = torch.empty(pat.n_rows, k, dtype=torch.float64, device=dev)
+                    if sched is None:
+                        H.set_schedule("bucketed")
+                        H.autotune(k, precision=prec)
+                    for _ in range(3):
+                        H.spmm(X, 1.0, 0.0, Y, precision=prec)
+                    torch.cuda.synchronize(dev)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    reps = max(5, steps // 5)
+                    a.record()
+                    for _ in range(reps):
+                        H.spmm(X, 1.0, 0.0, Y, precision=prec)
+                    b.record()
+                    torch.cuda.synchronize(dev)
+                    ms = a.elapsed_time(b) / reps
+                    by = _alg_bytes(pat, k)
+                    res[f"k{k}_{prec}{tag}"] = {"ms": ms, "gflops": 2.0 * pat.nnz * k / ms / 1e6,
+                                                "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm}
+        out[kind] = res
+        del H, w
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
     world, rank, _ = _dist()
@@ -333,7 +393,8 @@ def run_ours(args):
     fl_dom = 2.0 * pat.nnz * kdom
     by_dom = _alg_bytes(pat, kdom)
     roofline = {"bound": "alu", "achieved": fl_dom / t_dom / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": fl_dom / t_dom / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": fl_dom / t_dom / 1e12 / FP64_PEAK_TFLOPS,
+                "traffic": TRAFFIC_F64_K32 if kdom == 32 else None, "algorithmic_bytes": by_dom,
                 "kernel": f"fma_product_kernel<B, false, double, double, double>, k = {kdom}",
                 "peak_source": "unit counts x clock (152 SM x 2 FP64 FMA/clk x 2.07 GHz)",
                 "hbm_gbs": by_dom / t_dom / 1e9, "hbm_frac": by_dom / t_dom / 1e9 / hbm_peak,
@@ -357,16 +418,31 @@ def run_ours(args):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         reps = max(5, args.steps // 4)
+        kev = {k: [] for k in KS}
         a.record(stream)
         for _ in range(reps):
             for k in KS:
+                ka = torch.cuda.Event(enable_timing=True)
+                kb = torch.cuda.Event(enable_timing=True)
+                ka.record(stream)
                 H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
+                kb.record(stream)
+                kev[k].append((ka, kb))
         b.record(stream)
         torch.cuda.synchronize(dev)
         ms = a.elapsed_time(b) / reps
+        # the mixed modes stream a 4-byte copy of the values; X is converted
+        # (DF32: split) once per call inside the timed call
+        vb = 8 if mode == "df32" else 4
+        mk = {}
+        for k in KS:
+            t = sum(x.elapsed_time(y) for x, y in kev[k]) / reps
+            mk[str(k)] = {"ms": t, "gbs": _alg_bytes(pat, k, vb) / (t / 1e3) / 1e9,
+                          "hbm_frac": _alg_bytes(pat, k, vb) / (t / 1e3) / 1e9 / hbm_peak,
+                          "speedup_vs_f64": per_k_ms[k] / t}
         mixed[mode + ("_staged" if staged else "")] = {
             "ms_per_step": ms, "speedup_vs_f64": (total_ms / args.steps) / ms,
-            "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9}
+            "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9, "per_k": mk}
     H.set_schedule("bucketed")
 
     # ---- end to end through the public API: pinned host X in, Y out, every step ----
@@ -396,6 +472,7 @@ def run_ours(args):
            "d2h_bytes_per_step": int(sum(8 * pat.n_rows * k for k in KS)), "ms_per_step": e2e_ms}
 
     batched = batched_section(dev, args.steps) if not args.no_batched else None
+    domains = domains_section(dev, args.steps) if args.domains else None
     H.check()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -405,6 +482,7 @@ def run_ours(args):
                        "alpha": 1.0, "beta": 0.0, "parallelism": f"replicas x{world}",
                        "l2": "no flush: inputs larger than L2 (1.33 GB of values per product)"},
             "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
+            **({"domains": domains} if domains is not None else {}),
             "gpu_launches": n_buckets * len(KS) * args.steps, "clocks": clocks}
     if rank == 0:
         if not args.no_cpu_baseline:
@@ -424,6 +502,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--domains", action="store_true",
+                    help="also measure the CSR / BSR / VBCSR domains (~500 MiB each)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -89,8 +89,10 @@ typedef enum {
     VBCSR_SCHED_BUCKETED = 0,     /* one launch per work-item row count (default)      */
     VBCSR_SCHED_PERSISTENT = 1,   /* one launch over all items, costliest first, warps
                                      taking items from a device work counter           */
-    VBCSR_SCHED_MMA_STAGED = 2    /* flag: the tensor-core forward kernel stages value
+    VBCSR_SCHED_MMA_STAGED = 2,   /* flag: the tensor-core forward kernel stages value
                                      panels in shared memory with bulk async copies   */
+    VBCSR_SCHED_NO_CSR = 4        /* flag: a CSR-backend operator uses the block-row
+                                     kernels instead of the scalar kernel             */
 } vbcsr_schedule;
 
 /* Flags of vbcsr_autotune. */
@@ -107,7 +109,25 @@ typedef struct {
     int32_t n_shape_classes;      /* distinct (b_i, b_j) pairs among stored blocks   */
     int32_t n_row_classes;        /* distinct work heights used by the forward plan  */
     int32_t n_structs;            /* independent structures (1 unless batched)      */
+    int32_t backend;              /* vbcsr_backend chosen from the block sizes       */
+    int32_t reserved;
 } vbcsr_info_t;
+
+/*
+ * Backend chosen at creation from the block sizes (Sec. II.B: scalar operators
+ * map to CSR, a uniform basis to BSR, species-dependent bases to VBCSR):
+ *  CSR    every block 1 x 1: the forward product (FP64 / FP32 arithmetic) runs
+ *         a scalar kernel with several rows per warp
+ *  BSR    every block b x b for one b > 1: the block-row kernels specialised
+ *         for that b
+ *  VBCSR  otherwise
+ * Values, X and Y are laid out the same way for every backend.
+ */
+typedef enum {
+    VBCSR_BACKEND_CSR = 0,
+    VBCSR_BACKEND_BSR = 1,
+    VBCSR_BACKEND_VBCSR = 2
+} vbcsr_backend;
 
 /* Optional fused epilogue of vbcsr_spmm_ex (all fields may be zero/NULL). */
 typedef struct {
@@ -269,6 +289,37 @@ int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ld
                              const double *grad_mu, const double *ckpt, int64_t ckpt_every,
                              double *dvalues, double *work, int precision, void *stream);
 
+/* Damping kernels of vbcsr_kpm_dos. */
+#define VBCSR_KPM_NO_KERNEL 0
+#define VBCSR_KPM_JACKSON 1
+
+/*
+ * Kernel-polynomial moments mu_0 .. mu_{M-1} (Sec. V: the DOS of the InP
+ * particles comes from KPM moments) for a SYMMETRIC operator already scaled
+ * to H~, with half the products of vbcsr_chebyshev: t_0 = R, t_1 = H~ R,
+ * t_{n+1} = 2 H~ t_n - t_{n-1} up to n = ceil(M/2) - 1 or so, and
+ *   mu_0 = <R, R> / (N k),  mu_1 = <t_1, R> / (N k),
+ *   mu_{2n} = 2 <t_n, t_n> / (N k) - mu_0,  mu_{2n+1} = 2 <t_{n+1}, t_n> / (N k) - mu_1,
+ * from T_{2n} = 2 T_n^2 - T_0 and T_{2n+1} = 2 T_{n+1} T_n - T_1 (these need
+ * H~ = H~^T; for a non-symmetric operator use vbcsr_chebyshev). Arguments as
+ * vbcsr_chebyshev: R device [n_rows, k] (ldr), moments device [M], work device
+ * 2 * n_rows * k doubles; recurrence and moments FP64, products in `precision`.
+ */
+int vbcsr_kpm_moments(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
+                      double *moments, double *work, int precision, void *stream);
+
+/*
+ * Density of states from KPM moments at scaled energies x in (-1, 1):
+ *   dos[i] = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(x_i)] / (pi sqrt(1 - x_i^2)),
+ * g the Jackson damping factors (kernel = VBCSR_KPM_JACKSON,
+ *   g_n = [(M - n + 1) cos(pi n / (M + 1)) + sin(pi n / (M + 1)) cot(pi / (M + 1))] / (M + 1))
+ * or 1 (VBCSR_KPM_NO_KERNEL). In the energy of H = c + d H~, the density is
+ * dos / d at E = c + d x. moments, x, dos: device arrays of n_moments, n_x,
+ * n_x doubles. Needs no handle.
+ */
+int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kernel, const double *x, int64_t n_x,
+                  double *dos, void *stream);
+
 /*
  * Spectral bounds for the kernel polynomial method (Sec. V needs H scaled so
  * that its spectrum lies in [-1, 1]): Gershgorin discs over scalar rows,
@@ -311,9 +362,31 @@ int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream);
 int vbcsr_chebyshev_noalloc(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
                             double *moments, int precision, void *stream);
 
+/*
+ * Thresholded block sparse product C = A * B (Sec. III.B, Eqs. 2-3), a new
+ * handle in *C. A's block columns must be B's block rows (same count and
+ * sizes); same dtype. With Frobenius block norms:
+ *  symbolic stage  a candidate block (i, j) is kept when the bound
+ *                  sum_k ||A_ik|| ||B_kj|| (Eq. 3) is >= eps;
+ *  numeric stage   C_ij = sum_k A_ik B_kj over every k with both blocks stored
+ *                  (products grouped by output block, equal inner sizes b_k
+ *                  adjacent), on the GPU;
+ *  final filter    blocks with ||C_ij|| < eps are removed.
+ * eps = 0 keeps every block reached by a product path. The block norms, the
+ * candidate lists and the filtered pattern pass through host memory; the
+ * call synchronises `stream`. Errors: INVALID_ARG, NO_MEMORY, CUDA.
+ */
+int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcsr_t **C, void *stream);
+
 /* ---- inspection ---------------------------------------------------------- */
 
 int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out);
+
+/* Copies the pattern out (host arrays of n_brows, n_bcols, n_brows + 1 and
+   nblk elements, as vbcsr_get_info reports them; any pointer may be NULL),
+   block columns in the order the handle was created with. */
+int vbcsr_get_pattern(const vbcsr_t *A, int32_t *row_bsize, int32_t *col_bsize, int64_t *block_row_ptr,
+                      int32_t *block_col_idx);
 
 /*
  * Shape-class registry (Sec. III.B: every distinct (b_i, b_j) of a stored

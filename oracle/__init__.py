@@ -258,3 +258,116 @@ def moment_loss_grad(pat, values_t, R, n_moments) -> np.ndarray:
     for n in range(1, M - 1):
         grad += sddmm(pat, lam[n + 1], t[n], alpha=2.0)
     return grad
+
+
+# ----------------------------------------------------------------------------
+# kernel polynomial method: moments by the doubling identities, Jackson
+# damping, DOS reconstruction (Sec. V; Weisse, Wellein, Alvermann & Fehske,
+# Rev. Mod. Phys. 78, 275 (2006), Sec. II)
+
+
+def kpm_moments_doubling(pat, values_t, R, n_moments, nthreads=1) -> np.ndarray:
+    """mu_0 .. mu_{M-1} of a symmetric H~ from t_0 .. t_{ceil(M/2)} using
+    T_{2n} = 2 T_n^2 - T_0 and T_{2n+1} = 2 T_{n+1} T_n - T_1:
+    mu_{2n} = 2 <t_n, t_n> / (N k) - mu_0,  mu_{2n+1} = 2 <t_{n+1}, t_n> / (N k) - mu_1."""
+    R = np.asarray(R, dtype=np.float64)
+    s = 1.0 / R.size
+    mu = np.zeros(n_moments)
+    mu[0] = np.sum(R * R) * s
+    if n_moments == 1:
+        return mu
+    t_prev, t_cur = R, spmm(pat, values_t, R, nthreads=nthreads)      # t_0, t_1
+    mu[1] = np.sum(t_cur * R) * s
+    n = 1                                                               # t_cur = t_n
+    while True:
+        if 2 * n < n_moments:
+            mu[2 * n] = 2.0 * np.sum(t_cur * t_cur) * s - mu[0]
+        if 2 * n + 1 >= n_moments:
+            break
+        t_next = spmm(pat, values_t, t_cur, alpha=2.0, beta=-1.0, Y=t_prev, nthreads=nthreads)
+        mu[2 * n + 1] = 2.0 * np.sum(t_next * t_cur) * s - mu[1]
+        t_prev, t_cur = t_cur, t_next
+        n += 1
+    return mu
+
+
+def jackson_kernel(n_moments) -> np.ndarray:
+    """Jackson damping factors g_n, n = 0 .. M-1 (M = n_moments):
+    g_n = [(M - n + 1) cos(pi n / (M + 1)) + sin(pi n / (M + 1)) cot(pi / (M + 1))] / (M + 1)."""
+    M = n_moments
+    n = np.arange(M, dtype=np.float64)
+    q = np.pi / (M + 1)
+    return ((M - n + 1) * np.cos(q * n) + np.sin(q * n) / np.tan(q)) / (M + 1)
+
+
+def kpm_dos(mu, x, kernel="jackson") -> np.ndarray:
+    """rho(x) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(x)] / (pi sqrt(1 - x^2)),
+    x in (-1, 1) (the scaled energy), T_n(x) = cos(n arccos x)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    g = jackson_kernel(len(mu)) if kernel == "jackson" else np.ones(len(mu))
+    th = np.arccos(x)
+    acc = g[0] * mu[0] * np.ones_like(x)
+    for n in range(1, len(mu)):
+        acc += 2.0 * g[n] * mu[n] * np.cos(n * th)
+    return acc / (np.pi * np.sqrt(1.0 - x * x))
+
+
+# ----------------------------------------------------------------------------
+# thresholded block sparse product (Sec. III.B, Eqs. 2-3)
+
+
+def block_norms(pat, values) -> np.ndarray:
+    """Frobenius norm of every stored block (packed order)."""
+    off = pat.value_offset() if hasattr(pat, "value_offset") else None
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    rows = np.repeat(np.arange(len(rb)), np.diff(pat.block_row_ptr))
+    sizes = rb[rows] * cb[np.asarray(pat.block_col_idx, np.int64)]
+    if off is None:
+        off = np.concatenate([[0], np.cumsum(sizes)])
+    v = np.asarray(values, np.float64)
+    return np.sqrt(np.add.reduceat(v * v, off[:-1])) if len(sizes) else np.zeros(0)
+
+
+def spgemm(patA, valsA, patB, valsB, eps):
+    """C = A B on block patterns (patA's column blocks are patB's row blocks).
+    Symbolic stage: a candidate block (i, j) is kept when the bound
+    sum_k ||A_ik|| ||B_kj|| (Eq. 3) is >= eps; numeric stage: C_ij = sum_k A_ik B_kj
+    (Eq. 2) over every k with both blocks stored; final filter: blocks with
+    ||C_ij|| < eps are removed. Returns (row_bsize, col_bsize, block_row_ptr,
+    block_col_idx, values) with columns sorted inside each row; norms are
+    Frobenius norms."""
+    nA = block_norms(patA, valsA)
+    nB = block_norms(patB, valsB)
+    ra = np.asarray(patA.row_bsize, np.int64)
+    kb = np.asarray(patB.row_bsize, np.int64)
+    cb = np.asarray(patB.col_bsize, np.int64)
+    offA = np.concatenate([[0], np.cumsum(ra[np.repeat(np.arange(len(ra)), np.diff(patA.block_row_ptr))]
+                                          * np.asarray(patA.col_bsize, np.int64)[np.asarray(patA.block_col_idx)])])
+    offB = np.concatenate([[0], np.cumsum(kb[np.repeat(np.arange(len(kb)), np.diff(patB.block_row_ptr))]
+                                          * cb[np.asarray(patB.block_col_idx)])])
+    ptr, cols, vals = [0], [], []
+    for i in range(len(ra)):
+        bound = {}
+        for a in range(patA.block_row_ptr[i], patA.block_row_ptr[i + 1]):
+            k = int(patA.block_col_idx[a])
+            for b in range(patB.block_row_ptr[k], patB.block_row_ptr[k + 1]):
+                j = int(patB.block_col_idx[b])
+                bound[j] = bound.get(j, 0.0) + nA[a] * nB[b]
+        kept = sorted(j for j, bd in bound.items() if bd >= eps)
+        for j in kept:
+            Cij = np.zeros((ra[i], cb[j]))
+            for a in range(patA.block_row_ptr[i], patA.block_row_ptr[i + 1]):
+                k = int(patA.block_col_idx[a])
+                Aik = np.asarray(valsA[offA[a]:offA[a + 1]]).reshape(ra[i], kb[k])
+                for b in range(patB.block_row_ptr[k], patB.block_row_ptr[k + 1]):
+                    if int(patB.block_col_idx[b]) == j:
+                        Bkj = np.asarray(valsB[offB[b]:offB[b + 1]]).reshape(kb[k], cb[j])
+                        Cij += Aik @ Bkj
+            if np.sqrt(np.sum(Cij * Cij)) >= eps:
+                cols.append(j)
+                vals.append(Cij.ravel())
+        ptr.append(len(cols))
+    return (ra.astype(np.int32), cb.astype(np.int32), np.array(ptr, np.int64), np.array(cols, np.int32),
+            np.concatenate(vals) if vals else np.zeros(0))

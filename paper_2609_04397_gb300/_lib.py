@@ -22,7 +22,8 @@ _i64, _i32, _d, _p, _int = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctyp
 class Info(ctypes.Structure):
     _fields_ = [("n_brows", _i64), ("n_bcols", _i64), ("n_rows", _i64), ("n_cols", _i64),
                 ("nblk", _i64), ("nnz", _i64), ("panel_elems", _i64), ("device_bytes", _i64),
-                ("dtype", _i32), ("n_shape_classes", _i32), ("n_row_classes", _i32), ("n_structs", _i32)]
+                ("dtype", _i32), ("n_shape_classes", _i32), ("n_row_classes", _i32), ("n_structs", _i32),
+                ("backend", _i32), ("reserved", _i32)]
 
 
 class Epilogue(ctypes.Structure):
@@ -45,8 +46,12 @@ SIGNATURES = {
     "vbcsr_chebyshev_backward": ([_p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _p, _int, _p], _int),
     "vbcsr_chebyshev_noalloc": ([_p, _i64, _p, _i64, _i64, _p, _int, _p], _int),
     "vbcsr_gershgorin": ([_p, _p, _p], _int),
+    "vbcsr_kpm_moments": ([_p, _i64, _p, _i64, _i64, _p, _p, _int, _p], _int),
+    "vbcsr_kpm_dos": ([_p, _i64, _int, _p, _i64, _p, _p], _int),
     "vbcsr_shift_scale": ([_p, _d, _d, _p], _int),
+    "vbcsr_spgemm": ([_p, _p, _d, ctypes.POINTER(_p), _p], _int),
     "vbcsr_get_info": ([_p, ctypes.POINTER(Info)], _int),
+    "vbcsr_get_pattern": ([_p, _p, _p, _p, _p], _int),
     "vbcsr_shape_classes": ([_p, _p, _p, _p, _i32], _int),
     "vbcsr_set_tuning": ([_p, _i32, _i32], _int),
     "vbcsr_set_bucket_tuning": ([_p, _i32, _i32, _i32], _int),

@@ -42,6 +42,10 @@ class _Matmul(torch.autograd.Function):
         return dvalues, dX, None, None
 
 
+# The Function itself: VBCSRMatmul.apply(values, X, H, precision)
+VBCSRMatmul = _Matmul
+
+
 def vbcsr_matmul(H: VBCSR, values: torch.Tensor, X: torch.Tensor, precision="native") -> torch.Tensor:
     """Y = H X with the stored values taken from `values` (packed order)."""
     return _Matmul.apply(values, X, H, precision)

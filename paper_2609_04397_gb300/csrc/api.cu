@@ -85,6 +85,8 @@ struct vbcsr_matrix {
     size_t esize = 8;
     int64_t n_brows = 0, n_bcols = 0, n_rows = 0, n_cols = 0, nblk = 0, nnz = 0, panel_elems = 0;
     int32_t n_structs = 1;
+    int backend = VBCSR_BACKEND_VBCSR;
+    int csr_lanes[2] = {2, 8};      // lanes per row of the scalar kernel: FP64 / FP32-pipe kinds
     int kc_b[kMaxB + 1] = {0};      // column tile per row count (0: from k)
     int warps_b[kMaxB + 1] = {0};   // warps per CTA per row count (0: 4)
     int schedule = 0;               // 0: one launch per row count, 1: one persistent launch
@@ -99,6 +101,12 @@ struct vbcsr_matrix {
     std::vector<int64_t> cls_count;
 
     std::vector<Bucket> fwd_buckets, adj_buckets;
+    // host copies of the plan, for the symbolic stage of the block product
+    std::vector<int64_t> h_rowptr;     // plan blocks of every block row
+    std::vector<int32_t> h_pcol;       // block column of every plan block
+    std::vector<int32_t> h_ucol;       // block column of every block in the caller's order
+    std::vector<int64_t> h_pbase;      // panel element of its (0, 0) entry
+    std::vector<int32_t> h_kp;         // panel stride of its row
 
     // device
     std::vector<DevBuf> bufs;
@@ -241,6 +249,30 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
             A->uoff[u + 1] = A->uoff[u] + (int64_t)row_bsize[i] * col_bsize[block_col_idx[u]];
     A->nnz = A->uoff[nblk];
 
+    // backend (Sec. II.B): scalar, uniform-block or variable-block
+    {
+        bool scalar = true, uniform = n_brows > 0 || n_bcols > 0;
+        const int32_t b0 = n_brows > 0 ? row_bsize[0] : (n_bcols > 0 ? col_bsize[0] : 1);
+        for (int64_t i = 0; i < n_brows; ++i) {
+            scalar &= row_bsize[i] == 1;
+            uniform &= row_bsize[i] == b0;
+        }
+        for (int64_t j = 0; j < n_bcols; ++j) {
+            scalar &= col_bsize[j] == 1;
+            uniform &= col_bsize[j] == b0;
+        }
+        A->backend = scalar ? VBCSR_BACKEND_CSR : (uniform ? VBCSR_BACKEND_BSR : VBCSR_BACKEND_VBCSR);
+        if (scalar) {
+            // FP64 operations are charged per warp instruction on GB300's narrow FP64
+            // pipe, so an FP64 row gets few lanes (every instruction carries ~32 useful
+            // lanes, the finishing butterfly is short); FP32 rows get more lanes for
+            // coalesced loads
+            const double avg = n_brows > 0 ? (double)nblk / (double)n_brows : 0.0;
+            A->csr_lanes[0] = avg <= 64 ? 2 : (avg <= 256 ? 4 : 8);
+            A->csr_lanes[1] = avg <= 8 ? 4 : (avg <= 24 ? 8 : (avg <= 64 ? 16 : 32));
+        }
+    }
+
     // shape-class registry (Sec. III.B): every distinct (b_i, b_j)
     {
         std::map<std::pair<int32_t, int32_t>, int64_t> reg;
@@ -306,9 +338,11 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     {
         std::vector<std::vector<WorkItem>> bk(kMaxB + 1);
         for (int64_t i : page_order) {
-            for (int32_t r0 = 0; r0 < row_bsize[i]; r0 += kMaxB) {
+            // a row taller than kMaxB is cut into ceil(b / kMaxB) near-equal chunks
+            const int32_t nch = (row_bsize[i] + kMaxB - 1) / kMaxB;
+            for (int32_t c = 0, r0 = 0; c < nch; ++c) {
                 WorkItem w;
-                w.B = std::min(kMaxB, row_bsize[i] - r0);
+                w.B = row_bsize[i] / nch + (c < row_bsize[i] % nch ? 1 : 0);
                 w.vbase = poff[i] + (int64_t)r0 * Kp[i];
                 w.yrow = A->row_off[i] + r0;
                 w.lbegin = block_row_ptr[i];
@@ -316,6 +350,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
                 w.K = (int32_t)K[i];
                 w.Kp = (int32_t)Kp[i];
                 bk[w.B].push_back(w);
+                r0 += w.B;
             }
         }
         std::vector<WorkItem> items;
@@ -364,9 +399,10 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
                          [&](int64_t x, int64_t y) { return col_bsize[x] < col_bsize[y]; });
         std::vector<std::vector<WorkItem>> bk(kMaxB + 1);
         for (int64_t j : col_order) {
-            for (int32_t q0 = 0; q0 < col_bsize[j]; q0 += kMaxB) {
+            const int32_t nch = (col_bsize[j] + kMaxB - 1) / kMaxB;
+            for (int32_t c = 0, q0 = 0; c < nch; ++c) {
                 WorkItem w;
-                w.B = std::min(kMaxB, col_bsize[j] - q0);
+                w.B = col_bsize[j] / nch + (c < col_bsize[j] % nch ? 1 : 0);
                 w.vbase = 0;
                 w.yrow = A->col_off[j] + q0;
                 w.lbegin = tptr[j];
@@ -374,6 +410,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
                 w.K = (int32_t)Kt[j];
                 w.Kp = q0;
                 bk[w.B].push_back(w);
+                q0 += w.B;
             }
         }
         std::vector<WorkItem> items;
@@ -393,6 +430,12 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
         CUDA_TRY(upload(A, &A->tl_vcol, tl_vcol, s), "upload");
     }
 
+    A->h_rowptr = prow_ptr;
+    A->h_ucol.assign(block_col_idx, block_col_idx + nblk);
+    A->h_pcol.resize(nblk);
+    for (int64_t l = 0; l < nblk; ++l) A->h_pcol[l] = block_col_idx[perm[l]];
+    A->h_pbase = fl_pbase;
+    A->h_kp = fl_kp;
     CUDA_TRY(upload(A, &A->fl_xrow, fl_xrow, s), "upload");
     CUDA_TRY(upload(A, &A->fl_pcol, fl_pcol, s), "upload");
     CUDA_TRY(upload(A, &A->fl_w, fl_w, s), "upload");
@@ -783,6 +826,26 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         const void *kern = mma_kernel_ptr(mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
+    } else if (A->backend == VBCSR_BACKEND_CSR && !trans &&
+               !(A->schedule & (VBCSR_SCHED_NO_CSR | VBCSR_SCHED_PERSISTENT))) {
+        // scalar operator: several rows per warp; items are the scalar rows in page order
+        const int kind = mode == VBCSR_PREC_DF32 ? kCsrDF
+                       : mode == VBCSR_PREC_F32 ? kCsrF32OnF64 : (f64 ? kCsrF64 : kCsrF32);
+        const int L = A->csr_lanes[csr_lane_class(kind)];
+        a.items = A->fwd_items;
+        a.n_items = A->n_fwd_items;
+        a.warps = 8;
+        cudaError_t pending = cudaGetLastError();
+        if (pending != cudaSuccess) return cuda_fail(pending, "error pending before the product launch");
+        const int cap = cached_cap(csr_kernel_ptr(kind, L, k), a.warps, 0);
+        if (cap < 0) return cuda_fail(cudaGetLastError(), "occupancy query of the scalar kernel");
+        const int64_t need = (a.n_items + a.warps * (32 / L) - 1) / (a.warps * (32 / L));
+        a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
+        if (want_dot) {
+            a.partials = A->partials;
+            used = a.grid;
+        }
+        CUDA_TRY(launch_csr(kind, L, a, s), "scalar product launch");
     } else if (A->schedule & VBCSR_SCHED_PERSISTENT) {
         // persistent launch over every row count, items in descending cost from a work queue
         a.kc_log2_by_b = 0;
@@ -984,6 +1047,58 @@ extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, 
     return VBCSR_OK;
 }
 
+extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t M, double *moments,
+                                 double *work, int precision, void *stream) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
+    if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
+    if (k < 1 || M < 1) return fail(VBCSR_ERR_INVALID_ARG, "k and n_moments must be >= 1");
+    if (!R || !moments || !work || ldr < k) return fail(VBCSR_ERR_INVALID_ARG, "R / moments / work / ldr");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = A->n_rows, panel = N * k;
+    const double scale = 1.0 / ((double)N * (double)k);
+    double *buf[2] = {work, work + panel};
+    int64_t used = 0;
+    auto self_dot = [&](const double *t, int64_t ld, double *out) -> int {
+        CUDA_TRY(launch_dot_panels(true, N, k, t, ld, t, ld, A->partials, kPartialsCap, &used, s), "dot");
+        CUDA_TRY(launch_finalize_dot(A->partials, used, scale, out, s), "dot");
+        return VBCSR_OK;
+    };
+    int rc = self_dot(R, ldr, moments);                                     // mu_0
+    if (rc || M == 1) return rc;
+    vbcsr_epilogue_t epi;
+    memset(&epi, 0, sizeof(epi));
+    epi.R = R;
+    epi.ldr = ldr;
+    epi.dot_out = moments + 1;                                             // mu_1 = <t_1, t_0>
+    if ((rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale))) return rc;
+    CUDA_TRY(launch_copy_panel(N, k, R, ldr, buf[0], k, s), "copy R");
+    // t_n in buf[n & 1]; raw dots <t_n, t_n> -> moments[2n], <t_{n+1}, t_n> -> moments[2n+1]
+    for (int64_t n = 1;; ++n) {
+        double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
+        if (2 * n < M && (rc = self_dot(tn, k, moments + 2 * n))) return rc;
+        if (2 * n + 1 >= M) break;
+        epi.R = tn;
+        epi.ldr = k;
+        epi.dot_out = moments + 2 * n + 1;
+        if ((rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale))) return rc;
+    }
+    CUDA_TRY(launch_kpm_fixup(moments, M, s), "moment fix-up");
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kernel, const double *x, int64_t n_x,
+                             double *dos, void *stream) {
+    if (n_moments < 1 || n_x < 0) return fail(VBCSR_ERR_INVALID_ARG, "n_moments %lld, n_x %lld",
+                                             (long long)n_moments, (long long)n_x);
+    if (kernel != VBCSR_KPM_NO_KERNEL && kernel != VBCSR_KPM_JACKSON)
+        return fail(VBCSR_ERR_INVALID_ARG, "kernel %d", kernel);
+    if (!moments || (n_x > 0 && (!x || !dos))) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(launch_kpm_dos(moments, n_moments, kernel == VBCSR_KPM_JACKSON, x, n_x, dos, (cudaStream_t)stream),
+             "kpm dos");
+    return VBCSR_OK;
+}
+
 extern "C" int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream) {
     if (!A || !bounds) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
     if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "Gershgorin bounds need an FP64 operator");
@@ -1013,6 +1128,181 @@ extern "C" int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream) {
 }
 
 // ---------------------------------------------------------------------------
+// thresholded block sparse product (Eqs. 2-3)
+
+namespace {
+template <typename T>
+struct DevVec {   // temporary device array freed on scope exit
+    T *p = nullptr;
+    ~DevVec() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t put(const std::vector<T> &v, cudaStream_t s) {
+        cudaError_t e = cudaMalloc((void **)&p, std::max<size_t>(1, v.size()) * sizeof(T));
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+    cudaError_t alloc(size_t n) { return cudaMalloc((void **)&p, std::max<size_t>(1, n) * sizeof(T)); }
+};
+}  // namespace
+
+extern "C" int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcsr_t **Cout, void *stream) {
+    if (!Cout) return fail(VBCSR_ERR_INVALID_ARG, "out is NULL");
+    *Cout = nullptr;
+    if (!A || !B) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (A->dtype != B->dtype) return fail(VBCSR_ERR_INVALID_ARG, "A and B have different dtypes");
+    if (!(eps >= 0.0)) return fail(VBCSR_ERR_INVALID_ARG, "eps = %g", eps);
+    if (A->n_bcols != B->n_brows) return fail(VBCSR_ERR_INVALID_ARG, "inner block counts differ");
+    for (int64_t k = 0; k < A->n_bcols; ++k)
+        if (A->col_b[k] != B->row_b[k]) return fail(VBCSR_ERR_INVALID_ARG, "inner block %lld sizes differ", (long long)k);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f64 = A->dtype == VBCSR_F64;
+    try {
+        // block norms of both operands
+        std::vector<double> nA(A->nblk), nB(B->nblk);
+        {
+            DevVec<double> dA, dB;
+            CUDA_TRY(dA.alloc(A->nblk), "alloc norms");
+            CUDA_TRY(dB.alloc(B->nblk), "alloc norms");
+            CUDA_TRY(launch_block_norms(f64, A->nblk, A->panel, A->fl_pbase, A->fl_kp, A->fl_bi, A->fl_w, dA.p, s),
+                     "block norms");
+            CUDA_TRY(launch_block_norms(f64, B->nblk, B->panel, B->fl_pbase, B->fl_kp, B->fl_bi, B->fl_w, dB.p, s),
+                     "block norms");
+            if (A->nblk) CUDA_TRY(cudaMemcpyAsync(nA.data(), dA.p, A->nblk * 8, cudaMemcpyDeviceToHost, s), "copy");
+            if (B->nblk) CUDA_TRY(cudaMemcpyAsync(nB.data(), dB.p, B->nblk * 8, cudaMemcpyDeviceToHost, s), "copy");
+            CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        }
+        // symbolic stage: candidates, Eq. 3 bounds, product lists
+        const int64_t nbr = A->n_brows, nbc = B->n_bcols;
+        std::vector<int64_t> mark(nbc, -1);
+        std::vector<int64_t> touched;
+        std::vector<double> bound;
+        std::vector<int64_t> out_ptr(1, 0), out_pbeg(1, 0), out_uoff(1, 0);
+        std::vector<int32_t> out_col, out_bi, out_bj;
+        std::vector<int64_t> pa, pb;
+        std::vector<int32_t> kpa, kpb, bk;
+        struct Prod { int64_t o; int32_t k; int64_t a, b; };
+        std::vector<Prod> row_prods;
+        for (int64_t i = 0; i < nbr; ++i) {
+            touched.clear();
+            bound.clear();
+            for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
+                const int32_t k = A->h_pcol[a];
+                for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
+                    const int32_t j = B->h_pcol[b];
+                    if (mark[j] < 0) {
+                        mark[j] = (int64_t)touched.size();
+                        touched.push_back(j);
+                        bound.push_back(0.0);
+                    }
+                    bound[mark[j]] += nA[a] * nB[b];
+                }
+            }
+            std::vector<int64_t> kept;
+            for (size_t t = 0; t < touched.size(); ++t)
+                if (bound[t] >= eps) kept.push_back(touched[t]);
+            std::sort(kept.begin(), kept.end());
+            for (int64_t j : touched) mark[j] = -1;
+            const int64_t obase = (int64_t)out_col.size();
+            for (size_t t = 0; t < kept.size(); ++t) mark[kept[t]] = obase + (int64_t)t;
+            row_prods.clear();
+            for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
+                const int32_t k = A->h_pcol[a];
+                for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
+                    const int64_t o = mark[B->h_pcol[b]];
+                    if (o >= 0) row_prods.push_back({o, A->col_b[k], a, b});
+                }
+            }
+            // products of one output block together, equal inner sizes b_k adjacent
+            std::stable_sort(row_prods.begin(), row_prods.end(), [](const Prod &x, const Prod &y) {
+                return x.o != y.o ? x.o < y.o : x.k < y.k;
+            });
+            size_t u = 0;
+            for (size_t t = 0; t < kept.size(); ++t) {
+                const int64_t o = obase + (int64_t)t, j = kept[t];
+                out_col.push_back((int32_t)j);
+                out_bi.push_back(A->row_b[i]);
+                out_bj.push_back(B->col_b[j]);
+                out_uoff.push_back(out_uoff.back() + (int64_t)A->row_b[i] * B->col_b[j]);
+                for (; u < row_prods.size() && row_prods[u].o == o; ++u) {
+                    pa.push_back(A->h_pbase[row_prods[u].a]);
+                    kpa.push_back(A->h_kp[row_prods[u].a]);
+                    pb.push_back(B->h_pbase[row_prods[u].b]);
+                    kpb.push_back(B->h_kp[row_prods[u].b]);
+                    bk.push_back(row_prods[u].k);
+                }
+                out_pbeg.push_back((int64_t)pa.size());
+            }
+            for (int64_t j : kept) mark[j] = -1;
+            out_ptr.push_back((int64_t)out_col.size());
+        }
+        // numeric stage
+        const int64_t n_out = (int64_t)out_col.size(), n_val = out_uoff.back();
+        const size_t es = A->esize;
+        DevVec<int64_t> d_pbeg, d_uoff, d_pa, d_pb;
+        DevVec<int32_t> d_bi, d_bj, d_kpa, d_kpb, d_bk;
+        DevVec<double> d_norm;
+        DevVec<unsigned char> d_val;
+        CUDA_TRY(d_pbeg.put(out_pbeg, s), "upload");
+        CUDA_TRY(d_uoff.put(out_uoff, s), "upload");
+        CUDA_TRY(d_pa.put(pa, s), "upload");
+        CUDA_TRY(d_pb.put(pb, s), "upload");
+        CUDA_TRY(d_bi.put(out_bi, s), "upload");
+        CUDA_TRY(d_bj.put(out_bj, s), "upload");
+        CUDA_TRY(d_kpa.put(kpa, s), "upload");
+        CUDA_TRY(d_kpb.put(kpb, s), "upload");
+        CUDA_TRY(d_bk.put(bk, s), "upload");
+        CUDA_TRY(d_norm.alloc(n_out), "alloc norms");
+        CUDA_TRY(d_val.alloc((size_t)n_val * es), "alloc product values");
+        SpgemmArgs g;
+        g.n_out = n_out;
+        g.out_pbeg = d_pbeg.p;
+        g.out_uoff = d_uoff.p;
+        g.out_bi = d_bi.p;
+        g.out_bj = d_bj.p;
+        g.pa = d_pa.p;
+        g.pb = d_pb.p;
+        g.kpa = d_kpa.p;
+        g.kpb = d_kpb.p;
+        g.bk = d_bk.p;
+        g.A = A->panel;
+        g.B = B->panel;
+        g.C = d_val.p;
+        g.norms = d_norm.p;
+        CUDA_TRY(launch_spgemm_numeric(f64, g, s), "numeric stage");
+        // final filter on the computed block norms
+        std::vector<double> norms(n_out);
+        if (n_out) CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm.p, n_out * 8, cudaMemcpyDeviceToHost, s), "copy");
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        std::vector<int64_t> c_ptr(1, 0), keep_src, dst_off(1, 0);
+        std::vector<int32_t> c_col, keep_size;
+        for (int64_t i = 0; i < nbr; ++i) {
+            for (int64_t o = out_ptr[i]; o < out_ptr[i + 1]; ++o) {
+                if (norms[o] < eps) continue;
+                c_col.push_back(out_col[o]);
+                keep_src.push_back(out_uoff[o]);
+                keep_size.push_back(out_bi[o] * out_bj[o]);
+                dst_off.push_back(dst_off.back() + keep_size.back());
+            }
+            c_ptr.push_back((int64_t)c_col.size());
+        }
+        DevVec<int64_t> d_keep, d_dst;
+        DevVec<int32_t> d_size;
+        DevVec<unsigned char> d_cval;
+        CUDA_TRY(d_keep.put(keep_src, s), "upload");
+        CUDA_TRY(d_dst.put(dst_off, s), "upload");
+        CUDA_TRY(d_size.put(keep_size, s), "upload");
+        CUDA_TRY(d_cval.alloc((size_t)dst_off.back() * es), "alloc result values");
+        CUDA_TRY(launch_compact(f64, (int64_t)c_col.size(), d_keep.p, d_dst.p, d_size.p, d_val.p, d_cval.p, s),
+                 "compaction");
+        return vbcsr_create(Cout, nbr, nbc, A->row_b.data(), B->col_b.data(), c_ptr.data(), c_col.data(), d_cval.p,
+                            A->dtype, 1, stream);
+    } catch (const std::bad_alloc &) {
+        return fail(VBCSR_ERR_NO_MEMORY, "host allocation in the block product");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // inspection and control
 
 extern "C" int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out) {
@@ -1029,6 +1319,18 @@ extern "C" int vbcsr_get_info(const vbcsr_t *A, vbcsr_info_t *out) {
     out->n_shape_classes = (int32_t)A->cls_bi.size();
     out->n_row_classes = (int32_t)A->fwd_buckets.size();
     out->n_structs = A->n_structs;
+    out->backend = A->backend;
+    out->reserved = 0;
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_get_pattern(const vbcsr_t *A, int32_t *row_bsize, int32_t *col_bsize, int64_t *block_row_ptr,
+                                 int32_t *block_col_idx) {
+    if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (row_bsize) std::copy(A->row_b.begin(), A->row_b.end(), row_bsize);
+    if (col_bsize) std::copy(A->col_b.begin(), A->col_b.end(), col_bsize);
+    if (block_row_ptr) std::copy(A->h_rowptr.begin(), A->h_rowptr.end(), block_row_ptr);
+    if (block_col_idx) std::copy(A->h_ucol.begin(), A->h_ucol.end(), block_col_idx);
     return VBCSR_OK;
 }
 
@@ -1065,7 +1367,7 @@ extern "C" int vbcsr_set_bucket_tuning(vbcsr_t *A, int32_t B, int32_t kc, int32_
 
 extern "C" int vbcsr_set_schedule(vbcsr_t *A, int32_t schedule, int32_t persist_warps) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (schedule < 0 || schedule > (VBCSR_SCHED_PERSISTENT | VBCSR_SCHED_MMA_STAGED))
+    if (schedule < 0 || schedule > (VBCSR_SCHED_PERSISTENT | VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR))
         return fail(VBCSR_ERR_INVALID_ARG, "schedule %d", schedule);
     if (!valid_warps(persist_warps)) return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", persist_warps);
     A->schedule = schedule;
@@ -1139,7 +1441,8 @@ extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *
     const int kc_auto = auto_kc(k);
     // 1) per row count: the column tile and CTA width of its bucket launch
     const int saved_schedule = A->schedule;
-    const int mma_bit = saved_schedule & VBCSR_SCHED_MMA_STAGED;
+    // the tensor-core variant and the scalar-kernel opt-out are the caller's, not tuned here
+    const int mma_bit = saved_schedule & (VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR);
     A->schedule = VBCSR_SCHED_BUCKETED | mma_bit;
     const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
     int keep_kc[kMaxB + 1], keep_w[kMaxB + 1];

@@ -68,38 +68,51 @@ __device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_
     if (a.partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
 }
 
-// Reduce-scatter of B (<= 16) per-lane partial sums over all 32 lanes: after
-// it, lane l holds the full sum of row rs_row(l) (lanes l and l^1 agree). It
-// costs 16 adds per lane instead of 5 * B for a butterfly on every row.
+// Reduce-scatter of B (<= 16) per-lane partial sums over all 32 lanes, sized
+// to NV = the next power of two >= B: halving steps over the lane bits 16, 8,
+// 4, 2 while more than one value remains, plain butterfly steps for the rest.
+// Afterwards the lanes whose bits select row rs_row<NV>(lane) hold that row's
+// full sum. It costs (NV - 1) + (5 - log2 NV) adds per lane (5 for B <= 2,
+// 16 for B > 8) instead of 5 * B; FP64 adds are issued per warp instruction
+// on GB300's narrow FP64 pipe, so this matters for small rows.
+template <int B>
+struct RsShape {
+    static constexpr int NV = B <= 1 ? 1 : B <= 2 ? 2 : B <= 4 ? 4 : B <= 8 ? 8 : 16;
+    static constexpr int LOG = NV == 1 ? 0 : NV == 2 ? 1 : NV == 4 ? 2 : NV == 8 ? 3 : 4;
+};
+
+template <int NV>
 __device__ __forceinline__ int rs_row(int lane) {
-    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+    // the halving steps use lane bits 16, 8, 4, 2 in that order
+    int r = 0;
+    if (NV >= 2) r += ((lane >> 4) & 1) * (NV / 2);
+    if (NV >= 4) r += ((lane >> 3) & 1) * (NV / 4);
+    if (NV >= 8) r += ((lane >> 2) & 1) * (NV / 8);
+    if (NV >= 16) r += ((lane >> 1) & 1);
+    return r;
 }
 
 template <int B, typename TA>
 __device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
-    TA v8[8], v4[4], v2[2];
+    constexpr int NV = RsShape<B>::NV;
+    TA v[NV];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const TA lo = (j < B) ? acc[j] : (TA)0, hi = (j + 8 < B) ? acc[j + 8] : (TA)0;
-        const bool up = lane & 16;
-        const TA keep = up ? hi : lo, send = up ? lo : hi;
-        v8[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
+    for (int j = 0; j < NV; ++j) v[j] = (j < B) ? acc[j] : (TA)0;
+    // halving steps: keep the half selected by the lane bit, receive the partner's copy of it
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const bool up = lane & 8;
-        const TA keep = up ? v8[j + 4] : v8[j], send = up ? v8[j] : v8[j + 4];
-        v4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
+    for (int h = NV / 2, bit = 16; h >= 1; h >>= 1, bit >>= 1) {
+        const bool up = lane & bit;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const bool up = lane & 4;
-        const TA keep = up ? v4[j + 2] : v4[j], send = up ? v4[j] : v4[j + 2];
-        v2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        for (int j = 0; j < h; ++j) {
+            const TA keep = up ? v[j + h] : v[j], send = up ? v[j] : v[j + h];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
     }
-    const bool up = lane & 2;
-    TA v = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, up ? v2[0] : v2[1], 2);
-    return v + __shfl_xor_sync(0xffffffffu, v, 1);
+    // one value left; add over the lane bits not used above
+    TA r = v[0];
+#pragma unroll
+    for (int bit = 16 >> RsShape<B>::LOG; bit >= 1; bit >>= 1) r += __shfl_xor_sync(0xffffffffu, r, bit);
+    return r;
 }
 
 template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI>
@@ -168,10 +181,14 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
             }
         }
         if (KC == 1) {
-            // every lane worked on column c0; one reduce-scatter finishes all rows
+            // every lane worked on column c0; one reduce-scatter finishes all rows.
+            // Lanes agreeing in the bits the halving steps used hold the same row:
+            // the one with the unused low bits clear writes it.
+            constexpr int NV = RsShape<B>::NV, LOG = RsShape<B>::LOG;
             const TA v = reduce_scatter32<B>(acc, lane);
-            const int p = rs_row(lane);
-            if ((lane & 1) == 0 && p < B && cv) write_out<TX>(a, w.yrow + p, c, (TX)v, dot);
+            const int p = rs_row<NV>(lane);
+            const int owner_mask = (16 >> LOG) * 2 - 1;   // lane bits below the last halving bit
+            if ((lane & owner_mask) == 0 && p < B && cv) write_out<TX>(a, w.yrow + p, c, (TX)v, dot);
         } else {
             for (int m = KC; m < 32; m <<= 1) {
 #pragma unroll

@@ -97,6 +97,32 @@ cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t l
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
 
+// Scalar (all 1 x 1 blocks) operators: L lanes per row (2, 4 or 8 for the
+// FP64 kind, 4, 8, 16 or 32 for the others; csr_lane_class 0 and 1).
+enum CsrKind { kCsrF64 = 0, kCsrF32 = 1, kCsrF32OnF64 = 2, kCsrDF = 3 };
+int csr_lane_class(int kind);
+cudaError_t launch_csr(int kind, int L, const ProdArgs &a, cudaStream_t s);
+const void *csr_kernel_ptr(int kind, int L, int64_t k);
+
+// Thresholded block sparse product (spgemm.cu)
+struct SpgemmArgs {
+    int64_t n_out;              // output blocks
+    const int64_t *out_pbeg;    // [n_out + 1] range of each output block in the product list
+    const int64_t *out_uoff;    // packed-order offset of each output block
+    const int32_t *out_bi, *out_bj;
+    const int64_t *pa, *pb;     // panel element of A_ik[0,0] / B_kj[0,0] of every product
+    const int32_t *kpa, *kpb;   // their panel strides
+    const int32_t *bk;          // inner block size b_k
+    const void *A, *B;          // panels
+    void *C;                    // packed-order output
+    double *norms;              // [n_out] Frobenius norm of every output block
+};
+cudaError_t launch_block_norms(bool f64, int64_t nblk, const void *panel, const int64_t *pbase, const int32_t *kp,
+                               const int32_t *bi, const int32_t *bj, double *out, cudaStream_t s);
+cudaError_t launch_spgemm_numeric(bool f64, const SpgemmArgs &g, cudaStream_t s);
+cudaError_t launch_compact(bool f64, int64_t n, const int64_t *keep_src, const int64_t *dst_off, const int32_t *size,
+                           const void *src, void *dst, cudaStream_t s);
+
 // Occupancy-derived CTA count cap (SMs x resident CTAs per SM); -1 when a CUDA
 // query failed (the error stays pending for the caller to read).
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
@@ -146,6 +172,10 @@ cudaError_t launch_gershgorin(const WorkItem *items, int64_t n_items, const doub
 // panel <- (panel - c I) / d in place
 cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
                                const int32_t *pcol, const int32_t *wd, double c, double d, cudaStream_t s);
+// kernel polynomial method
+cudaError_t launch_kpm_fixup(double *mu, int64_t M, cudaStream_t s);
+cudaError_t launch_kpm_dos(const double *mu, int64_t M, int jackson, const double *x, int64_t nx, double *out,
+                           cudaStream_t s);
 // dst[rows, k] (ld ldd) = src (ld lds), FP64
 cudaError_t launch_copy_panel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst,
                               int64_t ldd, cudaStream_t s);

@@ -346,4 +346,66 @@ cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *p
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// kernel polynomial method: doubling fix-up and DOS reconstruction
+
+// raw[m] holds <t_a, t_b> / (N k) for m = 2n (a = b = n) and m = 2n+1 (a = n+1,
+// b = n), m >= 2; turn them into moments: mu_m = 2 raw[m] - mu_(m mod 2).
+__global__ void kpm_fixup_kernel(double *mu, int64_t M) {
+    const double m0 = mu[0], m1 = M > 1 ? mu[1] : 0.0;
+    for (int64_t m = 2 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x)
+        mu[m] = 2.0 * mu[m] - ((m & 1) ? m1 : m0);
+}
+
+cudaError_t launch_kpm_fixup(double *mu, int64_t M, cudaStream_t s) {
+    if (M <= 2) return cudaSuccess;
+    kpm_fixup_kernel<<<1, 256, 0, s>>>(mu, M);
+    return cudaGetLastError();
+}
+
+// rho(x) = [g_0 mu_0 + 2 sum_{n>=1} g_n mu_n T_n(x)] / (pi sqrt(1 - x^2)); g the Jackson
+// factors (jackson != 0) or 1. Each CTA computes g_n mu_n for a chunk of n into shared
+// memory; each thread runs T_n(x) = 2 x T_{n-1}(x) - T_{n-2}(x) for its own x.
+__global__ void kpm_dos_kernel(const double *mu, int64_t M, int jackson, const double *x, int64_t nx, double *out) {
+    constexpr int kChunk = 1024;
+    __shared__ double s_c[kChunk];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double xi = i < nx ? x[i] : 0.0;
+    const double q = 3.14159265358979323846 / (double)(M + 1);
+    const double cotq = cos(q) / sin(q);
+    double acc = 0.0, t_prev = 1.0, t_cur = xi;   // T_0, T_1
+    for (int64_t n0 = 0; n0 < M; n0 += kChunk) {
+        const int nc = (int)min((int64_t)kChunk, M - n0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+            const int64_t n = n0 + j;
+            double g = 1.0;
+            if (jackson) g = ((double)(M - n + 1) * cos(q * n) + sin(q * n) * cotq) / (double)(M + 1);
+            s_c[j] = (n == 0 ? 1.0 : 2.0) * g * mu[n];
+        }
+        __syncthreads();
+        for (int j = 0; j < nc; ++j) {
+            const int64_t n = n0 + j;
+            double tn;
+            if (n == 0) tn = 1.0;
+            else if (n == 1) tn = xi;
+            else {
+                tn = 2.0 * xi * t_cur - t_prev;
+                t_prev = t_cur;
+                t_cur = tn;
+            }
+            acc += s_c[j] * tn;
+        }
+    }
+    if (i < nx) out[i] = acc / (3.14159265358979323846 * sqrt(1.0 - xi * xi));
+}
+
+cudaError_t launch_kpm_dos(const double *mu, int64_t M, int jackson, const double *x, int64_t nx, double *out,
+                           cudaStream_t s) {
+    if (nx == 0) return cudaSuccess;
+    const int64_t grid = (nx + 255) / 256;
+    kpm_dos_kernel<<<(unsigned)grid, 256, 0, s>>>(mu, M, jackson, x, nx, out);
+    return cudaGetLastError();
+}
+
 }  // namespace vbcsr

@@ -154,31 +154,70 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
                         }
                         __syncwarp();
                     }
+                    if (!TRANS) {
+                        // forward: groups of U steps; all value and X loads of a group are
+                        // issued before its MMAs, so each warp has U steps of loads in flight
+                        // (U shrinks as the X fragments of wider column passes fill registers).
+                        // A window holds kKMax = 512 columns, a multiple of 16 U, so a group
+                        // never straddles two windows.
+                        constexpr int U = NT == 1 ? 4 : (NT == 2 ? 2 : 1);
+                        for (int cg = 0; cg < tn; cg += 16 * U) {
+                            float4 qa[U], qb[U];
+                            float xv[U][NT][4];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int64_t col = (int64_t)t0 + cg + 16 * u + 4 * t4;
+                                qa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                qb[u] = qa[u];
+                                if (col < w.Kp) {   // Kp is a multiple of 4: the float4 is inside the row
+                                    if (g < w.B)
+                                        qa[u] = __ldg(reinterpret_cast<const float4 *>(vals + w.vbase +
+                                                                                      (int64_t)g * w.Kp + col));
+                                    if (g + 8 < w.B)
+                                        qb[u] = __ldg(reinterpret_cast<const float4 *>(
+                                            vals + w.vbase + (int64_t)(g + 8) * w.Kp + col));
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int cl = cg + 16 * u + 4 * t4;
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const int xr = (cl + j < tn) ? s_x[cl + j] : -1;
+#pragma unroll
+                                    for (int n = 0; n < NT; ++n) {
+                                        const int64_t col = n0 + n * 8 + g;
+                                        xv[u][n][j] = (xr >= 0 && col < a.k) ? __ldg(X + (int64_t)xr * a.ldx + col)
+                                                                             : 0.f;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const float va[4] = {qa[u].x, qa[u].y, qa[u].z, qa[u].w};
+                                const float vb[4] = {qb[u].x, qb[u].y, qb[u].z, qb[u].w};
+                                Pieces pa, pb;
+                                split4<MODE>(va, pa);
+                                split4<MODE>(vb, pb);
+#pragma unroll
+                                for (int n = 0; n < NT; ++n) {
+                                    Pieces px;
+                                    split4<MODE>(xv[u][n], px);
+                                    step<MODE>(acc[n], pa, pb, px);
+                                }
+                            }
+                        }
+                        continue;
+                    }
                     for (int c16 = 0; c16 < tn; c16 += 16) {
                         const int cl = c16 + 4 * t4;   // first of this lane's 4 columns, window-relative
                         float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
-                        if (!TRANS) {
-                            const int64_t col = (int64_t)t0 + cl;
-                            if (col < w.Kp) {   // Kp is a multiple of 4: the float4 is inside the row
-                                if (g < w.B) {
-                                    const float4 q = __ldg(reinterpret_cast<const float4 *>(
-                                        vals + w.vbase + (int64_t)g * w.Kp + col));
-                                    va[0] = q.x; va[1] = q.y; va[2] = q.z; va[3] = q.w;
-                                }
-                                if (g + 8 < w.B) {
-                                    const float4 q = __ldg(reinterpret_cast<const float4 *>(
-                                        vals + w.vbase + (int64_t)(g + 8) * w.Kp + col));
-                                    vb[0] = q.x; vb[1] = q.y; vb[2] = q.z; vb[3] = q.w;
-                                }
-                            }
-                        } else {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                if (cl + j < tn) {
-                                    const float *base = vals + s_a[cl + j];
-                                    if (g < w.B) va[j] = __ldg(base + g);
-                                    if (g + 8 < w.B) vb[j] = __ldg(base + g + 8);
-                                }
+                        for (int j = 0; j < 4; ++j) {
+                            if (cl + j < tn) {
+                                const float *base = vals + s_a[cl + j];
+                                if (g < w.B) va[j] = __ldg(base + g);
+                                if (g + 8 < w.B) vb[j] = __ldg(base + g + 8);
                             }
                         }
                         Pieces pa, pb;

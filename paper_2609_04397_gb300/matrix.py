@@ -123,6 +123,11 @@ class VBCSR:
         return (int(self.info.n_rows), int(self.info.n_cols))
 
     @property
+    def backend(self) -> str:
+        """'csr', 'bsr' or 'vbcsr' (chosen from the block sizes)."""
+        return ("csr", "bsr", "vbcsr")[self.info.backend]
+
+    @property
     def nnz(self) -> int:
         return int(self.info.nnz)
 
@@ -144,10 +149,13 @@ class VBCSR:
         """Column tile and CTA width of the bucket of row count B (0: all)."""
         check(lib().vbcsr_set_bucket_tuning(self._h, B, kc, warps), "vbcsr_set_bucket_tuning")
 
-    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0, mma_staged: bool = False):
+    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0, mma_staged: bool = False,
+                     scalar_kernel: bool = True):
         """'bucketed' (one launch per row count) or 'persistent' (one launch);
-        mma_staged selects the shared-memory-staged tensor-core forward kernel."""
-        code = {"bucketed": 0, "persistent": 1}[schedule] | (2 if mma_staged else 0)
+        mma_staged selects the shared-memory-staged tensor-core forward kernel;
+        scalar_kernel=False makes a CSR-backend operator use the block-row kernels."""
+        code = ({"bucketed": 0, "persistent": 1}[schedule] | (2 if mma_staged else 0)
+                | (0 if scalar_kernel else 4))
         check(lib().vbcsr_set_schedule(self._h, code, persist_warps), "vbcsr_set_schedule")
 
     def get_tuning(self) -> dict:
@@ -315,6 +323,39 @@ class VBCSR:
                                     ckpt_every, _prec(precision), _stream(self.device)), "vbcsr_chebyshev")
         return mom, ck
 
+    def kpm_moments(self, R, n_moments: int, precision="native"):
+        """KPM moments of a symmetric operator scaled to [-1, 1], by the
+        doubling identities (about half the products of chebyshev())."""
+        R, ldr = self._panel(R, self.shape[0], "R")
+        k = R.shape[1]
+        mom = torch.empty(n_moments, dtype=torch.float64, device=self.device)
+        work = torch.empty(2 * self.shape[0] * k, dtype=torch.float64, device=self.device)
+        check(lib().vbcsr_kpm_moments(self._h, k, ctypes.c_void_p(R.data_ptr()), ldr, n_moments,
+                                      ctypes.c_void_p(mom.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                                      _prec(precision), _stream(self.device)), "vbcsr_kpm_moments")
+        return mom
+
+    def spgemm(self, other: "VBCSR", eps: float = 0.0) -> "VBCSR":
+        """C = self @ other with the block-norm threshold eps (Eqs. 2-3)."""
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().vbcsr_spgemm(self._h, other._h, float(eps), ctypes.byref(h), _stream(self.device)),
+                  "vbcsr_spgemm")
+        C = VBCSR(h, self._dtype, self.device, None)
+        C.pattern = C.read_pattern()
+        return C
+
+    def read_pattern(self):
+        """(row_bsize, col_bsize, block_row_ptr, block_col_idx) held by the handle."""
+        i = self.info
+        rb = np.zeros(i.n_brows, np.int32)
+        cb = np.zeros(i.n_bcols, np.int32)
+        rp = np.zeros(i.n_brows + 1, np.int64)
+        ci = np.zeros(i.nblk, np.int32)
+        check(lib().vbcsr_get_pattern(self._h, rb.ctypes.data, cb.ctypes.data, rp.ctypes.data, ci.ctypes.data),
+              "vbcsr_get_pattern")
+        return rb, cb, rp, ci
+
     def gershgorin(self):
         """(E_min, E_max): Gershgorin bounds of the spectrum, computed on the GPU."""
         out = torch.empty(2, dtype=torch.float64, device=self.device)
@@ -329,3 +370,35 @@ class VBCSR:
 
     def __matmul__(self, X):
         return self.spmm(X)
+
+
+def kpm_dos(moments: torch.Tensor, x: torch.Tensor, kernel: str = "jackson") -> torch.Tensor:
+    """Density of states at scaled energies x (device tensors, FP64) from KPM
+    moments, with Jackson damping (kernel='jackson') or none ('none')."""
+    moments = moments.contiguous()
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    code = {"none": 0, "jackson": 1}[kernel]
+    check(lib().vbcsr_kpm_dos(ctypes.c_void_p(moments.data_ptr()), moments.numel(), code,
+                              ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(out.data_ptr()),
+                              _stream(x.device)), "vbcsr_kpm_dos")
+    return out
+
+
+def kpm_gap(energies, dos, reference: float, threshold: float):
+    """Width of the largest interval around `reference` on the energy grid
+    where the DOS stays below `threshold` (host-side post-processing of the
+    reconstructed DOS): returns (E_low, E_high) or None if dos(reference) is
+    above the threshold."""
+    E = np.asarray(energies, dtype=np.float64)
+    D = np.asarray(dos, dtype=np.float64)
+    i = int(np.argmin(np.abs(E - reference)))
+    if D[i] >= threshold:
+        return None
+    lo = i
+    while lo > 0 and D[lo - 1] < threshold:
+        lo -= 1
+    hi = i
+    while hi + 1 < len(E) and D[hi + 1] < threshold:
+        hi += 1
+    return float(E[lo]), float(E[hi])

@@ -8,6 +8,7 @@ geometric graphs; Sec. V zinc-blende nanoparticles):
                           blocks to the third neighbour shell plus self
 * ``amorphous``           random sequential placement, b in {4, 9, 13} 40/40/20
 * ``batched_uneven``      many independent periodic structures of uneven size
+* ``domain``              ~500 MiB scalar / uniform-block / variable-block graphs
 
 Values follow a symmetric construction (H_ji = H_ij^T). All random numbers
 come from the counter-based generator in gen.c; nothing here computes a
@@ -165,3 +166,28 @@ def batched_uneven(n_structs: int = 256, n_min: int = 50, n_max: int = 2000,
     wl = Workload(f"batched_{n_structs}", pat, vals, None, boffs, boffs.copy())
     wl.parts = pats
     return wl
+
+
+def domain(kind: str, target_bytes: float = 500 * 2 ** 20, seed: int = 0) -> Workload:
+    """Atom-like periodic geometric graphs sized to ~target_bytes of stored
+    values and indices, in the three structural domains of the paper's kernel
+    benchmark (Sec. IV): 'csr' (every b = 1), 'bsr' (every b = 8) and 'vbcsr'
+    (b uniform at random in [9, 20]). Cube at density 0.0488 / A^3 with a
+    5 A cutoff plus self (~26 blocks per row); entries as tiny_multispecies."""
+    rng = np.random.default_rng(seed)
+    dens, cutoff, deg = 0.0488, 5.0, 26.6
+    # stored bytes per block row: blocks x (values + one column index)
+    per_row = {"csr": deg * (8 + 4), "bsr": deg * (64 * 8 + 4), "vbcsr": deg * (14.5 ** 2 * 8 + 4)}[kind]
+    n = int(target_bytes / per_row)
+    side = (n / dens) ** (1.0 / 3.0)
+    pos = rng.uniform(0.0, side, size=(n, 3))
+    if kind == "csr":
+        b = np.ones(n, np.int32)
+    elif kind == "bsr":
+        b = np.full(n, 8, np.int32)
+    else:
+        b = rng.integers(9, 21, size=n).astype(np.int32)
+    sys = _ordered(AtomSystem(pos, b, side))
+    pat = neighbor_pattern(sys, cutoff)
+    vals = symmetric_values(pat, nnz_row_scale(pat), seed)
+    return Workload(f"domain_{kind}_{n}", pat, vals, sys)

@@ -8,6 +8,7 @@ import torch
 
 import oracle
 import synthetic as syn
+from _fd import central_difference
 
 pytestmark = pytest.mark.gpu
 
@@ -94,18 +95,10 @@ def test_gradient_through_shift_scale_and_fd():
     (mu ** 2).sum().backward()
     g = v.grad.cpu().numpy()
 
-    def loss(vals):
-        return oracle.moment_loss(w.pattern, oracle.shift_scale_values(w.pattern, vals, c, d), R, 30)
-
     h = 1e-6
     idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
-    fd = []
-    for i in idx:
-        vp, vm = w.values.copy(), w.values.copy()
-        vp[i] += h
-        vm[i] -= h
-        fd.append((loss(vp) - loss(vm)) / (2 * h))
-    fd = np.array(fd)
+    # dL/dH = dL/dH~ / d: the central difference in H~ at step h / d is the one in H at step h
+    fd = np.array([central_difference(w.pattern, vt, R, 30, i, h / d) / d for i in idx])
     # max-norm relative deviation over the sampled entries
     assert np.abs(fd - g[idx]).max() <= 1e-6 * np.abs(g[idx]).max()
 
@@ -153,27 +146,15 @@ def test_amorphous_20k_gradient_fd_50_entries():
     nthreads = os.cpu_count() or 1
     pat = w.pattern
 
-    def loss(vals):
-        t0 = R
-        t1 = oracle.spmm(pat, vals, t0, nthreads=nthreads)
-        mu = [np.sum(R * t0) / R.size, np.sum(R * t1) / R.size]
-        for n in range(1, 29):
-            t0, t1 = t1, oracle.spmm(pat, vals, t1, 2.0, -1.0, t0, nthreads=nthreads)
-            mu.append(np.sum(R * t1) / R.size)
-        return float(np.sum(np.square(mu)))
-
     h = 1e-6
     idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
-    fd = []
-    for i in idx:
-        vp, vm = vt.copy(), vt.copy()
-        vp[i] += h
-        vm[i] -= h
-        fd.append((loss(vp) - loss(vm)) / (2 * h))
-    fd = np.array(fd)
+    fd = np.array([central_difference(pat, vt, R, 30, i, h, nthreads) for i in idx])
     worst = np.abs(fd - g[idx]).max() / np.abs(g[idx]).max()
     print(f"amorphous 20k: max-norm relative FD deviation over 50 entries = {worst:.3e}")
     assert worst <= 1e-6
+    # and the exact reverse-mode gradient of the oracle, every stored entry
+    ref = oracle.moment_loss_grad(pat, vt, R, 30)
+    assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
 def test_gershgorin_and_shift_scale_on_gpu():

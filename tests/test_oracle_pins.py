@@ -261,3 +261,117 @@ def test_gershgorin_matches_dense_definition():
     rad = np.abs(H).sum(axis=1) - np.abs(d)
     lo, hi = oracle.gershgorin_bounds(pat, v)
     assert abs(lo - (d - rad).min()) < 1e-13 and abs(hi - (d + rad).max()) < 1e-13
+
+
+def test_kpm_doubling_moments_equal_direct_recurrence():
+    """T_{2n} = 2 T_n^2 - 1 and T_{2n+1} = 2 T_{n+1} T_n - T_1 for a symmetric H."""
+    w = syn.tiny_multispecies(0)
+    c, d = oracle.cheb_scale(w.pattern, w.values)
+    vt = oracle.shift_scale_values(w.pattern, w.values, c, d)
+    R = syn.rademacher_panel(w.pattern.n_rows, 4, 2)
+    for M in (1, 2, 3, 10, 31):
+        a = oracle.kpm_moments_doubling(w.pattern, vt, R, M)
+        b = oracle.chebyshev_moments(w.pattern, vt, R, M)
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_jackson_kernel_and_dos_normalisation():
+    M = 64
+    g = oracle.jackson_kernel(M)
+    assert abs(g[0] - 1.0) < 1e-15 and np.all(np.diff(g) < 0) and g[-1] > 0
+    # Chebyshev-Gauss quadrature on J > M nodes integrates rho exactly: integral = g_0 mu_0
+    J = 4 * M
+    xj = np.cos(np.pi * (np.arange(J) + 0.5) / J)
+    mu = np.random.default_rng(0).uniform(-1, 1, M)
+    mu[0] = 1.0
+    rho = oracle.kpm_dos(mu, xj)
+    integral = np.sum(rho * np.pi * np.sqrt(1 - xj ** 2)) / J
+    assert abs(integral - 1.0) < 1e-13
+
+
+def test_jackson_damped_delta_is_positive_and_localised():
+    """The Jackson-damped expansion of a delta at x0 (mu_n = T_n(x0)) is
+    non-negative and concentrated within a few pi/M of x0."""
+    M, x0 = 128, 0.3
+    mu = np.cos(np.arange(M) * np.arccos(x0))
+    x = np.linspace(-0.999, 0.999, 4001)
+    rho = oracle.kpm_dos(mu, x)
+    assert rho.min() > -1e-12
+    w = np.abs(x - x0) < 6 * np.pi / M
+    dx = x[1] - x[0]
+    assert np.sum(rho[w]) * dx > 0.99
+
+
+def test_kpm_dos_of_diagonal_operator_counts_eigenvalues():
+    """DOS of a diagonal H~ with exact traces (R = sqrt(N) I) integrates to the
+    fraction of eigenvalues inside an interval (within the kernel's width)."""
+    h = np.concatenate([np.full(30, -0.5), np.full(10, 0.4)])
+    n = len(h)
+    pat = BlockPattern(np.ones(n), np.ones(n), np.arange(n + 1), np.arange(n))
+    mu = oracle.kpm_moments_doubling(pat, h, np.sqrt(n) * np.eye(n), 200)
+    x = np.linspace(-0.999, 0.999, 8001)
+    rho = oracle.kpm_dos(mu, x)
+    dx = x[1] - x[0]
+    assert abs(np.sum(rho[x < 0]) * dx - 0.75) < 1e-3
+    assert abs(np.sum(rho[x > 0]) * dx - 0.25) < 1e-3
+
+
+def test_central_difference_helper_against_plain_differences():
+    """The cancellation-free central difference (tests/_fd.py) equals the
+    plain (L+ - L-) / 2h at a step where the plain one is accurate."""
+    from _fd import central_difference
+    pat = syn.random_pattern(9, 9, (1, 2, 4), 0.35, 11)
+    pat = syn.BlockPattern(pat.row_bsize, pat.row_bsize, pat.block_row_ptr, pat.block_col_idx)
+    v = 0.3 * syn.random_values(pat, 11)
+    R = syn.rademacher_panel(pat.n_rows, 3, 2)
+    for i in (0, 7, len(v) - 1):
+        h = 1e-3
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        plain = (oracle.moment_loss(pat, vp, R, 8) - oracle.moment_loss(pat, vm, R, 8)) / (2 * h)
+        assert abs(central_difference(pat, v, R, 8, i, h) - plain) <= 1e-9 * max(1.0, abs(plain))
+
+
+
+
+def test_spgemm_eps0_is_dense_product():
+    """With eps = 0 every block reached by a product path is kept and C = A B."""
+    pa = syn.random_pattern(12, 9, (1, 3, 4), 0.3, 41)
+    pb = syn.random_pattern(9, 11, (2, 5), 0.3, 42)
+    pb = BlockPattern(pa.col_bsize, pb.col_bsize, pb.block_row_ptr, pb.block_col_idx)
+    va, vb = syn.random_values(pa, 41), syn.random_values(pb, 42)
+    rb, cb, ptr, cols, vals = oracle.spgemm(pa, va, pb, vb, 0.0)
+    C = oracle.to_dense(BlockPattern(rb, cb, ptr, cols), vals)
+    ref = oracle.to_dense(pa, va) @ oracle.to_dense(pb, vb)
+    assert np.abs(C - ref).max() < 1e-13
+    # every structurally reachable block is present, none else
+    A0, B0 = oracle.to_dense(pa, np.ones(pa.nnz)), oracle.to_dense(pb, np.ones(pb.nnz))
+    reach = (A0 @ B0) > 0
+    present = oracle.to_dense(BlockPattern(rb, cb, ptr, cols), np.ones(len(vals))) > 0
+    assert np.array_equal(reach, present)
+
+
+def test_spgemm_threshold_respects_norm_bound():
+    """Dropped blocks have true norm below eps (the Eq. 3 bound makes the
+    symbolic drop safe); kept blocks equal the exact product blocks."""
+    pa = syn.random_pattern(15, 15, (2, 3), 0.3, 43)
+    pa = BlockPattern(pa.row_bsize, pa.row_bsize, pa.block_row_ptr, pa.block_col_idx)
+    va = syn.random_values(pa, 43) * np.exp(-np.random.default_rng(0).uniform(0, 6, pa.nnz))
+    exact = oracle.to_dense(pa, va) @ oracle.to_dense(pa, va)
+    r = np.concatenate([[0], np.cumsum(pa.row_bsize)])
+    eps = 0.5
+    rb, cb, ptr, cols, vals = oracle.spgemm(pa, va, pa, va, eps)
+    C = oracle.to_dense(BlockPattern(rb, cb, ptr, cols), vals)
+    kept = set()
+    for i in range(len(rb)):
+        for u in range(ptr[i], ptr[i + 1]):
+            kept.add((i, int(cols[u])))
+    for i in range(len(rb)):
+        for j in range(len(rb)):
+            blk = exact[r[i]:r[i + 1], r[j]:r[j + 1]]
+            if (i, j) in kept:
+                assert np.allclose(C[r[i]:r[i + 1], r[j]:r[j + 1]], blk, atol=1e-13)
+                assert np.linalg.norm(blk) >= eps - 1e-12
+            else:
+                assert np.linalg.norm(blk) < eps + 1e-12

@@ -224,10 +224,15 @@ def test_zincblende_full_size_sampled_rows():
     H.check()
 
 
+@pytest.mark.parametrize("sizes,precision", [((4, 9, 13), "native"), ((1,), "native"), ((1,), "df32"),
+                                              ((1,), "f32")])
 @pytest.mark.parametrize("transpose", [False, True])
-def test_fused_epilogue_gamma_z_and_dot(transpose):
-    """Y = alpha op(H) X + beta Y + gamma Z and dot = sum(R * Y) through vbcsr_spmm_ex."""
-    pat = syn.random_pattern(33, 33, (4, 9, 13), 0.2, 21)
+def test_fused_epilogue_gamma_z_and_dot(transpose, sizes, precision):
+    """Y = alpha op(H) X + beta Y + gamma Z and dot = sum(R * Y) through
+    vbcsr_spmm_ex, on a variable-block operator and on a scalar one (whose
+    forward product runs in the scalar kernel, in each arithmetic kind)."""
+    n = 33 if sizes != (1,) else 200
+    pat = syn.random_pattern(n, n, sizes, 0.2, 21)
     vals = syn.random_values(pat, 21)
     H = _handle(pat, vals)
     rng = np.random.default_rng(3)
@@ -238,12 +243,15 @@ def test_fused_epilogue_gamma_z_and_dot(transpose):
     R = rng.standard_normal((n_out, 5))
     Yd = _dev(Y0)
     dot = torch.zeros(1, dtype=torch.float64, device="cuda:0")
-    H.spmm_ex(_dev(X), 2.0, -1.0, Yd, transpose=transpose, gamma=0.5, Z=_dev(Z), R=_dev(R), dot_out=dot)
+    H.spmm_ex(_dev(X), 2.0, -1.0, Yd, transpose=transpose, gamma=0.5, Z=_dev(Z), R=_dev(R), dot_out=dot,
+              precision=precision)
     fn = oracle.spmm_adjoint if transpose else oracle.spmm
     ref = fn(pat, vals, X, 2.0, -1.0, Y0) + 0.5 * Z
     got = Yd.cpu().numpy()
-    assert rel_fro(got, ref) <= TOL_F64
-    assert abs(dot.item() - np.sum(R * ref)) <= 1e-12 * np.sum(np.abs(R * ref))
+    tol = TOL_MIXED if precision == "f32" else TOL_F64
+    assert rel_fro(got, ref) <= tol
+    # the dot is of the stored Y: exact to FP64 rounding of the sum in every mode
+    assert abs(dot.item() - np.sum(R * got)) <= 1e-12 * np.sum(np.abs(R * got))
 
 
 @pytest.mark.parametrize("sizes", SIZES)
@@ -275,3 +283,53 @@ def test_df32_mode_zincblende_sampled_rows():
     # and the FP32 copy is not what it used: the plain FP32 mode is far less accurate
     got32 = H.spmm(_dev(X), precision="f32").cpu().numpy()
     assert rel_fro(got32, ref) > 100 * rel_fro(got, ref)
+
+
+def test_backend_selection():
+    w = syn.tiny_multispecies(0)
+    assert _handle(w.pattern, w.values).backend == "vbcsr"
+    n = 50
+    rng = np.random.default_rng(0)
+    mask = rng.random((n, n)) < 0.1
+    np.fill_diagonal(mask, True)
+    ptr = np.concatenate([[0], np.cumsum(mask.sum(1))])
+    cols = np.concatenate([np.nonzero(mask[i])[0] for i in range(n)])
+    for b, name in ((1, "csr"), (8, "bsr")):
+        pat = BlockPattern(np.full(n, b), np.full(n, b), ptr, cols)
+        assert _handle(pat, syn.random_values(pat, 1)).backend == name
+
+
+@pytest.mark.parametrize("density", [0.02, 0.2, 0.6, 1.0])
+@pytest.mark.parametrize("k", [1, 3, 8, 9, 17])
+def test_csr_backend_scalar_kernel(density, k):
+    """Scalar operators (all blocks 1 x 1) through the scalar kernel, against
+    the oracle and against the block-row kernels on the same operator. The
+    densities give ~5, ~52, ~156 and 300 entries per row, so every lane count
+    the kernel picks from the row length (2, 4, 8 for FP64; 4 to 32 for FP32)
+    runs."""
+    pat = syn.random_pattern(300, 300, (1,), density, 90 + k, empty_rows=7, unsorted=True)
+    vals = syn.random_values(pat, 90 + k)
+    H = _handle(pat, vals)
+    assert H.backend == "csr"
+    for alpha, beta in ((1.0, 0.0), (2.0, -1.0), (0.0, 0.5)):
+        _run_forward(H, pat, vals, k, alpha, beta, ld_extra=1, seed=k)
+    Xh = np.random.default_rng(k).standard_normal((pat.n_cols, k))
+    X = _dev(Xh)
+    Ys = H.spmm(X)
+    H.set_schedule("bucketed", scalar_kernel=False)
+    Yb = H.spmm(X)
+    # the two kernels sum a row in different orders: they agree to the
+    # forward-error scale of a reordered dot product, 1e-12 (|H| |X|)
+    _, scale = forward_ref(pat, vals, Xh, 1.0, 0.0, None)
+    check_elementwise(Ys.cpu().numpy(), Yb.cpu().numpy(), scale, TOL_F64)
+    H32 = _handle(pat, vals.astype(np.float32), torch.float32)
+    _run_forward(H32, pat, vals.astype(np.float32).astype(np.float64), k, 1.0, 0.0, tol=TOL_MIXED)
+    # the FP64-accurate double-FP32 mode and FP32 products run in the scalar kernel too
+    H.set_schedule("bucketed")
+    _run_forward(H, pat, vals, k, 2.0, -1.0, ld_extra=1, seed=k + 1, precision="df32")
+    Y0 = np.random.default_rng(k + 2).standard_normal((pat.n_rows, k))
+    Yd = _dev(Y0)
+    H.spmm(X, 2.0, -1.0, Yd, precision="f32")
+    ref, scale = forward_ref(pat, vals, Xh, 2.0, -1.0, Y0)
+    assert rel_fro(Yd.cpu().numpy(), ref) <= TOL_MIXED
+    check_elementwise(Yd.cpu().numpy(), ref, scale, 1e-4)
