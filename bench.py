@@ -53,9 +53,9 @@ FP64_PEAK_TFLOPS = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 TRAFFIC_F64_K32 = 806001408 + 54032384 + 1060621568 + 76182784
 
 
-def _workload():
+def _workload(n_atoms=N_ATOMS):
     import synthetic as syn
-    return syn.zincblende(N_ATOMS, seed=0)
+    return syn.zincblende(n_atoms, seed=0)
 
 
 def _alg_bytes(pat, k, value_bytes=8):
@@ -249,23 +249,24 @@ def domains_section(dev, steps):
         H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
         res = {"atoms": pat.n_brows, "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk,
                "value_bytes": 8 * pat.nnz, "backend": H.backend}
-        # default schedule; the block-row kernels on the scalar domain; one
-        # persistent launch and the autotuned choice on the block domains
+        # default (persistent) schedule; the block-row kernels on the scalar
+        # domain; one launch per row count and the autotuned choice on the
+        # block domains
         variants = [("", {})]
         if kind == "csr":
             variants.append(("_blockrow", {"scalar_kernel": False}))
         else:
-            variants += [("_persistent", {"schedule": "persistent"}), ("_tuned", None)]
+            variants += [("_bucketed", {"schedule": "bucketed"}), ("_tuned", None)]
         for tag, sched in variants:
             if sched is not None:
                 sched = dict(sched)
-                H.set_schedule(sched.pop("schedule", "bucketed"), **sched)
+                H.set_schedule(sched.pop("schedule", "persistent"), **sched)
             for k in (1, 16):
                 for prec in ("native", "df32"):
                     X = torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev)
                     Y = torch.empty(pat.n_rows, k, dtype=torch.float64, device=dev)
                     if sched is None:
-                        H.set_schedule("bucketed")
+                        H.set_schedule("persistent")
                         H.autotune(k, precision=prec)
                     for _ in range(3):
                         H.spmm(X, 1.0, 0.0, Y, precision=prec)
@@ -293,7 +294,7 @@ def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    w = _workload()
+    w = _workload(args.atoms)
     pat = w.pattern
     import oracle
     cores = os.cpu_count() or 1
@@ -342,7 +343,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     hbm_peak, peak_src = _peaks()
 
-    w = _workload()
+    w = _workload(args.atoms)
     pat = w.pattern
     H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
     stream = torch.cuda.current_stream(dev)
@@ -410,7 +411,7 @@ def run_ours(args):
     variants = [("df32", False), ("bf16x2", False), ("bf16x2", True), ("tf32x3", False), ("tf32x3", True),
                 ("f32", False)]
     for mode, staged in variants:
-        H.set_schedule("bucketed", mma_staged=staged)
+        H.set_schedule("persistent", mma_staged=staged)
         for k in KS:
             H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
         torch.cuda.synchronize(dev)
@@ -443,7 +444,7 @@ def run_ours(args):
         mixed[mode + ("_staged" if staged else "")] = {
             "ms_per_step": ms, "speedup_vs_f64": (total_ms / args.steps) / ms,
             "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9, "per_k": mk}
-    H.set_schedule("bucketed")
+    H.set_schedule("persistent")
 
     # ---- end to end through the public API: pinned host X in, Y out, every step ----
     hX = {k: torch.randn(pat.n_cols, k, dtype=torch.float64).pin_memory() for k in KS}
@@ -502,6 +503,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--atoms", type=int, default=N_ATOMS,
+                    help="zinc-blende target atom count (a smaller case for profiler captures)")
     ap.add_argument("--domains", action="store_true",
                     help="also measure the CSR / BSR / VBCSR domains (~500 MiB each)")
     args = ap.parse_args()

@@ -24,7 +24,10 @@
  *    an invalid call launches nothing and leaves its outputs untouched.
  *  - Pointers are borrowed for the duration of the call only. Device pointers
  *    must belong to the device that was current at vbcsr_create.
- *  - A handle may be used from one host thread at a time.
+ *  - A handle may be used from one host thread at a time, and its compute
+ *    calls must not overlap on the GPU (issue them on one stream, or order the
+ *    streams): the handle's work counter, converted-X buffers and dot partials
+ *    are shared by its calls.
  */
 #ifndef VBCSR_H
 #define VBCSR_H
@@ -86,13 +89,17 @@ typedef enum {
 
 /* Launch schedules of the CUDA-core products (vbcsr_set_schedule). */
 typedef enum {
-    VBCSR_SCHED_BUCKETED = 0,     /* one launch per work-item row count (default)      */
+    VBCSR_SCHED_BUCKETED = 0,     /* one launch per work-item row count                */
     VBCSR_SCHED_PERSISTENT = 1,   /* one launch over all items, costliest first, warps
-                                     taking items from a device work counter           */
+                                     taking items from a device work counter (default:
+                                     no per-launch tail, which at large k is ~1 item
+                                     per warp and dominates a launch of few waves)     */
     VBCSR_SCHED_MMA_STAGED = 2,   /* flag: the tensor-core forward kernel stages value
                                      panels in shared memory with bulk async copies   */
     VBCSR_SCHED_NO_CSR = 4        /* flag: a CSR-backend operator uses the block-row
-                                     kernels instead of the scalar kernel             */
+                                     kernels instead of the scalar kernel (which
+                                     otherwise serves its forward products under
+                                     either schedule)                                  */
 } vbcsr_schedule;
 
 /* Flags of vbcsr_autotune. */

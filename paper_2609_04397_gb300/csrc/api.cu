@@ -89,7 +89,7 @@ struct vbcsr_matrix {
     int csr_lanes[2] = {2, 8};      // lanes per row of the scalar kernel: FP64 / FP32-pipe kinds
     int kc_b[kMaxB + 1] = {0};      // column tile per row count (0: from k)
     int warps_b[kMaxB + 1] = {0};   // warps per CTA per row count (0: 4)
-    int schedule = 0;               // 0: one launch per row count, 1: one persistent launch
+    int schedule = VBCSR_SCHED_PERSISTENT;   // or one launch per row count (VBCSR_SCHED_BUCKETED)
     int persist_warps = 0;          // warps per CTA of the persistent launch (0: 4)
     int debug_checks = 0;
 
@@ -264,9 +264,9 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
         A->backend = scalar ? VBCSR_BACKEND_CSR : (uniform ? VBCSR_BACKEND_BSR : VBCSR_BACKEND_VBCSR);
         if (scalar) {
             // FP64 operations are charged per warp instruction on GB300's narrow FP64
-            // pipe, so an FP64 row gets few lanes (every instruction carries ~32 useful
-            // lanes, the finishing butterfly is short); FP32 rows get more lanes for
-            // coalesced loads
+            // pipe, so an FP64 (or double-FP32) row gets few lanes (every instruction
+            // carries ~32 useful lanes, the finishing butterfly is short); FP32 rows
+            // get more lanes for coalesced loads
             const double avg = n_brows > 0 ? (double)nblk / (double)n_brows : 0.0;
             A->csr_lanes[0] = avg <= 64 ? 2 : (avg <= 256 ? 4 : 8);
             A->csr_lanes[1] = avg <= 8 ? 4 : (avg <= 24 ? 8 : (avg <= 64 ? 16 : 32));
@@ -657,10 +657,10 @@ extern "C" int vbcsr_get_values(const vbcsr_t *Ac, void *values, int on_device, 
 // products
 
 namespace vbcsr {
-const void *fma_f64_kernel(bool trans, bool persistent);
-const void *fma_f32_kernel(bool trans, bool persistent);
-const void *fma_f32_on_f64_kernel(bool trans, bool persistent);
-const void *fma_df_kernel(bool trans, bool persistent);
+const void *fma_f64_kernel(bool trans, bool persistent, int B);
+const void *fma_f32_kernel(bool trans, bool persistent, int B);
+const void *fma_f32_on_f64_kernel(bool trans, bool persistent, int B);
+const void *fma_df_kernel(bool trans, bool persistent, int B);
 const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int64_t k);
 }  // namespace vbcsr
 
@@ -812,10 +812,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
         return VBCSR_OK;
     };
-    auto fma_kern = [&](bool persistent) {
-        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent);
-        return (mode == VBCSR_PREC_NATIVE) ? (f64 ? fma_f64_kernel(trans, persistent) : fma_f32_kernel(trans, persistent))
-                                           : fma_f32_on_f64_kernel(trans, persistent);
+    auto fma_kern = [&](bool persistent, int B) {
+        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B);
+        return (mode == VBCSR_PREC_NATIVE)
+                   ? (f64 ? fma_f64_kernel(trans, persistent, B) : fma_f32_kernel(trans, persistent, B))
+                   : fma_f32_on_f64_kernel(trans, persistent, B);
     };
     const int64_t n_all = trans ? A->n_adj_items : A->n_fwd_items;
     int rc = VBCSR_OK;
@@ -827,7 +828,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
     } else if (A->backend == VBCSR_BACKEND_CSR && !trans &&
-               !(A->schedule & (VBCSR_SCHED_NO_CSR | VBCSR_SCHED_PERSISTENT))) {
+               !(A->schedule & VBCSR_SCHED_NO_CSR)) {
         // scalar operator: several rows per warp; items are the scalar rows in page order
         const int kind = mode == VBCSR_PREC_DF32 ? kCsrDF
                        : mode == VBCSR_PREC_F32 ? kCsrF32OnF64 : (f64 ? kCsrF64 : kCsrF32);
@@ -857,14 +858,14 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         a.queue = A->queue;
         CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         const int warps = A->persist_warps ? A->persist_warps : 4;
-        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps, fma_kern(true), fma_smem_bytes(trans, warps));
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps, fma_kern(true, 0), fma_smem_bytes(trans, warps));
     } else {
         const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
         const WorkItem *items = trans ? A->adj_items : A->fwd_items;
         for (const Bucket &b : buckets) {
             a.kc = kc_for(b.B);
             const int warps = A->warps_b[b.B] ? A->warps_b[b.B] : 4;
-            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false), fma_smem_bytes(trans, warps));
+            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false, b.B), fma_smem_bytes(trans, warps));
             if (rc) return rc;
         }
     }

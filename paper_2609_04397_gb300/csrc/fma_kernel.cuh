@@ -317,14 +317,25 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
     return cudaGetLastError();
 }
 
+// The kernel a launch runs (persistent, or the bucket kernel of row count B),
+// for its occupancy-derived grid size.
 template <typename TV, typename TA, typename TX, typename TXI>
-const void *fma_kernel_ptr(bool trans, bool persistent) {
-    // B = 16 is the largest register footprint of the bucketed kernels
+const void *fma_kernel_ptr(bool trans, bool persistent, int B) {
     if (persistent)
         return trans ? (const void *)fma_persistent_kernel<true, TV, TA, TX, TXI>
                      : (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;
-    return trans ? (const void *)fma_product_kernel<16, true, TV, TA, TX, TXI>
-                 : (const void *)fma_product_kernel<16, false, TV, TA, TX, TXI>;
+#define VBCSR_PTR_CASE(NB)                                                                 \
+    case NB:                                                                               \
+        return trans ? (const void *)fma_product_kernel<NB, true, TV, TA, TX, TXI>         \
+                     : (const void *)fma_product_kernel<NB, false, TV, TA, TX, TXI>;
+    switch (B) {
+        VBCSR_PTR_CASE(1) VBCSR_PTR_CASE(2) VBCSR_PTR_CASE(3) VBCSR_PTR_CASE(4)
+        VBCSR_PTR_CASE(5) VBCSR_PTR_CASE(6) VBCSR_PTR_CASE(7) VBCSR_PTR_CASE(8)
+        VBCSR_PTR_CASE(9) VBCSR_PTR_CASE(10) VBCSR_PTR_CASE(11) VBCSR_PTR_CASE(12)
+        VBCSR_PTR_CASE(13) VBCSR_PTR_CASE(14) VBCSR_PTR_CASE(15) VBCSR_PTR_CASE(16)
+        default: return nullptr;
+    }
+#undef VBCSR_PTR_CASE
 }
 
 }  // namespace vbcsr

@@ -31,6 +31,14 @@ constexpr int kMaxB = 16;        // rows per work item
 constexpr int kPadK = 8;         // panel width padding (elements)
 constexpr int kKMax = 512;       // virtual columns staged in shared memory per pass
 constexpr int kPartialsCap = 1 << 16;
+constexpr uint32_t kPrefetchMax = 256u << 10;   // bytes of one item's values prefetched into L2
+
+// Hint that [p, p + bytes) be brought into L2 ahead of use (one bulk request:
+// nothing moves into the SM, nothing waits, no fault for an in-bounds range).
+// p must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // One warp task.
 struct WorkItem {
@@ -98,7 +106,8 @@ cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t l
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
 
 // Scalar (all 1 x 1 blocks) operators: L lanes per row (2, 4 or 8 for the
-// FP64 kind, 4, 8, 16 or 32 for the others; csr_lane_class 0 and 1).
+// FP64 and double-FP32 kinds, 4, 8, 16 or 32 for the FP32 ones; csr_lane_class
+// 0 and 1).
 enum CsrKind { kCsrF64 = 0, kCsrF32 = 1, kCsrF32OnF64 = 2, kCsrDF = 3 };
 int csr_lane_class(int kind);
 cudaError_t launch_csr(int kind, int L, const ProdArgs &a, cudaStream_t s);

@@ -93,10 +93,12 @@ namespace {
 int csr_cw(int64_t k) { return k == 1 ? 1 : (k <= 4 ? 4 : 8); }
 
 // Kernel of lane count L and column tile CW for arithmetic kind <TV, TA, TX, TXI>.
-// FP64 rows use 2, 4 or 8 lanes; the FP32-pipe kinds 4, 8, 16 or 32.
+// FP64 and double-FP32 rows use 2, 4 or 8 lanes (an FP64 instruction, or the
+// dozen FP32 instructions of a double-FP32 step, is dear: few lanes keep the
+// finishing butterfly short); the FP32 kinds use 4, 8, 16 or 32.
 template <typename TV, typename TA, typename TX, typename TXI, int CW>
 const void *ptr_l(int L) {
-    if constexpr (std::is_same<TA, double>::value) {
+    if constexpr (std::is_same<TA, double>::value || std::is_same<TA, DF>::value) {
         switch (L) {
             case 2: return (const void *)csr_kernel<TV, TA, TX, TXI, 2, CW>;
             case 4: return (const void *)csr_kernel<TV, TA, TX, TXI, 4, CW>;
@@ -123,7 +125,7 @@ const void *ptr_k(int L, int64_t k) {
 
 }  // namespace
 
-int csr_lane_class(int kind) { return kind == kCsrF64 ? 0 : 1; }
+int csr_lane_class(int kind) { return (kind == kCsrF64 || kind == kCsrDF) ? 0 : 1; }
 
 const void *csr_kernel_ptr(int kind, int L, int64_t k) {
     switch (kind) {

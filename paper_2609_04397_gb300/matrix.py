@@ -149,9 +149,10 @@ class VBCSR:
         """Column tile and CTA width of the bucket of row count B (0: all)."""
         check(lib().vbcsr_set_bucket_tuning(self._h, B, kc, warps), "vbcsr_set_bucket_tuning")
 
-    def set_schedule(self, schedule: str = "bucketed", persist_warps: int = 0, mma_staged: bool = False,
+    def set_schedule(self, schedule: str = "persistent", persist_warps: int = 0, mma_staged: bool = False,
                      scalar_kernel: bool = True):
-        """'bucketed' (one launch per row count) or 'persistent' (one launch);
+        """'persistent' (one launch over every item, the default) or 'bucketed'
+        (one launch per row count);
         mma_staged selects the shared-memory-staged tensor-core forward kernel;
         scalar_kernel=False makes a CSR-backend operator use the block-row kernels."""
         code = ({"bucketed": 0, "persistent": 1}[schedule] | (2 if mma_staged else 0)

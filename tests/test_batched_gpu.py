@@ -55,6 +55,7 @@ def test_batched_matches_per_structure_oracle():
 def test_persistent_schedule_equals_bucketed(dtype):
     w, H, vals = _batched(dtype=dtype)
     X = torch.randn(w.pattern.n_cols, 8, dtype=dtype, device="cuda:0")
+    H.set_schedule("bucketed")
     Yb = H.spmm(X)
     for warps in (0, 2, 8):
         H.set_schedule("persistent", warps)

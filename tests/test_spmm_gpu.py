@@ -57,13 +57,17 @@ def test_tiny_multispecies_forward():
 SIZES = [(1, 2, 3), (4, 9, 13), (1, 5, 16), (17, 3, 20), (7, 8, 9, 10, 11, 12)]
 
 
+@pytest.mark.parametrize("schedule", ["persistent", "bucketed"])
 @pytest.mark.parametrize("sizes", SIZES)
 @pytest.mark.parametrize("k", [1, 2, 3, 7, 8, 16, 32, 33])
-def test_random_patterns_forward_adjoint(sizes, k):
+def test_random_patterns_forward_adjoint(sizes, k, schedule):
+    """Both launch schedules: one persistent launch over every item (the
+    default) and one launch per row count."""
     seed = hash((sizes, k)) % 1000
     pat = syn.random_pattern(37, 29, sizes, 0.15, seed, empty_rows=3, unsorted=True)
     vals = syn.random_values(pat, seed)
     H = _handle(pat, vals)
+    H.set_schedule(schedule)
     for alpha, beta in ((1.0, 0.0), (-1.0, 1.0), (2.0, -1.0), (0.0, -1.0), (0.5, 0.25)):
         _run_forward(H, pat, vals, k, alpha, beta, ld_extra=(k % 3), seed=seed)
         rng = np.random.default_rng(seed + 1)
