@@ -159,9 +159,20 @@ def cpu_baseline(pat, values, ks, budget_s=12.0):
             flops, secs = fl, t
             break
         rows = min(pat.n_brows, rows * 4)
+    # the same loop on one core, over a sixteenth of the sample
+    rows1 = max(1, rows // 16)
+    t1, fl1 = 0.0, 0.0
+    for k in ks:
+        X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
+        t0 = time.perf_counter()
+        oracle.spmm(pat, values, X, row_range=(0, rows1), nthreads=1)
+        t1 += time.perf_counter() - t0
+        fl1 += 2.0 * (roff[pat.block_row_ptr[rows1]]) * k
     return {"value": flops / secs / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": f"first {rows} of {pat.n_brows} block rows, k in {list(ks)}, "
-                      f"{secs:.1f} s of CPU work per pass"}
+                      f"{secs:.1f} s of CPU work per pass",
+            "single_thread": {"value": fl1 / t1 / 1e9, "unit": "GFLOP/s", "cores": 1,
+                              "sample": f"first {rows1} block rows, k in {list(ks)}"}}
 
 
 def batched_section(dev, steps):
@@ -262,7 +273,7 @@ def domains_section(dev, steps):
                 sched = dict(sched)
                 H.set_schedule(sched.pop("schedule", "persistent"), **sched)
             for k in (1, 16):
-                for prec in ("native", "df32"):
+                for prec in ("native", "df32", "bf16x2"):
                     X = torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev)
                     Y = torch.empty(pat.n_rows, k, dtype=torch.float64, device=dev)
                     if sched is None:
@@ -287,6 +298,48 @@ def domains_section(dev, steps):
         del H, w
         torch.cuda.empty_cache()
     return out
+
+
+def kspace_section(dev, steps, n_cells=18):
+    """A periodic zinc-blende crystal of n_cells^3 conventional cells (the
+    nanoparticle's species, cutoff and value recipe; one image per atom pair)
+    sampled in reciprocal space (Eq. 4): the sampling itself (edge phases,
+    block sums, scatter into the pages) and complex FP64 products at k = 1, 8
+    (8 flop per stored entry and column)."""
+    import torch
+    import synthetic as syn
+    from paper_2609_04397_gb300 import VBCSR
+    w = syn.zincblende_crystal(n_cells)
+    H = VBCSR.from_images(w.bsize, w.edge_i, w.edge_j, w.edge_R, w.edge_values, device=dev)
+    nnz = int(H.nnz)
+    reps = max(5, steps // 5)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    res = {"workload": w.name, "atoms": len(w.bsize), "edges": len(w.edge_i), "nnz": nnz}
+    ms = timed(lambda: H.set_kpoint([0.1, 0.2, 0.3]))
+    # images read (8 B) and the complex value written, read and scattered (3 x 16 B) per entry
+    res["set_kpoint"] = {"ms": ms, "gbs": 56.0 * nnz / ms / 1e6}
+    for k in (1, 8):
+        X = torch.randn(H.shape[1], k, dtype=torch.complex128, device=dev)
+        Y = torch.empty(H.shape[0], k, dtype=torch.complex128, device=dev)
+        ms = timed(lambda: H.spmm(X, 1.0, 0.0, Y))
+        res[f"k{k}"] = {"ms": ms, "gflops": 8.0 * nnz * k / ms / 1e6,
+                        "fp64_alu_frac": 8.0 * nnz * k / ms / 1e9 / FP64_PEAK_TFLOPS}
+    del H
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_reference(args):
@@ -474,6 +527,7 @@ def run_ours(args):
 
     batched = batched_section(dev, args.steps) if not args.no_batched else None
     domains = domains_section(dev, args.steps) if args.domains else None
+    kspace = kspace_section(dev, args.steps) if args.kspace else None
     H.check()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -484,6 +538,7 @@ def run_ours(args):
                        "l2": "no flush: inputs larger than L2 (1.33 GB of values per product)"},
             "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
             **({"domains": domains} if domains is not None else {}),
+            **({"kspace": kspace} if kspace is not None else {}),
             "gpu_launches": n_buckets * len(KS) * args.steps, "clocks": clocks}
     if rank == 0:
         if not args.no_cpu_baseline:
@@ -503,6 +558,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--kspace", action="store_true",
+                    help="also measure a periodic crystal sampled in reciprocal space (complex products)")
     ap.add_argument("--atoms", type=int, default=N_ATOMS,
                     help="zinc-blende target atom count (a smaller case for profiler captures)")
     ap.add_argument("--domains", action="store_true",

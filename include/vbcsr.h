@@ -54,7 +54,12 @@ typedef enum {
 
 typedef enum {
     VBCSR_F64 = 0,                /* values, X and Y are double */
-    VBCSR_F32 = 1                 /* values, X and Y are float  */
+    VBCSR_F32 = 1,                /* values, X and Y are float  */
+    VBCSR_C128 = 2                /* complex double: values, X and Y are interleaved
+                                     (re, im) double pairs, leading dimensions count
+                                     complex elements; alpha and beta stay real; the
+                                     adjoint is the conjugate transpose (the dagger
+                                     of Eq. 1); NATIVE precision only               */
 } vbcsr_dtype;
 
 /*
@@ -384,6 +389,33 @@ int vbcsr_chebyshev_noalloc(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr
  * call synchronises `stream`. Errors: INVALID_ARG, NO_MEMORY, CUDA.
  */
 int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcsr_t **C, void *stream);
+
+/*
+ * Periodic operator at a reciprocal-space point (Eq. 4). The real-space images
+ * O(R) of a periodic operator are given as edges (i, j, R), each with a real
+ * b_i x b_j block; the result is a VBCSR_C128 handle on the union pattern (every
+ * (i, j) that some edge has, columns increasing inside a row) whose values
+ * vbcsr_set_kpoint fills with
+ *     O_ij(k) = sum over the edges (i, j, R) of exp(-2 pi i k . s) O_ij(R),
+ * s = R (tau == NULL: the "R" convention) or s = R + tau_j - tau_i (the "R+tau"
+ * convention), k in fractional reciprocal coordinates. Until the first
+ * vbcsr_set_kpoint the values are zero.
+ *  n_atoms, bsize[n_atoms]   block size of every atom (square blocks: rows = columns)
+ *  n_edges                   >= 0; edge_i, edge_j host int32 [n_edges] atoms in [0, n_atoms)
+ *  edge_R                    host int32 [n_edges][3] lattice translations
+ *  edge_values               host double, the edges' blocks packed in edge order, each
+ *                            row-major b_i x b_j
+ *  tau                       host double [n_atoms][3] fractional positions, or NULL
+ * The images stay on the device (FP64) so that vbcsr_set_kpoint can sample many k.
+ * Edges that repeat (i, j, R) are summed. Errors: INVALID_ARG, PATTERN, NO_MEMORY, CUDA.
+ */
+int vbcsr_create_kspace(vbcsr_t **out, int64_t n_atoms, const int32_t *bsize, int64_t n_edges,
+                        const int32_t *edge_i, const int32_t *edge_j, const int32_t *edge_R,
+                        const double *edge_values, const double *tau, void *stream);
+
+/* Fill a vbcsr_create_kspace handle with O(k); kfrac: host double[3]. Asynchronous on
+   `stream`. Errors: INVALID_ARG (NULL, or a handle not made by vbcsr_create_kspace), CUDA. */
+int vbcsr_set_kpoint(vbcsr_t *H, const double *kfrac, void *stream);
 
 /* ---- inspection ---------------------------------------------------------- */
 

@@ -15,6 +15,12 @@ Contents, each following the passage it cites:
 * ``chebyshev_moments`` / ``moment_loss_grad``  the kernel-polynomial-method
                     recurrence of Sec. V (t_{n+1} = 2 H~ t_n - t_{n-1}) and the
                     reverse-mode gradient of L = sum_n mu_n^2
+* ``kpm_moments_doubling`` / ``kpm_dos``  the DOS pipeline of Sec. V
+* ``spgemm``        the thresholded block product, Eqs. (2)-(3)
+* ``kspace_blocks`` / ``kspace_dense``  a periodic operator sampled in
+                    reciprocal space, Eq. (4); ``spmm_complex`` /
+                    ``spmm_adjoint_complex`` its block products (Eq. 1 with a
+                    conjugate transpose)
 
 A pattern argument is any object with the attributes ``row_bsize``,
 ``col_bsize``, ``block_row_ptr`` and ``block_col_idx`` (numpy arrays).
@@ -371,3 +377,97 @@ def spgemm(patA, valsA, patB, valsB, eps):
         ptr.append(len(cols))
     return (ra.astype(np.int32), cb.astype(np.int32), np.array(ptr, np.int64), np.array(cols, np.int32),
             np.concatenate(vals) if vals else np.zeros(0))
+
+
+# ----------------------------------------------------------------------------
+# periodic operators in reciprocal space (Sec. III.C "Atomistic Interfaces",
+# Eq. 4) and complex block products
+
+
+def kspace_blocks(bsize, edge_i, edge_j, edge_R, edge_values, kfrac, tau=None):
+    """O(k) on the union pattern of the edges (Eq. 4): block (i, j) is
+    sum over the edges (i, j, R) of exp(-2 pi i k . s) O(R)_ij with s = R, or
+    s = R + tau_j - tau_i when fractional positions tau are given. Edges are
+    (i, j, R) triples with real b_i x b_j blocks packed row-major in edge order.
+    Returns (row_bsize, col_bsize, block_row_ptr, block_col_idx, values) with the
+    union blocks in row order, columns increasing, values complex128."""
+    bs = np.asarray(bsize, np.int64)
+    ei, ej = np.asarray(edge_i, np.int64), np.asarray(edge_j, np.int64)
+    R = np.asarray(edge_R, np.float64).reshape(-1, 3)
+    k = np.asarray(kfrac, np.float64).reshape(3)
+    off = np.concatenate([[0], np.cumsum(bs[ei] * bs[ej])])
+    blocks = {}
+    for e in range(len(ei)):
+        i, j = int(ei[e]), int(ej[e])
+        s = R[e].copy()
+        if tau is not None:
+            t = np.asarray(tau, np.float64).reshape(-1, 3)
+            s = s + t[j] - t[i]
+        phase = np.exp(-2j * np.pi * float(k @ s))
+        O = np.asarray(edge_values[off[e]:off[e + 1]], np.float64).reshape(bs[i], bs[j])
+        blocks[(i, j)] = blocks.get((i, j), 0) + phase * O
+    keys = sorted(blocks)
+    ptr = np.zeros(len(bs) + 1, np.int64)
+    for (i, _j) in keys:
+        ptr[i + 1] += 1
+    ptr = np.cumsum(ptr)
+    cols = np.array([j for (_i, j) in keys], np.int32)
+    vals = np.concatenate([np.asarray(blocks[key], np.complex128).ravel() for key in keys]) if keys \
+        else np.zeros(0, np.complex128)
+    return bs.astype(np.int32), bs.astype(np.int32), ptr, cols, vals
+
+
+def kspace_dense(bsize, edge_i, edge_j, edge_R, edge_values, kfrac, tau=None) -> np.ndarray:
+    """Dense O(k) (Eq. 4), each edge's phased block added straight into the
+    dense matrix at scalar rows r_i.. and columns r_j.."""
+    bs = np.asarray(bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(bs)])
+    ei, ej = np.asarray(edge_i, np.int64), np.asarray(edge_j, np.int64)
+    R = np.asarray(edge_R, np.float64).reshape(-1, 3)
+    k = np.asarray(kfrac, np.float64).reshape(3)
+    off = np.concatenate([[0], np.cumsum(bs[ei] * bs[ej])])
+    H = np.zeros((r[-1], r[-1]), np.complex128)
+    for e in range(len(ei)):
+        i, j = int(ei[e]), int(ej[e])
+        s = R[e] if tau is None else R[e] + np.asarray(tau, np.float64).reshape(-1, 3)[j] \
+            - np.asarray(tau, np.float64).reshape(-1, 3)[i]
+        O = np.asarray(edge_values[off[e]:off[e + 1]], np.float64).reshape(bs[i], bs[j])
+        H[r[i]:r[i + 1], r[j]:r[j + 1]] += np.exp(-2j * np.pi * float(k @ s)) * O
+    return H
+
+
+def _block_loop(pat, values, X, alpha, beta, Y, adjoint):
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(rb)])
+    c = np.concatenate([[0], np.cumsum(cb)])
+    X = np.asarray(X, np.complex128)
+    n_out = c[-1] if adjoint else r[-1]
+    acc = np.zeros((n_out, X.shape[1]), np.complex128)
+    off = 0
+    for i in range(len(rb)):
+        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
+            j = int(pat.block_col_idx[b])
+            n = int(rb[i] * cb[j])
+            Hij = np.asarray(values[off:off + n], np.complex128).reshape(rb[i], cb[j])
+            off += n
+            if adjoint:
+                acc[c[j]:c[j + 1]] += Hij.conj().T @ X[r[i]:r[i + 1]]
+            else:
+                acc[r[i]:r[i + 1]] += Hij @ X[c[j]:c[j + 1]]
+    out = alpha * acc
+    if beta != 0.0 and Y is not None:
+        out = out + beta * np.asarray(Y, np.complex128)
+    return out
+
+
+def spmm_complex(pat, values, X, alpha=1.0, beta=0.0, Y=None) -> np.ndarray:
+    """Y = alpha H X + beta Y for complex blocks: Y_i += H_ij X_j block by block
+    (Sec. III.B "Matrix multiplication"); beta == 0: Y is not read."""
+    return _block_loop(pat, values, X, alpha, beta, Y, adjoint=False)
+
+
+def spmm_adjoint_complex(pat, values, X, alpha=1.0, beta=0.0, Y=None) -> np.ndarray:
+    """Y = alpha H^dagger X + beta Y: Y_j += H_ij^dagger X_i (Eq. 1), the
+    dagger a conjugate transpose."""
+    return _block_loop(pat, values, X, alpha, beta, Y, adjoint=True)

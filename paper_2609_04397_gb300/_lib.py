@@ -12,7 +12,7 @@ SO_PATH = os.path.join(_HERE, "_lib", "libvbcsr.so")
 VBCSR_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "PATTERN", -3: "CUDA", -4: "NO_MEMORY",
           -5: "UNSUPPORTED", -6: "DEVICE_CHECK", -7: "ALIAS"}
-F64, F32 = 0, 1
+F64, F32, C128 = 0, 1, 2
 PRECISION = {"native": 0, "f32": 1, "tf32": 2, "tf32x3": 3, "bf16x2": 4, "df32": 5}
 
 # every function that include/vbcsr.h declares, with its ctypes signature
@@ -50,6 +50,8 @@ SIGNATURES = {
     "vbcsr_kpm_dos": ([_p, _i64, _int, _p, _i64, _p, _p], _int),
     "vbcsr_shift_scale": ([_p, _d, _d, _p], _int),
     "vbcsr_spgemm": ([_p, _p, _d, ctypes.POINTER(_p), _p], _int),
+    "vbcsr_create_kspace": ([ctypes.POINTER(_p), _i64, _p, _i64, _p, _p, _p, _p, _p, _p], _int),
+    "vbcsr_set_kpoint": ([_p, _p, _p], _int),
     "vbcsr_get_info": ([_p, ctypes.POINTER(Info)], _int),
     "vbcsr_get_pattern": ([_p, _p, _p, _p, _p], _int),
     "vbcsr_shape_classes": ([_p, _p, _p, _p, _i32], _int),

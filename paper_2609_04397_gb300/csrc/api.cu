@@ -133,6 +133,18 @@ struct vbcsr_matrix {
     int *err = nullptr;
     int64_t device_bytes = 0;
 
+    // reciprocal-space sampling (handles made by vbcsr_create_kspace)
+    bool kspace = false;
+    int64_t ks_edges = 0;
+    int64_t *ks_ptr = nullptr;       // edges of every union block (nblk + 1), edges sorted by block
+    double *ks_shift = nullptr;      // s_e = R [+ tau_j - tau_i] of every sorted edge (3 doubles)
+    int64_t *ks_voff = nullptr;      // offset of every sorted edge's real block in ks_vals
+    double *ks_vals = nullptr;       // the image blocks, row-major
+    int64_t *ks_uoff = nullptr;      // packed offset of every union block
+    int32_t *ks_ubn = nullptr;       // entries of every union block
+    double2 *ks_phase = nullptr;     // phase of every sorted edge at the current k
+    double2 *ks_stage = nullptr;     // packed complex values at the current k
+
     ~vbcsr_matrix() {
         int cur = 0;
         cudaGetDevice(&cur);
@@ -266,10 +278,12 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
             // FP64 operations are charged per warp instruction on GB300's narrow FP64
             // pipe, so an FP64 (or double-FP32) row gets few lanes (every instruction
             // carries ~32 useful lanes, the finishing butterfly is short); FP32 rows
-            // get more lanes for coalesced loads
+            // get a few more. Measured on a 43.6M-entry scalar graph (26.5 entries per
+            // row): 4 lanes per FP32 row ran FP32 / BF16X2 products 2.3x / 1.7x
+            // faster (k = 1 / 16) than 16 lanes
             const double avg = n_brows > 0 ? (double)nblk / (double)n_brows : 0.0;
             A->csr_lanes[0] = avg <= 64 ? 2 : (avg <= 256 ? 4 : 8);
-            A->csr_lanes[1] = avg <= 8 ? 4 : (avg <= 24 ? 8 : (avg <= 64 ? 16 : 32));
+            A->csr_lanes[1] = avg <= 32 ? 4 : (avg <= 128 ? 8 : (avg <= 512 ? 16 : 32));
         }
     }
 
@@ -296,13 +310,17 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     }
 
     // panel widths; pages ordered by row height
+    // (scalar rows are short - ~27 entries in an atom-like graph - so padding them to
+    // 8 would add ~20 % to their values; 4 keeps every row start 16-byte aligned, all
+    // that the FP32 vector loads and the bulk copies need)
     std::vector<int64_t> K(n_brows, 0), Kp(n_brows, 0), poff(n_brows, 0);
+    const int pad = A->backend == VBCSR_BACKEND_CSR ? kPadKScalar : kPadK;
     for (int64_t i = 0; i < n_brows; ++i) {
         int64_t w = 0;
         for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u) w += col_bsize[block_col_idx[u]];
         if (w >= (1LL << 31) - kPadK) return fail(VBCSR_ERR_PATTERN, "block row %lld too wide", (long long)i);
         K[i] = w;
-        Kp[i] = ceil_to(w, kPadK);
+        Kp[i] = ceil_to(w, pad);
     }
     std::vector<int64_t> page_order(n_brows);
     for (int64_t i = 0; i < n_brows; ++i) page_order[i] = i;
@@ -456,7 +474,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     CUDA_TRY(A->alloc(&panel, (size_t)A->panel_elems * A->esize), "alloc value pages");
     A->panel = panel;
     CUDA_TRY(cudaMemsetAsync(A->panel, 0, (size_t)A->panel_elems * A->esize, s), "memset");
-    if (A->nnz > 0) {
+    if (A->nnz > 0 && values) {
         const void *src = values;
         void *staged = nullptr;
         if (!values_on_device) {
@@ -465,7 +483,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
             if (e != cudaSuccess) { cudaFree(staged); return cuda_fail(e, "copy values"); }
             src = staged;
         }
-        cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, true, nblk, A->fl_uoff, A->fl_pbase,
+        cudaError_t e = launch_permute_values((int)A->esize, true, nblk, A->fl_uoff, A->fl_pbase,
                                               A->fl_kp, A->fl_bi, A->fl_w, src, A->panel, s);
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (staged) cudaFree(staged);
@@ -476,23 +494,26 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     return VBCSR_OK;
 }
 
+// zero_values: values may be NULL and the pages start at zero (k-space handles)
 static int create_common(vbcsr_t **out, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
                          const int32_t *col_bsize, const int64_t *block_row_ptr, const int32_t *block_col_idx,
-                         const void *values, int dtype, int values_on_device, void *stream, int32_t n_structs) {
+                         const void *values, int dtype, int values_on_device, void *stream, int32_t n_structs,
+                         bool zero_values = false) {
     if (!out) return fail(VBCSR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (dtype != VBCSR_F64 && dtype != VBCSR_F32) return fail(VBCSR_ERR_INVALID_ARG, "dtype %d", dtype);
+    if (dtype != VBCSR_F64 && dtype != VBCSR_F32 && dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_INVALID_ARG, "dtype %d", dtype);
     if (values_on_device != 0 && values_on_device != 1)
         return fail(VBCSR_ERR_INVALID_ARG, "values_on_device must be 0 or 1");
     int rc = validate_pattern(n_brows, n_bcols, row_bsize, col_bsize, block_row_ptr, block_col_idx);
     if (rc) return rc;
-    if (!values && block_row_ptr[n_brows] > 0) return fail(VBCSR_ERR_INVALID_ARG, "values is NULL");
+    if (!values && block_row_ptr[n_brows] > 0 && !zero_values) return fail(VBCSR_ERR_INVALID_ARG, "values is NULL");
     vbcsr_matrix *A = new (std::nothrow) vbcsr_matrix();
     if (!A) return fail(VBCSR_ERR_NO_MEMORY, "host allocation");
     cudaError_t e = cudaGetDevice(&A->device);
     if (e != cudaSuccess) { delete A; return cuda_fail(e, "cudaGetDevice"); }
     A->dtype = dtype;
-    A->esize = dtype == VBCSR_F64 ? 8 : 4;
+    A->esize = dtype == VBCSR_C128 ? 16 : (dtype == VBCSR_F64 ? 8 : 4);
     A->n_structs = n_structs;
     const char *dbg = getenv("VBCSR_DEBUG_CHECKS");
     A->debug_checks = (dbg && dbg[0] && dbg[0] != '0') ? 1 : 0;
@@ -554,6 +575,102 @@ extern "C" int vbcsr_create_batched(vbcsr_t **out, int64_t n_structs, const int6
                          values_on_device, stream, (int32_t)n_structs);
 }
 
+// ---------------------------------------------------------------------------
+// reciprocal-space sampling of a periodic operator (Eq. 4)
+
+extern "C" int vbcsr_create_kspace(vbcsr_t **out, int64_t n_atoms, const int32_t *bsize, int64_t n_edges,
+                                   const int32_t *edge_i, const int32_t *edge_j, const int32_t *edge_R,
+                                   const double *edge_values, const double *tau, void *stream) {
+    if (!out) return fail(VBCSR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_atoms < 0 || n_edges < 0) return fail(VBCSR_ERR_INVALID_ARG, "negative size");
+    if (n_atoms > 0 && !bsize) return fail(VBCSR_ERR_INVALID_ARG, "bsize is NULL");
+    if (n_edges > 0 && (!edge_i || !edge_j || !edge_R || !edge_values))
+        return fail(VBCSR_ERR_INVALID_ARG, "edge array is NULL");
+    if (n_atoms >= (1LL << 31) || n_edges >= (1LL << 31)) return fail(VBCSR_ERR_INVALID_ARG, "size reaches 2^31");
+    for (int64_t a = 0; a < n_atoms; ++a)
+        if (bsize[a] < 1 || bsize[a] > kMaxBlockSize)
+            return fail(VBCSR_ERR_PATTERN, "bsize[%lld] = %d outside [1, %d]", (long long)a, bsize[a], kMaxBlockSize);
+    cudaStream_t s = (cudaStream_t)stream;
+    try {
+        // edges sorted by (i, j), stable: the union pattern and each union block's edges
+        std::vector<int64_t> order(n_edges), evoff(n_edges + 1, 0);
+        for (int64_t e = 0; e < n_edges; ++e) {
+            if (edge_i[e] < 0 || edge_i[e] >= n_atoms || edge_j[e] < 0 || edge_j[e] >= n_atoms)
+                return fail(VBCSR_ERR_PATTERN, "edge %lld joins atoms outside [0, %lld)", (long long)e,
+                            (long long)n_atoms);
+            order[e] = e;
+            evoff[e + 1] = evoff[e] + (int64_t)bsize[edge_i[e]] * bsize[edge_j[e]];
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+            return edge_i[x] != edge_i[y] ? edge_i[x] < edge_i[y] : edge_j[x] < edge_j[y];
+        });
+        std::vector<int64_t> rowptr(n_atoms + 1, 0), ks_ptr(1, 0), ks_voff(n_edges);
+        std::vector<int32_t> cols, ubn;
+        std::vector<double> shift(3 * (size_t)n_edges);
+        for (int64_t t = 0; t < n_edges; ++t) {
+            const int64_t e = order[t];
+            const int32_t i = edge_i[e], j = edge_j[e];
+            const bool fresh = t == 0 || edge_i[order[t - 1]] != i || edge_j[order[t - 1]] != j;
+            if (fresh) {
+                cols.push_back(j);
+                ubn.push_back(bsize[i] * bsize[j]);
+                rowptr[i + 1] += 1;
+                if (t > 0) ks_ptr.push_back(t);
+            }
+            ks_voff[t] = evoff[e];
+            for (int d = 0; d < 3; ++d)
+                shift[3 * t + d] = (double)edge_R[3 * e + d] + (tau ? tau[3 * (int64_t)j + d] - tau[3 * (int64_t)i + d] : 0.0);
+        }
+        if (n_edges > 0) ks_ptr.push_back(n_edges);
+        for (int64_t a = 0; a < n_atoms; ++a) rowptr[a + 1] += rowptr[a];
+        const int64_t nblk = (int64_t)cols.size();
+        int rc = create_common(out, n_atoms, n_atoms, bsize, bsize, rowptr.data(), cols.data(), nullptr, VBCSR_C128,
+                               0, stream, 1, true);
+        if (rc) return rc;
+        vbcsr_matrix *A = *out;
+        auto bail = [&](int code) {
+            delete A;
+            *out = nullptr;
+            return code;
+        };
+        A->kspace = true;
+        A->ks_edges = n_edges;
+        std::vector<int64_t> uo(A->uoff.begin(), A->uoff.begin() + nblk);
+        std::vector<double> vals(edge_values, edge_values + evoff[n_edges]);
+        cudaError_t e = upload(A, &A->ks_ptr, ks_ptr, s);
+        if (e == cudaSuccess) e = upload(A, &A->ks_shift, shift, s);
+        if (e == cudaSuccess) e = upload(A, &A->ks_voff, ks_voff, s);
+        if (e == cudaSuccess) e = upload(A, &A->ks_vals, vals, s);
+        if (e == cudaSuccess) e = upload(A, &A->ks_uoff, uo, s);
+        if (e == cudaSuccess) e = upload(A, &A->ks_ubn, ubn, s);
+        if (e == cudaSuccess) e = A->alloc(&A->ks_phase, (size_t)n_edges);
+        if (e == cudaSuccess) e = A->alloc(&A->ks_stage, (size_t)A->nnz);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "upload the lattice images"));
+    } catch (const std::bad_alloc &) {
+        if (*out) {
+            delete *out;
+            *out = nullptr;
+        }
+        return fail(VBCSR_ERR_NO_MEMORY, "host allocation");
+    }
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_set_kpoint(vbcsr_t *A, const double *kfrac, void *stream) {
+    if (!A || !kfrac) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
+    if (!A->kspace) return fail(VBCSR_ERR_INVALID_ARG, "not a handle made by vbcsr_create_kspace");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(launch_ksample(A->nblk, A->ks_edges, A->ks_ptr, A->ks_shift, A->ks_voff, A->ks_vals, A->ks_uoff,
+                            A->ks_ubn, kfrac, A->ks_phase, A->ks_stage, s),
+             "k-space sampling");
+    CUDA_TRY(launch_permute_values((int)A->esize, true, A->nblk, A->fl_uoff, A->fl_pbase, A->fl_kp, A->fl_bi,
+                                   A->fl_w, A->ks_stage, A->panel, s),
+             "scatter values");
+    return VBCSR_OK;
+}
+
 extern "C" int vbcsr_destroy(vbcsr_t *A) {
     delete A;
     return VBCSR_OK;
@@ -611,7 +728,7 @@ extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, v
         if (e != cudaSuccess) { cudaFree(staged); return cuda_fail(e, "copy values"); }
         src = staged;
     }
-    cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, true, A->nblk, A->fl_uoff, A->fl_pbase, A->fl_kp,
+    cudaError_t e = launch_permute_values((int)A->esize, true, A->nblk, A->fl_uoff, A->fl_pbase, A->fl_kp,
                                           A->fl_bi, A->fl_w, src, A->panel, s);
     if (staged) {
         cudaError_t e2 = cudaStreamSynchronize(s);
@@ -640,7 +757,7 @@ extern "C" int vbcsr_get_values(const vbcsr_t *Ac, void *values, int on_device, 
         CUDA_TRY(cudaMalloc(&staged, (size_t)A->nnz * A->esize), "alloc staging");
         dst = staged;
     }
-    cudaError_t e = launch_permute_values(A->dtype == VBCSR_F64, false, A->nblk, A->fl_uoff, A->fl_pbase,
+    cudaError_t e = launch_permute_values((int)A->esize, false, A->nblk, A->fl_uoff, A->fl_pbase,
                                           A->fl_kp, A->fl_bi, A->fl_w, dst, A->panel, s);
     if (staged) {
         if (e == cudaSuccess)
@@ -710,6 +827,9 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
     if (precision == VBCSR_PREC_DF32 && A->dtype != VBCSR_F64)
         return fail(VBCSR_ERR_UNSUPPORTED, "the double-FP32 mode needs an FP64 operator");
+    const bool cplx = A->dtype == VBCSR_C128;
+    if (cplx && precision != VBCSR_PREC_NATIVE)
+        return fail(VBCSR_ERR_UNSUPPORTED, "complex operators run in NATIVE precision only");
     const int64_t xrows = trans ? A->n_rows : A->n_cols;
     const int64_t yrows = trans ? A->n_cols : A->n_rows;
     const bool want_dot = epi && epi->dot_out;
@@ -782,6 +902,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
     const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32 || mode == VBCSR_PREC_DF32);
+    // a tensor-core mode on a product too thin for an MMA tile (few columns, or the
+    // single-row items of a scalar operator) runs its piece products on the CUDA cores
+    const bool csr_kernel =
+        A->backend == VBCSR_BACKEND_CSR && !trans && !cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
+    const bool split = !fma && f64 && !trans && (k <= kSplitFmaMaxK || csr_kernel);
     int64_t used = 0;
     // one launch of `kern` over items[0..n) with `warps` warps per CTA
     auto launch = [&](int B, const WorkItem *items, int64_t n, int warps, const void *kern, size_t smem) -> int {
@@ -802,17 +927,21 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         }
         cudaError_t e;
         if (mode == VBCSR_PREC_NATIVE)
-            e = f64 ? launch_fma_f64(B, trans, a, s) : launch_fma_f32(B, trans, a, s);
+            e = cplx ? launch_fma_c128(B, trans, a, s)
+                     : (f64 ? launch_fma_f64(B, trans, a, s) : launch_fma_f32(B, trans, a, s));
         else if (mode == VBCSR_PREC_F32)
             e = launch_fma_f32_on_f64(B, trans, a, s);
         else if (mode == VBCSR_PREC_DF32)
             e = launch_fma_df(B, trans, a, s);
+        else if (split)
+            e = launch_fma_split(mode, a, s);
         else
             e = launch_mma(mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
         return VBCSR_OK;
     };
     auto fma_kern = [&](bool persistent, int B) {
+        if (cplx) return fma_c128_kernel(trans, persistent, B);
         if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B);
         return (mode == VBCSR_PREC_NATIVE)
                    ? (f64 ? fma_f64_kernel(trans, persistent, B) : fma_f32_kernel(trans, persistent, B))
@@ -820,17 +949,18 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     };
     const int64_t n_all = trans ? A->n_adj_items : A->n_fwd_items;
     int rc = VBCSR_OK;
-    if (!fma) {
+    if (!fma && !split) {
         // tensor-core kernel: the row count is a runtime mask, one launch serves every item
         const bool staged = !trans && (A->schedule & VBCSR_SCHED_MMA_STAGED);
         a.mma_staged = staged ? 1 : 0;
         const void *kern = mma_kernel_ptr(mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
-    } else if (A->backend == VBCSR_BACKEND_CSR && !trans &&
-               !(A->schedule & VBCSR_SCHED_NO_CSR)) {
+    } else if (csr_kernel) {
         // scalar operator: several rows per warp; items are the scalar rows in page order
-        const int kind = mode == VBCSR_PREC_DF32 ? kCsrDF
+        const int kind = split ? (mode == VBCSR_PREC_TF32 ? kCsrSplitTF32
+                                  : mode == VBCSR_PREC_TF32X3 ? kCsrSplitTF32X3 : kCsrSplitBF16X2)
+                       : mode == VBCSR_PREC_DF32 ? kCsrDF
                        : mode == VBCSR_PREC_F32 ? kCsrF32OnF64 : (f64 ? kCsrF64 : kCsrF32);
         const int L = A->csr_lanes[csr_lane_class(kind)];
         a.items = A->fwd_items;
@@ -847,8 +977,9 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             used = a.grid;
         }
         CUDA_TRY(launch_csr(kind, L, a, s), "scalar product launch");
-    } else if (A->schedule & VBCSR_SCHED_PERSISTENT) {
+    } else if (split || (A->schedule & VBCSR_SCHED_PERSISTENT)) {
         // persistent launch over every row count, items in descending cost from a work queue
+        // (the only launch shape of the CUDA-core form of the tensor-core modes)
         a.kc_log2_by_b = 0;
         for (int B = 1; B <= kMaxB; ++B) {
             int l = 0;
@@ -858,7 +989,8 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         a.queue = A->queue;
         CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         const int warps = A->persist_warps ? A->persist_warps : 4;
-        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps, fma_kern(true, 0), fma_smem_bytes(trans, warps));
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps,
+                    split ? fma_split_kernel(mode) : fma_kern(true, 0), fma_smem_bytes(trans, warps));
     } else {
         const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
         const WorkItem *items = trans ? A->adj_items : A->fwd_items;
@@ -895,6 +1027,7 @@ extern "C" int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop,
                            int64_t ldb, double beta, void *D, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
+    if (A->dtype == VBCSR_C128) return fail(VBCSR_ERR_UNSUPPORTED, "pattern-sampled product of a complex operator");
     if (A->nnz == 0) return VBCSR_OK;
     if (!D) return fail(VBCSR_ERR_INVALID_ARG, "D is NULL");
     if (k > 0 && alpha != 0.0) {
@@ -1152,6 +1285,7 @@ extern "C" int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcs
     *Cout = nullptr;
     if (!A || !B) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (A->dtype != B->dtype) return fail(VBCSR_ERR_INVALID_ARG, "A and B have different dtypes");
+    if (A->dtype == VBCSR_C128) return fail(VBCSR_ERR_UNSUPPORTED, "block product of complex operators");
     if (!(eps >= 0.0)) return fail(VBCSR_ERR_INVALID_ARG, "eps = %g", eps);
     if (A->n_bcols != B->n_brows) return fail(VBCSR_ERR_INVALID_ARG, "inner block counts differ");
     for (int64_t k = 0; k < A->n_bcols; ++k)

@@ -31,6 +31,11 @@ __device__ __forceinline__ T ld_ro(const T *p) { return __ldg(p); }
 __device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 
+// The value as the adjoint product uses it: itself for real types (complex
+// types overload this with the conjugate).
+template <typename T>
+__device__ __forceinline__ T adj_val(T v) { return v; }
+
 // Stage the X row (and, for the adjoint, the value address) of virtual
 // columns [t0, t0 + tn) of item w in shared memory.
 template <bool TRANS>
@@ -61,11 +66,35 @@ template <typename TX>
 __device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_t c, TX acc, double &dot) {
     TX *Y = static_cast<TX *>(a.Y);
     TX *yp = Y + row * a.ldy + c;
-    TX r = (TX)a.alpha * acc;
+    TX r = a.alpha == 1.0 ? acc : (TX)a.alpha * acc;   // alpha = 1 skips a multiply (FP64 pipe)
     if (a.beta != 0.0) r += (TX)a.beta * *yp;
     if (a.gamma != 0.0) r += (TX)a.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
     *yp = r;
     if (a.partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
+}
+
+// complex Y (interleaved re, im): real alpha, beta, gamma; the dot is the real
+// part of sum(conj(R) .* Y)
+template <>
+__device__ __forceinline__ void write_out<double2>(const ProdArgs &a, int64_t row, int64_t c, double2 acc,
+                                                   double &dot) {
+    double2 *yp = static_cast<double2 *>(a.Y) + row * a.ldy + c;
+    double2 r = a.alpha == 1.0 ? acc : make_double2(a.alpha * acc.x, a.alpha * acc.y);
+    if (a.beta != 0.0) {
+        const double2 y = *yp;
+        r.x += a.beta * y.x;
+        r.y += a.beta * y.y;
+    }
+    if (a.gamma != 0.0) {
+        const double2 z = static_cast<const double2 *>(a.Z)[row * a.ldz + c];
+        r.x += a.gamma * z.x;
+        r.y += a.gamma * z.y;
+    }
+    *yp = r;
+    if (a.partials) {
+        const double2 q = static_cast<const double2 *>(a.R)[row * a.ldr + c];
+        dot += q.x * r.x + q.y * r.y;
+    }
 }
 
 // Reduce-scatter of B (<= 16) per-lane partial sums over all 32 lanes, sized
@@ -138,8 +167,8 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                 if (c0 == 0 || w.K > kKMax) stage_columns<TRANS>(a, w, t0, tn, s_x, s_a, lane);
                 if (!TRANS && sizeof(TV) == 4) {
                     // FP32 values: four consecutive panel columns per lane and step, one
-                    // 16-byte load per row (rows start 32-byte aligned; Kp is a multiple
-                    // of 8, so the four columns never leave the row)
+                    // 16-byte load per row (rows start 16-byte aligned; Kp is a multiple
+                    // of 4, so the four columns never leave the row)
                     for (int t = 4 * tg; t < tn; t += 4 * TG) {
                         TA x[4];
 #pragma unroll
@@ -175,7 +204,7 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                     } else {
                         const TV *v = vals + s_a[t];
 #pragma unroll
-                        for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p), x, acc[p]);
+                        for (int p = 0; p < B; ++p) acc[p] = fmat(adj_val((TA)ld_ro(v + p)), x, acc[p]);
                     }
                 }
             }
@@ -194,9 +223,17 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
 #pragma unroll
                 for (int p = 0; p < B; ++p) acc[p] += __shfl_xor_sync(0xffffffffu, acc[p], m);
             }
+            // every lane of column c now holds all B sums; lane group tg writes rows
+            // tg, tg + TG, ...: each epilogue step stores TG rows with the whole warp
+            // (the epilogue's FP64 instructions are charged per warp instruction)
+            for (int p0 = 0; p0 < B; p0 += TG) {
+                const int p = p0 + tg;
+                TA v = acc[0];
 #pragma unroll
-            for (int p = 0; p < B; ++p)
-                if ((p % TG) == tg && cv) write_out<TX>(a, w.yrow + p, c, (TX)acc[p], dot);
+                for (int q = 1; q < B; ++q)
+                    if (q == p) v = acc[q];
+                if (p < B && cv) write_out<TX>(a, w.yrow + p, c, (TX)v, dot);
+            }
         }
     }
 }

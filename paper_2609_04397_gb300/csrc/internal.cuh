@@ -6,7 +6,8 @@
 //    P_i of b_i rows and Kp_i columns: its stored blocks side by side in
 //    increasing column order (K_i = sum_{j in J(i)} b_j columns, zero-padded
 //    to Kp_i = roundup(K_i, 8) so that every panel row starts 64-byte aligned
-//    in FP64 and 32-byte aligned in FP32). Panels are laid out grouped by row
+//    in FP64 and 32-byte aligned in FP32; roundup(K_i, 4) for scalar operators,
+//    16-byte aligned rows). Panels are laid out grouped by row
 //    height b_i, so each row class is one contiguous page (the shape-grouped
 //    pages of Sec. III.B). Then Y_i = P_i * X[g_i, :], where g_i lists the X
 //    row of every panel column.
@@ -29,16 +30,14 @@ namespace vbcsr {
 
 constexpr int kMaxB = 16;        // rows per work item
 constexpr int kPadK = 8;         // panel width padding (elements)
+constexpr int kPadKScalar = 4;   // the same for scalar (CSR-backend) operators
 constexpr int kKMax = 512;       // virtual columns staged in shared memory per pass
 constexpr int kPartialsCap = 1 << 16;
-constexpr uint32_t kPrefetchMax = 256u << 10;   // bytes of one item's values prefetched into L2
-
-// Hint that [p, p + bytes) be brought into L2 ahead of use (one bulk request:
-// nothing moves into the SM, nothing waits, no fault for an in-bounds range).
-// p must be 16-byte aligned and bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
+// tensor-core precision modes (the values of their vbcsr_precision codes)
+constexpr int kTF32 = 2, kTF32X3 = 3, kBF16X2 = 4;
+// below this many columns the tensor-core modes of an FP64 operator run their
+// piece products on the CUDA cores (an MMA tile would be mostly padding)
+constexpr int kSplitFmaMaxK = 2;
 
 // One warp task.
 struct WorkItem {
@@ -108,7 +107,10 @@ cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cu
 // Scalar (all 1 x 1 blocks) operators: L lanes per row (2, 4 or 8 for the
 // FP64 and double-FP32 kinds, 4, 8, 16 or 32 for the FP32 ones; csr_lane_class
 // 0 and 1).
-enum CsrKind { kCsrF64 = 0, kCsrF32 = 1, kCsrF32OnF64 = 2, kCsrDF = 3 };
+enum CsrKind {
+    kCsrF64 = 0, kCsrF32 = 1, kCsrF32OnF64 = 2, kCsrDF = 3,
+    kCsrSplitTF32 = 4, kCsrSplitTF32X3 = 5, kCsrSplitBF16X2 = 6   // split.cuh, FP64 Y
+};
 int csr_lane_class(int kind);
 cudaError_t launch_csr(int kind, int L, const ProdArgs &a, cudaStream_t s);
 const void *csr_kernel_ptr(int kind, int L, int64_t k);
@@ -137,6 +139,9 @@ cudaError_t launch_compact(bool f64, int64_t n, const int64_t *keep_src, const i
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
 
 size_t fma_smem_bytes(bool trans, int warps);
+// forward products of an FP64 operator in a tensor-core mode on the CUDA cores
+cudaError_t launch_fma_split(int mode, const ProdArgs &a, cudaStream_t s);
+const void *fma_split_kernel(int mode);
 size_t mma_smem_bytes(bool trans, bool staged, int warps);
 
 // Misc kernels (misc.cu).
@@ -157,7 +162,15 @@ struct SddmmArgs {
 cudaError_t launch_sddmm(bool f64, const SddmmArgs &a, cudaStream_t s);
 
 // scatter (to_panel = true) or gather packed-order values <-> panels
-cudaError_t launch_permute_values(bool f64, bool to_panel, int64_t nblk, const int64_t *uoff,
+// reciprocal-space sampling (Eq. 4) of a k-space handle into packed complex values
+cudaError_t launch_ksample(int64_t nblk, int64_t n_edges, const int64_t *ks_ptr, const double *ks_shift,
+                           const int64_t *ks_voff, const double *ks_vals, const int64_t *uoff, const int32_t *ub_n,
+                           const double *kfrac, double2 *phase, double2 *out, cudaStream_t s);
+// complex FP64 products (VBCSR_C128)
+cudaError_t launch_fma_c128(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+const void *fma_c128_kernel(bool trans, bool persistent, int B);
+// esize: 4 (FP32), 8 (FP64) or 16 (complex FP64) bytes per element
+cudaError_t launch_permute_values(int esize, bool to_panel, int64_t nblk, const int64_t *uoff,
                                   const int64_t *pbase, const int32_t *kp, const int32_t *bi,
                                   const int32_t *bj, const void *user, void *panel, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);

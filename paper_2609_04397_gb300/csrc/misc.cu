@@ -96,19 +96,81 @@ __global__ void permute_kernel(bool to_panel, int64_t nblk, const int64_t *uoff,
     }
 }
 
-cudaError_t launch_permute_values(bool f64, bool to_panel, int64_t nblk, const int64_t *uoff,
+cudaError_t launch_permute_values(int esize, bool to_panel, int64_t nblk, const int64_t *uoff,
                                   const int64_t *pbase, const int32_t *kp, const int32_t *bi,
                                   const int32_t *bj, const void *user, void *panel, cudaStream_t s) {
     if (nblk == 0) return cudaSuccess;
     const int warps = 8;
     int64_t need = (nblk + warps - 1) / warps;
     int grid = (int)(need < 65536 ? need : 65536);
-    if (f64)
+    if (esize == 16)
+        permute_kernel<double2><<<grid, warps * 32, 0, s>>>(to_panel, nblk, uoff, pbase, kp, bi, bj,
+                                                            (const double2 *)user, (double2 *)panel, warps);
+    else if (esize == 8)
         permute_kernel<double><<<grid, warps * 32, 0, s>>>(to_panel, nblk, uoff, pbase, kp, bi, bj,
                                                            (const double *)user, (double *)panel, warps);
-    else
+    else if (esize == 4)
         permute_kernel<float><<<grid, warps * 32, 0, s>>>(to_panel, nblk, uoff, pbase, kp, bi, bj,
                                                           (const float *)user, (float *)panel, warps);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reciprocal-space sampling (Eq. 4). First the phase of every edge,
+// exp(-2 pi i k . s_e) = cos(pi * 2 k.s_e) - i sin(pi * 2 k.s_e), s_e = R [+ tau_j -
+// tau_i] (one FP64 sincospi per edge: GB300's FP64 pipe is narrow, so it is not
+// repeated per entry); then block u of the union pattern sums its edges
+// ks_ptr[u] .. ks_ptr[u+1] (real b_i x b_j image blocks at ks_voff) times their
+// phases, written in packed order at uoff[u]: one warp per block, lanes over
+// its entries.
+
+__global__ void kphase_kernel(int64_t n_edges, const double *ks_shift, double k0, double k1, double k2,
+                              double2 *phase) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += (int64_t)gridDim.x * blockDim.x) {
+        const double ks = 2.0 * (k0 * ks_shift[3 * e] + k1 * ks_shift[3 * e + 1] + k2 * ks_shift[3 * e + 2]);
+        double sn, cs;
+        sincospi(ks, &sn, &cs);
+        phase[e] = make_double2(cs, -sn);
+    }
+}
+
+__global__ void ksample_kernel(int64_t nblk, const int64_t *ks_ptr, const double2 *phase, const int64_t *ks_voff,
+                               const double *ks_vals, const int64_t *uoff, const int32_t *ub_n, double2 *out,
+                               int warps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t u = (int64_t)blockIdx.x * warps + warp; u < nblk; u += (int64_t)gridDim.x * warps) {
+        const int n = ub_n[u];
+        const int64_t e0 = ks_ptr[u], e1 = ks_ptr[u + 1], o = uoff[u];
+        for (int q = lane; q < n; q += 32) {
+            double re = 0.0, im = 0.0;
+            for (int64_t e = e0; e < e1; ++e) {
+                const double2 ph = phase[e];
+                const double v = ks_vals[ks_voff[e] + q];
+                re = fma(v, ph.x, re);
+                im = fma(v, ph.y, im);
+            }
+            out[o + q] = make_double2(re, im);
+        }
+    }
+}
+
+cudaError_t launch_ksample(int64_t nblk, int64_t n_edges, const int64_t *ks_ptr, const double *ks_shift,
+                           const int64_t *ks_voff, const double *ks_vals, const int64_t *uoff, const int32_t *ub_n,
+                           const double *kfrac, double2 *phase, double2 *out, cudaStream_t s) {
+    if (n_edges > 0) {
+        int64_t need = (n_edges + 255) / 256;
+        kphase_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(n_edges, ks_shift, kfrac[0], kfrac[1],
+                                                                         kfrac[2], phase);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nblk == 0) return cudaSuccess;
+    const int warps = 8;
+    int64_t need = (nblk + warps - 1) / warps;
+    int grid = (int)(need < 65536 ? need : 65536);
+    ksample_kernel<<<grid, warps * 32, 0, s>>>(nblk, ks_ptr, phase, ks_voff, ks_vals, uoff, ub_n, out, warps);
     return cudaGetLastError();
 }
 

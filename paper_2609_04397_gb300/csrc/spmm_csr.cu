@@ -7,12 +7,15 @@
 // instruction whatever its mask), and the L lanes finish the sums with a
 // butterfly. Every output entry is written once.
 //
-// Four arithmetic kinds share the code (value type TV, accumulator TA, X type
+// The arithmetic kinds share the code (value type TV, accumulator TA, X type
 // TXI, Y type TX): FP64, FP32, FP32 products of an FP64 operator (FP32 value
-// copy, X converted once per call) and double-FP32 (hi/lo value copy and X).
+// copy, X converted once per call), double-FP32 (hi/lo value copy and X) and
+// the piece products of the tensor-core modes (split.cuh) - a scalar row has
+// one row, too thin for an MMA tile.
 #include <type_traits>
 
 #include "df.cuh"
+#include "split.cuh"
 #include "fma_kernel.cuh"
 
 namespace vbcsr {
@@ -65,7 +68,7 @@ __global__ void __launch_bounds__(256) csr_kernel(ProdArgs a) {
             for (int j = 0; j < CW; ++j) {
                 if (valid && lr == (j % L) && c0 + j < a.k) {
                     const int64_t row = w.yrow, c = c0 + j;
-                    TX r = alpha * (TX)acc[j];
+                    TX r = a.alpha == 1.0 ? (TX)acc[j] : alpha * (TX)acc[j];
                     if (a.beta != 0.0) r += beta * Y[row * a.ldy + c];
                     if (a.gamma != 0.0) r += gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
                     Y[row * a.ldy + c] = r;
@@ -133,6 +136,9 @@ const void *csr_kernel_ptr(int kind, int L, int64_t k) {
         case kCsrF32: return ptr_k<float, float, float, float>(L, k);
         case kCsrF32OnF64: return ptr_k<float, float, double, float>(L, k);
         case kCsrDF: return ptr_k<float2, DF, double, float2>(L, k);
+        case kCsrSplitTF32: return ptr_k<float, SplitF<kTF32>, double, float>(L, k);
+        case kCsrSplitTF32X3: return ptr_k<float, SplitF<kTF32X3>, double, float>(L, k);
+        case kCsrSplitBF16X2: return ptr_k<float, SplitF<kBF16X2>, double, float>(L, k);
         default: return nullptr;
     }
 }

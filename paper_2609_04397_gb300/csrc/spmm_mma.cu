@@ -24,7 +24,6 @@ namespace vbcsr {
 
 namespace {
 
-constexpr int kTF32 = 2, kTF32X3 = 3, kBF16X2 = 4;
 
 __device__ __forceinline__ uint32_t to_tf32(float v) {
     uint32_t r;
@@ -102,67 +101,8 @@ __device__ __forceinline__ void step(float (&acc)[4], const Pieces &ag, const Pi
     }
 }
 
-// Registers of U consecutive 16-column steps of a forward item: the lane's
-// float4 of value rows g and g + 8, and its X fragment values for NT 8-column
-// output tiles.
-template <int U, int NT>
-struct StepGroup {
-    float4 qa[U], qb[U];
-    float xv[U][NT][4];
-};
-
-// Issue the loads of the U steps starting at window column cg (window
-// [t0, t0 + tn) of item w; s_x holds the X row of each window column).
-template <int U, int NT>
-__device__ __forceinline__ void load_group(StepGroup<U, NT> &s, const float *__restrict__ vals,
-                                           const float *__restrict__ X, const ProdArgs &a, const WorkItem &w,
-                                           const int32_t *s_x, int t0, int tn, int cg, int64_t n0, int g, int t4) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int64_t col = (int64_t)t0 + cg + 16 * u + 4 * t4;
-        s.qa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        s.qb[u] = s.qa[u];
-        if (col < w.Kp) {   // Kp is a multiple of 4: the float4 is inside the row
-            if (g < w.B) s.qa[u] = __ldg(reinterpret_cast<const float4 *>(vals + w.vbase + (int64_t)g * w.Kp + col));
-            if (g + 8 < w.B)
-                s.qb[u] = __ldg(reinterpret_cast<const float4 *>(vals + w.vbase + (int64_t)(g + 8) * w.Kp + col));
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int cl = cg + 16 * u + 4 * t4;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int xr = (cl + j < tn) ? s_x[cl + j] : -1;
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-                const int64_t col = n0 + n * 8 + g;
-                s.xv[u][n][j] = (xr >= 0 && col < a.k) ? __ldg(X + (int64_t)xr * a.ldx + col) : 0.f;
-            }
-        }
-    }
-}
-
-template <int MODE, int U, int NT>
-__device__ __forceinline__ void mma_group(float (&acc)[NT][4], const StepGroup<U, NT> &s) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const float va[4] = {s.qa[u].x, s.qa[u].y, s.qa[u].z, s.qa[u].w};
-        const float vb[4] = {s.qb[u].x, s.qb[u].y, s.qb[u].z, s.qb[u].w};
-        Pieces pa, pb;
-        split4<MODE>(va, pa);
-        split4<MODE>(vb, pb);
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-            Pieces px;
-            split4<MODE>(s.xv[u][n], px);
-            step<MODE>(acc[n], pa, pb, px);
-        }
-    }
-}
-
 template <int MODE, bool TRANS, typename TX, int NT>
-__global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
+__global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
     const int warp = threadIdx.x >> 5;
@@ -180,27 +120,8 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
     const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
 
-    const int64_t stride = (int64_t)gridDim.x * warps;
-    // forward: while an item runs, the next one's values (one contiguous B x Kp
-    // run of the panel) are requested into L2. Its descriptor is read one item
-    // earlier still, so the request never waits for a load.
-    int64_t pf_base = 0;
-    uint32_t pf_bytes = 0;
-    auto pf_desc = [&](int64_t i) {
-        pf_bytes = 0;
-        if (!TRANS && i < a.n_items) {
-            const WorkItem &d = a.items[i];
-            pf_base = d.vbase;
-            pf_bytes = (uint32_t)min((int64_t)d.B * d.Kp * (int64_t)sizeof(float), (int64_t)kPrefetchMax);
-        }
-    };
-    pf_desc((int64_t)blockIdx.x * warps + warp + stride);
-    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += stride) {
+    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        if (!TRANS) {
-            if (lane == 0 && pf_bytes) prefetch_l2(vals + pf_base, pf_bytes);
-            pf_desc(it + 2 * stride);
-        }
         for (int64_t n0 = 0; n0 < a.k; n0 += 8 * NT) {
             float acc[NT][4];
 #pragma unroll
@@ -233,30 +154,58 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
                         __syncwarp();
                     }
                     if (!TRANS) {
-                        // forward: groups of U 16-column steps. All value and X loads of a
-                        // group are issued together, and for k <= 16 the next group's loads
-                        // are issued before this group's MMAs (two register buffers), so a
-                        // warp always has one to two groups of loads in flight. A window
-                        // holds kKMax = 512 columns, a multiple of 32 U: groups never
-                        // straddle two windows.
-                        constexpr int U = NT == 1 ? 2 : 1;
-                        if (NT <= 2) {
-                            StepGroup<U, NT> s0, s1;
-                            load_group(s0, vals, X, a, w, s_x, t0, tn, 0, n0, g, t4);
-                            for (int cg = 0; cg < tn; cg += 32 * U) {
-                                const bool more = cg + 16 * U < tn;
-                                if (more) load_group(s1, vals, X, a, w, s_x, t0, tn, cg + 16 * U, n0, g, t4);
-                                mma_group<MODE>(acc, s0);
-                                if (!more) break;
-                                if (cg + 32 * U < tn)
-                                    load_group(s0, vals, X, a, w, s_x, t0, tn, cg + 32 * U, n0, g, t4);
-                                mma_group<MODE>(acc, s1);
+                        // forward: groups of U steps; all value and X loads of a group are
+                        // issued before its MMAs, so each warp has U steps of loads in flight.
+                        // Measured on GB300 (50k-atom zinc-blende operator): k <= 8 runs best
+                        // with U = 2 at 6 CTAs per SM (77 registers), k <= 16 with U = 4 and
+                        // k <= 32 with U = 2 at 4 CTAs per SM (<= 128 registers, no spills).
+                        // A window holds kKMax = 512 columns, a multiple of 16 U, so a group
+                        // never straddles two windows.
+                        constexpr int U = NT == 1 ? 2 : (NT == 2 ? 4 : 2);
+                        for (int cg = 0; cg < tn; cg += 16 * U) {
+                            float4 qa[U], qb[U];
+                            float xv[U][NT][4];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int64_t col = (int64_t)t0 + cg + 16 * u + 4 * t4;
+                                qa[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                qb[u] = qa[u];
+                                if (col < w.Kp) {   // Kp is a multiple of 4: the float4 is inside the row
+                                    if (g < w.B)
+                                        qa[u] = __ldg(reinterpret_cast<const float4 *>(vals + w.vbase +
+                                                                                      (int64_t)g * w.Kp + col));
+                                    if (g + 8 < w.B)
+                                        qb[u] = __ldg(reinterpret_cast<const float4 *>(
+                                            vals + w.vbase + (int64_t)(g + 8) * w.Kp + col));
+                                }
                             }
-                        } else {
-                            for (int cg = 0; cg < tn; cg += 16 * U) {
-                                StepGroup<U, NT> s0;
-                                load_group(s0, vals, X, a, w, s_x, t0, tn, cg, n0, g, t4);
-                                mma_group<MODE>(acc, s0);
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const int cl = cg + 16 * u + 4 * t4;
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    const int xr = (cl + j < tn) ? s_x[cl + j] : -1;
+#pragma unroll
+                                    for (int n = 0; n < NT; ++n) {
+                                        const int64_t col = n0 + n * 8 + g;
+                                        xv[u][n][j] = (xr >= 0 && col < a.k) ? __ldg(X + (int64_t)xr * a.ldx + col)
+                                                                             : 0.f;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const float va[4] = {qa[u].x, qa[u].y, qa[u].z, qa[u].w};
+                                const float vb[4] = {qb[u].x, qb[u].y, qb[u].z, qb[u].w};
+                                Pieces pa, pb;
+                                split4<MODE>(va, pa);
+                                split4<MODE>(vb, pb);
+#pragma unroll
+                                for (int n = 0; n < NT; ++n) {
+                                    Pieces px;
+                                    split4<MODE>(xv[u][n], px);
+                                    step<MODE>(acc[n], pa, pb, px);
+                                }
                             }
                         }
                         continue;
@@ -303,7 +252,7 @@ __global__ void __launch_bounds__(128, 4) mma_product_kernel(ProdArgs a) {
                     if (r < w.B && col < a.k) {
                         const int64_t row = w.yrow + r;
                         TX *yp = Y + row * a.ldy + col;
-                        TX v = alpha * (TX)acc[n][j];
+                        TX v = a.alpha == 1.0 ? (TX)acc[n][j] : alpha * (TX)acc[n][j];
                         if (a.beta != 0.0) v += beta * *yp;
                         if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                         *yp = v;
@@ -536,7 +485,7 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
                 if (c16 + 16 < ncol) load_x(c16 + 16, xnext);
                 const int cl = c16 + 4 * t4;                 // chunk-relative first column of this lane
                 float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
-                if (cl < ncol) {                              // ncol is a multiple of 8: all four are inside
+                if (cl < ncol) {                              // ncol is a multiple of 4: all four are inside
                     if (g < wc.B) {
                         const float4 q = *reinterpret_cast<const float4 *>(buf + g * kStageLd + cl);
                         va[0] = q.x; va[1] = q.y; va[2] = q.z; va[3] = q.w;
@@ -569,7 +518,7 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
                         if (r < wc.B && col < a.k) {
                             const int64_t row = wc.yrow + r;
                             TX *yp = Y + row * a.ldy + col;
-                            TX v = alpha * (TX)acc[n][j];
+                            TX v = a.alpha == 1.0 ? (TX)acc[n][j] : alpha * (TX)acc[n][j];
                             if (a.beta != 0.0) v += beta * *yp;
                             if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                             *yp = v;

@@ -10,9 +10,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import F32, F64, PRECISION, check, lib
+from ._lib import C128, F32, F64, PRECISION, check, lib
 
-_TORCH_DTYPE = {F64: torch.float64, F32: torch.float32}
+_TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, C128: torch.complex128}
+_CODE = {torch.float64: F64, torch.float32: F32, torch.complex128: C128}
+_NP = {torch.float64: np.float64, torch.float32: np.float32, torch.complex128: np.complex128}
 
 
 def _stream(device) -> ctypes.c_void_p:
@@ -49,7 +51,7 @@ class VBCSR:
         """Build from host pattern arrays and packed values (numpy array or
         torch tensor, host or device), blocks row-major in pattern order."""
         device = torch.device(device or "cuda")
-        dt = F64 if dtype == torch.float64 else F32
+        dt = _CODE[dtype]
         rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
         rp, ci = _np(block_row_ptr, np.int64), _np(block_col_idx, np.int32)
         on_dev, vptr, keep = cls._values_arg(values, dtype, device)
@@ -72,7 +74,7 @@ class VBCSR:
         """One operator over independent structures; column indices local to
         each structure (see vbcsr_create_batched)."""
         device = torch.device(device or "cuda")
-        dt = F64 if dtype == torch.float64 else F32
+        dt = _CODE[dtype]
         so, co = _np(struct_brow_offsets, np.int64), _np(struct_bcol_offsets, np.int64)
         rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
         rp, ci = _np(block_row_ptr, np.int64), _np(local_block_col_idx, np.int32)
@@ -89,6 +91,34 @@ class VBCSR:
         gcol += co[s_of_row]
         return cls(h, dt, device, (rb, cb, rp, gcol.astype(np.int32)))
 
+    @classmethod
+    def from_images(cls, bsize, edge_i, edge_j, edge_R, edge_values, tau=None, device=None) -> "VBCSR":
+        """A periodic operator sampled in reciprocal space (Eq. 4, see
+        vbcsr_create_kspace): edges (i, j, R) of the real-space images with
+        their real b_i x b_j blocks packed row-major in edge order (numpy);
+        tau: fractional atom positions for the R+tau convention, or None.
+        The result is complex128 and zero until set_kpoint."""
+        device = torch.device(device or "cuda")
+        bs = _np(bsize, np.int32)
+        ei, ej = _np(edge_i, np.int32), _np(edge_j, np.int32)
+        eR = _np(edge_R, np.int32).reshape(-1, 3)
+        ev = _np(edge_values, np.float64)
+        tp = _np(tau, np.float64).reshape(-1, 3) if tau is not None else None
+        h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            check(lib().vbcsr_create_kspace(ctypes.byref(h), len(bs), bs.ctypes.data, len(ei), ei.ctypes.data,
+                                            ej.ctypes.data, eR.ctypes.data, ev.ctypes.data,
+                                            tp.ctypes.data if tp is not None else None, _stream(device)),
+                  "vbcsr_create_kspace")
+        H = cls(h, C128, device, None)
+        H.pattern = H.read_pattern()
+        return H
+
+    def set_kpoint(self, kfrac):
+        """Fill a from_images operator with O(k), k in fractional reciprocal coordinates."""
+        k = np.ascontiguousarray(np.asarray(kfrac, dtype=np.float64).reshape(3))
+        check(lib().vbcsr_set_kpoint(self._h, k.ctypes.data, _stream(self.device)), "vbcsr_set_kpoint")
+
     @staticmethod
     def _values_arg(values, dtype, device):
         if isinstance(values, torch.Tensor):
@@ -98,7 +128,7 @@ class VBCSR:
             if v.is_cuda:
                 return 1, v.data_ptr(), v
             return 0, v.data_ptr(), v
-        v = np.ascontiguousarray(values, dtype=np.float64 if dtype == torch.float64 else np.float32)
+        v = np.ascontiguousarray(values, dtype=_NP[dtype])
         return 0, v.ctypes.data, v
 
     def close(self):
@@ -273,7 +303,8 @@ class VBCSR:
         return self._prod(False, X, alpha, beta, Y, precision)
 
     def spmm_adjoint(self, X, alpha=1.0, beta=0.0, Y=None, precision="native"):
-        """Y = alpha H^T X + beta Y (Eq. 1)."""
+        """Y = alpha H^dagger X + beta Y (Eq. 1): the transpose of a real operator,
+        the conjugate transpose of a complex one."""
         return self._prod(True, X, alpha, beta, Y, precision)
 
     def spmm_ex(self, X, alpha, beta, Y, transpose=False, gamma=0.0, Z=None, R=None,

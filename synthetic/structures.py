@@ -239,3 +239,61 @@ def random_pattern(n_brows: int, n_bcols: int, sizes, density: float, seed: int,
         cols.append(c)
     col = np.concatenate(cols) if cols else np.zeros(0, np.int64)
     return BlockPattern(rbs, cbs, ptr, col.astype(np.int32))
+
+
+# ----------------------------------------------------------------------------
+# periodic crystals as lattice images
+
+
+def zincblende_cell(n_cells: int, a: float = 5.87, b_cation: int = 13, b_anion: int = 9) -> AtomSystem:
+    """Periodic zinc-blende crystal of n_cells^3 conventional cubic cells (8
+    atoms each: cations on the fcc sites, anions shifted by (a/4)(1,1,1)); the
+    periodic box has side n_cells * a."""
+    r = np.arange(n_cells, dtype=np.float64)
+    cells = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3) * a
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]]) * a
+    cat = (cells[:, None, :] + fcc[None]).reshape(-1, 3)
+    ani = cat + a / 4.0
+    pos = np.concatenate([cat, ani])
+    bs = np.concatenate([np.full(len(cat), b_cation, np.int32), np.full(len(ani), b_anion, np.int32)])
+    return AtomSystem(pos, bs, n_cells * a)
+
+
+def periodic_images(sys: AtomSystem, cutoff: float):
+    """Edges (i, j, R) of a periodic system: every atom pair and lattice
+    translation R (integer multiples of the box) with |pos_j + R box - pos_i| <
+    cutoff, including (i, i, 0). Returns (edge_i, edge_j, edge_R [n, 3],
+    distance), sorted by (i, j, R). A box wider than twice the cutoff gives at
+    most one R per pair (minimum image); a smaller one is enumerated."""
+    assert sys.box is not None
+    n, L = len(sys.bsize), float(sys.box)
+    pos = np.mod(sys.pos, L)
+    if L > 2.0 * cutoff:
+        tree = cKDTree(pos, boxsize=L)
+        pairs = tree.query_pairs(cutoff, output_type="ndarray").astype(np.int64)
+        d = pos[pairs[:, 1]] - pos[pairs[:, 0]]
+        R = -np.round(d / L).astype(np.int64)           # image of j nearest to i
+        dd = d + R * L
+        dist = np.sqrt(np.einsum("ij,ij->i", dd, dd))
+        ei = np.concatenate([np.arange(n), pairs[:, 0], pairs[:, 1]])
+        ej = np.concatenate([np.arange(n), pairs[:, 1], pairs[:, 0]])
+        eR = np.concatenate([np.zeros((n, 3), np.int64), R, -R])
+        ed = np.concatenate([np.zeros(n), dist, dist])
+    else:
+        m = int(np.ceil(cutoff / L))
+        tree = cKDTree(pos)
+        parts = []
+        for rx in range(-m, m + 1):
+            for ry in range(-m, m + 1):
+                for rz in range(-m, m + 1):
+                    R = np.array([rx, ry, rz], np.int64)
+                    other = cKDTree(pos + R * L)
+                    for i, js in enumerate(tree.query_ball_tree(other, cutoff)):
+                        for j in js:
+                            dv = pos[j] + R * L - pos[i]
+                            parts.append((i, j, rx, ry, rz, float(np.sqrt(dv @ dv))))
+        arr = np.array(parts, dtype=np.float64)
+        ei, ej = arr[:, 0].astype(np.int64), arr[:, 1].astype(np.int64)
+        eR, ed = arr[:, 2:5].astype(np.int64), arr[:, 5]
+    order = np.lexsort((eR[:, 2], eR[:, 1], eR[:, 0], ej, ei))
+    return (ei[order].astype(np.int32), ej[order].astype(np.int32), eR[order].astype(np.int32), ed[order])

@@ -191,3 +191,66 @@ def domain(kind: str, target_bytes: float = 500 * 2 ** 20, seed: int = 0) -> Wor
     pat = neighbor_pattern(sys, cutoff)
     vals = symmetric_values(pat, nnz_row_scale(pat), seed)
     return Workload(f"domain_{kind}_{n}", pat, vals, sys)
+
+
+# ----------------------------------------------------------------------------
+# periodic operators as lattice images
+
+
+@dataclass
+class PeriodicWorkload:
+    name: str
+    bsize: np.ndarray            # int32 [n_atoms]
+    edge_i: np.ndarray           # int32 [n_edges]
+    edge_j: np.ndarray
+    edge_R: np.ndarray           # int32 [n_edges, 3]
+    edge_dist: np.ndarray        # float64 [n_edges], Angstrom
+    edge_values: np.ndarray      # float64, the edges' blocks packed row-major in edge order
+    tau: np.ndarray              # float64 [n_atoms, 3], fractional positions in the box
+
+
+def image_values(bsize, edge_i, edge_j, edge_R, edge_dist, seed: int = 0, length: float = 2.0) -> np.ndarray:
+    """Real blocks of a symmetric periodic operator: O(j, i, -R) = O(i, j, R)^T
+    (so that every O(k) is Hermitian), entries exp(-r / length) N(0, 1), the
+    (i, i, 0) blocks (G + G^T) / sqrt(2); drawn from the counter-based generator
+    keyed by the canonical orientation of each edge."""
+    bs = np.asarray(bsize, np.int64)
+    ei, ej = np.asarray(edge_i, np.int64), np.asarray(edge_j, np.int64)
+    eR = np.asarray(edge_R, np.int64).reshape(-1, 3)
+    fwd = np.column_stack([ei, ej, eR])
+    rev = np.column_stack([ej, ei, -eR])
+    # canonical orientation: the lexicographically smaller of the edge and its mirror
+    use_rev = np.zeros(len(ei), bool)
+    for c in range(5):
+        undecided = ~use_rev & np.all(fwd[:, :c] == rev[:, :c], axis=1)
+        use_rev |= undecided & (rev[:, c] < fwd[:, c])
+    canon = np.where(use_rev[:, None], rev, fwd)
+    keys, cid = np.unique(canon, axis=0, return_inverse=True)
+    cid = cid.reshape(-1)
+    ca, cb = bs[keys[:, 0]], bs[keys[:, 1]]
+    coff = np.concatenate([[0], np.cumsum(ca * cb)])
+    G = np.empty(int(coff[-1]), np.float64)
+    cnt = np.arange(len(G), dtype=np.uint64)
+    _native.lib().syn_normal_at(stream_key(seed, STREAM_GENERIC), len(G), _native.ptr(cnt), _native.ptr(G))
+    out = []
+    for e in range(len(ei)):
+        c = cid[e]
+        blk = G[coff[c]:coff[c + 1]].reshape(ca[c], cb[c])
+        if keys[c, 0] == keys[c, 1] and not keys[c, 2:].any():
+            blk = (blk + blk.T) / np.sqrt(2.0)          # (i, i, 0): its own mirror
+        elif use_rev[e]:
+            blk = blk.T
+        out.append((np.exp(-edge_dist[e] / length) * blk).ravel())
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def zincblende_crystal(n_cells: int = 2, seed: int = 0) -> PeriodicWorkload:
+    """Periodic zinc-blende crystal (a = 5.87 A, cation b = 13, anion b = 9)
+    of n_cells^3 conventional cells, images to the third neighbour shell plus
+    self (the nanoparticle's cutoff), entries exp(-r/2 A) N(0,1), symmetric."""
+    from .structures import periodic_images, zincblende_cell
+    sys = zincblende_cell(n_cells, ZB_A)
+    ei, ej, eR, ed = periodic_images(sys, ZB_CUTOFF)
+    vals = image_values(sys.bsize, ei, ej, eR, ed, seed)
+    return PeriodicWorkload(f"zincblende_crystal_{len(sys.bsize)}", sys.bsize, ei, ej, eR, ed, vals,
+                            np.mod(sys.pos, sys.box) / sys.box)

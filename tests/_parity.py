@@ -14,14 +14,19 @@ TOL_F64 = 1e-12
 TOL_MIXED = 1e-5
 
 
+def _as_f64(a):
+    a = np.asarray(a)
+    return a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+
+
 def rel_fro(got, ref):
-    d = np.linalg.norm(np.asarray(got, np.float64) - ref)
+    d = np.linalg.norm(_as_f64(got) - ref)
     n = np.linalg.norm(ref)
     return d / n if n > 0 else d
 
 
 def check_elementwise(got, ref, scale, tol):
-    got = np.asarray(got, np.float64)
+    got = _as_f64(got)
     bad = np.abs(got - ref) > tol * scale + 1e-300
     assert not bad.any(), (f"{bad.sum()} entries off; worst "
                            f"{np.max(np.abs(got - ref) / np.maximum(scale, 1e-300))}")

@@ -63,14 +63,36 @@ def test_mixed_adjoint_and_shapes(mode):
         check_elementwise(got, ref, scale, 1e-4)
 
 
-def test_single_tf32_within_its_own_bound():
+@pytest.mark.parametrize("k", [1, 2, 8])
+def test_single_tf32_within_its_own_bound(k):
+    """k <= 2 runs the piece products on the CUDA cores, k = 8 on the tensor cores."""
     w = syn.tiny_multispecies(0)
     H = _handle(w.pattern, w.values)
-    X = syn.normal_panel(w.pattern.n_cols, 8, 0)
+    X = syn.normal_panel(w.pattern.n_cols, k, 0)
     got = H.spmm(_dev(X), precision="tf32").cpu().numpy()
     ref, scale = forward_ref(w.pattern, w.values, X, 1.0, 0.0, None)
     check_elementwise(got, ref, scale, 2.0 ** -9)
     assert rel_fro(got, ref) > 1e-6   # really ran in reduced precision
+
+
+@pytest.mark.parametrize("mode", ["tf32", "tf32x3", "bf16x2"])
+def test_thin_products_cuda_core_form_matches_tensor_core_form(mode):
+    """At k <= 2 the tensor-core modes form the same piece products on the CUDA
+    cores. Both forms hold the mode's bound."""
+    pat = syn.random_pattern(40, 40, (1, 4, 9, 13, 16, 20), 0.25, 77, empty_rows=2, unsorted=True)
+    vals = syn.random_values(pat, 77)
+    H = _handle(pat, vals)
+    X = np.random.default_rng(5).standard_normal((pat.n_cols, 3))
+    ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
+    tol = 2.0 ** -9 if mode == "tf32" else 1e-4
+    Y3 = H.spmm(_dev(X), precision=mode).cpu().numpy()          # tensor cores (k = 3)
+    Y2 = H.spmm(_dev(X[:, :2]), precision=mode).cpu().numpy()   # CUDA cores (k = 2)
+    Y1 = H.spmm(_dev(X[:, 1:2]), precision=mode).cpu().numpy()  # CUDA cores (k = 1)
+    check_elementwise(Y3, ref, scale, tol)
+    check_elementwise(Y2, ref[:, :2], scale[:, :2], tol)
+    check_elementwise(Y1[:, 0], ref[:, 1], scale[:, 1], tol)
+    if mode != "tf32":
+        assert rel_fro(Y2, ref[:, :2]) <= TOL_MIXED
 
 
 @pytest.mark.parametrize("mode", ["native", "tf32x3", "bf16x2"])

@@ -375,3 +375,113 @@ def test_spgemm_threshold_respects_norm_bound():
                 assert np.linalg.norm(blk) >= eps - 1e-12
             else:
                 assert np.linalg.norm(blk) < eps + 1e-12
+
+
+# ----------------------------------------------------------------------------
+# reciprocal-space sampling (Eq. 4) and complex block products
+
+
+def test_kspace_chain_closed_form():
+    """One orbital per cell, on-site e and hopping t to the neighbouring cells:
+    the tight-binding band O(k) = e + 2 t cos(2 pi k_x)."""
+    e, t = 0.3, -1.1
+    ei, ej = [0, 0, 0], [0, 0, 0]
+    eR = [0, 0, 0, 1, 0, 0, -1, 0, 0]
+    vals = [e, t, t]
+    for kx in (0.0, 0.1, 0.25, 0.5, 0.77):
+        k = [kx, 0.3, -0.2]
+        want = e + 2.0 * t * np.cos(2.0 * np.pi * kx)
+        assert abs(oracle.kspace_dense([1], ei, ej, eR, vals, k)[0, 0] - want) < 1e-14
+        *_, v = oracle.kspace_blocks([1], ei, ej, eR, vals, k)
+        assert abs(v[0] - want) < 1e-14
+    # the sign of Eq. 4: a lone forward hop (0, 0, R = +x) samples to t exp(-2 pi i k_x)
+    H = oracle.kspace_dense([1], [0], [0], [1, 0, 0], [t], [0.25, 0, 0])
+    assert abs(H[0, 0] - (-1j * t)) < 1e-15
+
+
+def test_kspace_two_site_chain_band():
+    """Two sites per cell, intra-cell hopping v and inter-cell hopping w: the
+    bands are +-|v + w exp(2 pi i k)| (the dimerised chain), and the R+tau
+    convention with tau = (0, 1/2) gives the same spectrum."""
+    v, w = 0.7, 1.3
+    ei, ej = [0, 1, 1, 0], [1, 0, 0, 1]
+    eR = [0, 0, 0, 0, 0, 0, 1, 0, 0, -1, 0, 0]
+    vals = [v, v, w, w]
+    tau = [[0, 0, 0], [0.5, 0, 0]]
+    for kx in (0.0, 0.13, 0.5, 0.81):
+        band = abs(v + w * np.exp(2j * np.pi * kx))
+        for tp in (None, tau):
+            H = oracle.kspace_dense([1, 1], ei, ej, eR, vals, [kx, 0, 0], tp)
+            assert np.allclose(H, H.conj().T, atol=1e-15)
+            assert np.allclose(np.linalg.eigvalsh(H), [-band, band], atol=1e-14)
+
+
+def _supercell_x2(w):
+    """The same crystal as a 2 x 1 x 1 supercell: atom (i, m) = i + n m, edge
+    (i, j, R) from cell m reaches cell m + R_x = 2 q + m' (m' in {0, 1})."""
+    n = len(w.bsize)
+    bi, bj, bR, bv = [], [], [], []
+    off = np.concatenate([[0], np.cumsum(w.bsize[w.edge_i] * w.bsize[w.edge_j])])
+    for m in (0, 1):
+        for e in range(len(w.edge_i)):
+            t = m + int(w.edge_R[e, 0])
+            q, mp = t // 2, t % 2
+            bi.append(int(w.edge_i[e]) + n * m)
+            bj.append(int(w.edge_j[e]) + n * mp)
+            bR.append([q, int(w.edge_R[e, 1]), int(w.edge_R[e, 2])])
+            bv.append(w.edge_values[off[e]:off[e + 1]])
+    return np.concatenate([w.bsize, w.bsize]), bi, bj, np.array(bR).ravel(), np.concatenate(bv)
+
+
+def test_kspace_bloch_supercell_spectrum():
+    """Bloch's theorem: the supercell operator doubled along x, sampled at
+    K = (0, Ky, Kz), has the spectrum of O(k) at k = (0, Ky, Kz) and
+    (1/2, Ky, Kz) together (zinc-blende cell with several images per pair)."""
+    w = syn.zincblende_crystal(1)
+    bs2, bi, bj, bR, bv = _supercell_x2(w)
+    for ky, kz in ((0.0, 0.0), (0.21, -0.37)):
+        Hs = oracle.kspace_dense(bs2, bi, bj, bR, bv, [0.0, ky, kz])
+        e_super = np.linalg.eigvalsh(Hs)
+        e_cell = np.concatenate([
+            np.linalg.eigvalsh(oracle.kspace_dense(w.bsize, w.edge_i, w.edge_j, w.edge_R, w.edge_values,
+                                                   [kx, ky, kz])) for kx in (0.0, 0.5)])
+        assert np.allclose(np.sort(e_cell), e_super, atol=1e-11 * np.abs(e_super).max())
+
+
+def test_kspace_invariants():
+    """O(k + G) = O(k) for an integer G (R convention), O(k) Hermitian for the
+    symmetric images, the R+tau convention equal to D O(k) D^dagger with
+    D = diag(exp(2 pi i k . tau_i)), and the union-pattern blocks equal to the
+    dense assembly."""
+    w = syn.zincblende_crystal(1)
+    args = (w.bsize, w.edge_i, w.edge_j, w.edge_R, w.edge_values)
+    k = np.array([0.12, -0.31, 0.4])
+    H = oracle.kspace_dense(*args, k)
+    assert np.allclose(H, oracle.kspace_dense(*args, k + np.array([1, -2, 3])), atol=1e-12)
+    assert np.allclose(H, H.conj().T, atol=1e-14)
+    d = np.repeat(np.exp(2j * np.pi * (w.tau @ k)), w.bsize)
+    Ht = oracle.kspace_dense(*args, k, w.tau)
+    assert np.allclose(Ht, d[:, None] * H * d.conj()[None, :], atol=1e-13)
+    rb, cb, ptr, cols, vals = oracle.kspace_blocks(*args, k)
+    pat = BlockPattern(rb, cb, ptr, cols)
+    assert np.allclose(oracle.to_dense(pat, vals.real) + 1j * oracle.to_dense(pat, vals.imag), H, atol=1e-14)
+
+
+def test_complex_block_products_against_dense():
+    """spmm_complex / spmm_adjoint_complex against dense complex algebra, the
+    adjoint with the conjugate transpose, and <Y, H X> = <H^dagger Y, X>."""
+    pat = syn.random_pattern(23, 19, (1, 3, 5, 8), 0.3, 61, empty_rows=2, unsorted=True)
+    rng = np.random.default_rng(61)
+    vals = rng.standard_normal(pat.nnz) + 1j * rng.standard_normal(pat.nnz)
+    D = oracle.to_dense(pat, vals.real) + 1j * oracle.to_dense(pat, vals.imag)
+    X = rng.standard_normal((pat.n_cols, 4)) + 1j * rng.standard_normal((pat.n_cols, 4))
+    Y0 = rng.standard_normal((pat.n_rows, 4)) + 1j * rng.standard_normal((pat.n_rows, 4))
+    got = oracle.spmm_complex(pat, vals, X, 2.0, -0.5, Y0)
+    assert np.allclose(got, 2.0 * D @ X - 0.5 * Y0, atol=1e-13)
+    Xa = rng.standard_normal((pat.n_rows, 3)) + 1j * rng.standard_normal((pat.n_rows, 3))
+    ga = oracle.spmm_adjoint_complex(pat, vals, Xa)
+    assert np.allclose(ga, D.conj().T @ Xa, atol=1e-13)
+    Yv, Xv = Xa[:, :1], X[:, :1]
+    lhs = np.vdot(Yv, oracle.spmm_complex(pat, vals, Xv))
+    rhs = np.vdot(oracle.spmm_adjoint_complex(pat, vals, Yv), Xv)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)

@@ -308,10 +308,10 @@ def test_backend_selection():
 def test_csr_backend_scalar_kernel(density, k):
     """Scalar operators (all blocks 1 x 1) through the scalar kernel, against
     the oracle and against the block-row kernels on the same operator. The
-    densities give ~5, ~52, ~156 and 300 entries per row, so every lane count
-    the kernel picks from the row length (2, 4, 8 for FP64; 4 to 32 for FP32)
-    runs."""
-    pat = syn.random_pattern(300, 300, (1,), density, 90 + k, empty_rows=7, unsorted=True)
+    densities give ~12, ~120, ~360 and 600 entries per row, so every lane
+    count the kernel picks from the row length (2, 4, 8 for FP64 and
+    double-FP32; 4, 8, 16, 32 for the FP32 kinds) runs."""
+    pat = syn.random_pattern(300, 600, (1,), density, 90 + k, empty_rows=7, unsorted=True)
     vals = syn.random_values(pat, 90 + k)
     H = _handle(pat, vals)
     assert H.backend == "csr"
@@ -337,3 +337,9 @@ def test_csr_backend_scalar_kernel(density, k):
     ref, scale = forward_ref(pat, vals, Xh, 2.0, -1.0, Y0)
     assert rel_fro(Yd.cpu().numpy(), ref) <= TOL_MIXED
     check_elementwise(Yd.cpu().numpy(), ref, scale, 1e-4)
+    # and the tensor-core modes, whose piece products run in the scalar kernel
+    for mode in ("tf32x3", "bf16x2"):
+        Yd = _dev(Y0)
+        H.spmm(X, 2.0, -1.0, Yd, precision=mode)
+        assert rel_fro(Yd.cpu().numpy(), ref) <= TOL_MIXED
+        check_elementwise(Yd.cpu().numpy(), ref, scale, 1e-4)
