@@ -300,7 +300,7 @@ def domains_section(dev, steps):
     return out
 
 
-def kspace_section(dev, steps, n_cells=18):
+def kspace_section(dev, steps, n_cells):
     """A periodic zinc-blende crystal of n_cells^3 conventional cells (the
     nanoparticle's species, cutoff and value recipe; one image per atom pair)
     sampled in reciprocal space (Eq. 4): the sampling itself (edge phases,
@@ -527,7 +527,7 @@ def run_ours(args):
 
     batched = batched_section(dev, args.steps) if not args.no_batched else None
     domains = domains_section(dev, args.steps) if args.domains else None
-    kspace = kspace_section(dev, args.steps) if args.kspace else None
+    kspace = kspace_section(dev, args.steps, max(1, round((args.atoms / 8) ** (1 / 3)))) if args.kspace else None
     H.check()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

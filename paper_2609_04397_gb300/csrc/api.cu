@@ -119,6 +119,10 @@ struct vbcsr_matrix {
     bool paneldf_valid = false;
     float2 *xdf = nullptr;        // (hi, lo) pairs of the current X for the double-FP32 mode
     size_t xdf_elems = 0;
+    uint32_t *panelbf = nullptr;  // values split into packed bf16 (hi, lo) words for the BF16X2 mode
+    bool panelbf_valid = false;
+    uint32_t *xbf = nullptr;      // the current X split the same way
+    size_t xbf_elems = 0;
     WorkItem *fwd_items = nullptr, *adj_items = nullptr;   // bucketed by row count
     WorkItem *fwd_lpt = nullptr, *adj_lpt = nullptr;       // all items, descending cost
     int64_t n_fwd_items = 0, n_adj_items = 0;
@@ -679,6 +683,14 @@ extern "C" int vbcsr_destroy(vbcsr_t *A) {
 // ---------------------------------------------------------------------------
 // values
 
+static int refresh_panelbf(vbcsr_t *A, cudaStream_t s) {
+    if (A->dtype != VBCSR_F64) return VBCSR_OK;
+    if (!A->panelbf) CUDA_TRY(A->alloc(&A->panelbf, (size_t)A->panel_elems), "alloc split value copy");
+    CUDA_TRY(launch_split_bf16((const double *)A->panel, A->panelbf, A->panel_elems, s), "split values");
+    A->panelbf_valid = true;
+    return VBCSR_OK;
+}
+
 static int refresh_panel32(vbcsr_t *A, cudaStream_t s) {
     if (A->dtype != VBCSR_F64) return VBCSR_OK;
     if (!A->panel32) CUDA_TRY(A->alloc(&A->panel32, (size_t)A->panel_elems), "alloc FP32 value copy");
@@ -738,6 +750,10 @@ extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, v
     if (e != cudaSuccess) return cuda_fail(e, "set_values");
     if (A->panel32) {
         int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+    if (A->panelbf) {
+        int rc = refresh_panelbf(A, s);
         if (rc) return rc;
     }
     if (A->paneldf) return refresh_paneldf(A, s);
@@ -849,8 +865,23 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const bool f64 = A->dtype == VBCSR_F64;
     int mode = precision;
     if (!f64 && mode == VBCSR_PREC_F32) mode = VBCSR_PREC_NATIVE;
-    if (f64 && mode != VBCSR_PREC_NATIVE && mode != VBCSR_PREC_DF32 && !A->panel32_valid) {
+    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32 || mode == VBCSR_PREC_DF32);
+    // a tensor-core mode on a product too thin for an MMA tile (few columns, or the
+    // single-row items of a scalar operator) runs its piece products on the CUDA cores
+    const bool csr_kernel =
+        A->backend == VBCSR_BACKEND_CSR && !trans && !cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
+    const bool split = !fma && f64 && !trans && (k <= kSplitFmaMaxK || csr_kernel);
+    // the BF16X2 forward kernel of an FP64 operator reads values and X split once
+    // into packed bf16 (hi, lo) words (the plain kernel; the staged one splits itself)
+    const bool presplit = f64 && mode == VBCSR_PREC_BF16X2 && !trans && !split &&
+                          !(A->schedule & VBCSR_SCHED_MMA_STAGED);
+    const int mma_mode = presplit ? kBF16X2Presplit : mode;
+    if (f64 && mode != VBCSR_PREC_NATIVE && mode != VBCSR_PREC_DF32 && !presplit && !A->panel32_valid) {
         int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+    if (presplit && !A->panelbf_valid) {
+        int rc = refresh_panelbf(A, s);
         if (rc) return rc;
     }
     if (mode == VBCSR_PREC_DF32 && !A->paneldf_valid) {
@@ -868,6 +899,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             if (rc) return rc;
             CUDA_TRY(launch_split_df(xrows, k, (const double *)X, ldx, A->xdf, s), "split X");
             X = A->xdf;
+        } else if (presplit) {
+            int rc = grow(A, &A->xbf, &A->xbf_elems, need, s, "alloc split copy of X");
+            if (rc) return rc;
+            CUDA_TRY(launch_split_bf16_panel(xrows, k, (const double *)X, ldx, A->xbf, s), "split X");
+            X = A->xbf;
         } else {
             int rc = grow(A, &A->xconv, &A->xconv_elems, need, s, "alloc FP32 copy of X");
             if (rc) return rc;
@@ -880,6 +916,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     ProdArgs a;
     memset(&a, 0, sizeof(a));
     a.values = mode == VBCSR_PREC_DF32 ? (const void *)A->paneldf
+             : presplit ? (const void *)A->panelbf
              : (f64 && mode != VBCSR_PREC_NATIVE) ? (const void *)A->panel32 : A->panel;
     a.fl = {A->fl_xrow, A->fl_pcol, A->fl_w};
     a.tl = {A->tl_pbase, A->tl_kp, A->tl_bi, A->tl_xrow, A->tl_vcol};
@@ -901,12 +938,6 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const int kc_auto = auto_kc(k);
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
-    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32 || mode == VBCSR_PREC_DF32);
-    // a tensor-core mode on a product too thin for an MMA tile (few columns, or the
-    // single-row items of a scalar operator) runs its piece products on the CUDA cores
-    const bool csr_kernel =
-        A->backend == VBCSR_BACKEND_CSR && !trans && !cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
-    const bool split = !fma && f64 && !trans && (k <= kSplitFmaMaxK || csr_kernel);
     int64_t used = 0;
     // one launch of `kern` over items[0..n) with `warps` warps per CTA
     auto launch = [&](int B, const WorkItem *items, int64_t n, int warps, const void *kern, size_t smem) -> int {
@@ -936,7 +967,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         else if (split)
             e = launch_fma_split(mode, a, s);
         else
-            e = launch_mma(mode, f64, trans, a, s);
+            e = launch_mma(mma_mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
         return VBCSR_OK;
     };
@@ -953,7 +984,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         // tensor-core kernel: the row count is a runtime mask, one launch serves every item
         const bool staged = !trans && (A->schedule & VBCSR_SCHED_MMA_STAGED);
         a.mma_staged = staged ? 1 : 0;
-        const void *kern = mma_kernel_ptr(mode, f64, trans, staged, k);
+        const void *kern = mma_kernel_ptr(mma_mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
     } else if (csr_kernel) {
@@ -1255,6 +1286,10 @@ extern "C" int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream) {
              "shift_scale");
     if (A->panel32) {
         int rc = refresh_panel32(A, s);
+        if (rc) return rc;
+    }
+    if (A->panelbf) {
+        int rc = refresh_panelbf(A, s);
         if (rc) return rc;
     }
     if (A->paneldf) return refresh_paneldf(A, s);

@@ -66,7 +66,7 @@ template <typename TX>
 __device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_t c, TX acc, double &dot) {
     TX *Y = static_cast<TX *>(a.Y);
     TX *yp = Y + row * a.ldy + c;
-    TX r = a.alpha == 1.0 ? acc : (TX)a.alpha * acc;   // alpha = 1 skips a multiply (FP64 pipe)
+    TX r = (TX)a.alpha * acc;
     if (a.beta != 0.0) r += (TX)a.beta * *yp;
     if (a.gamma != 0.0) r += (TX)a.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
     *yp = r;
@@ -79,7 +79,7 @@ template <>
 __device__ __forceinline__ void write_out<double2>(const ProdArgs &a, int64_t row, int64_t c, double2 acc,
                                                    double &dot) {
     double2 *yp = static_cast<double2 *>(a.Y) + row * a.ldy + c;
-    double2 r = a.alpha == 1.0 ? acc : make_double2(a.alpha * acc.x, a.alpha * acc.y);
+    double2 r = make_double2(a.alpha * acc.x, a.alpha * acc.y);
     if (a.beta != 0.0) {
         const double2 y = *yp;
         r.x += a.beta * y.x;

@@ -33,8 +33,10 @@ constexpr int kPadK = 8;         // panel width padding (elements)
 constexpr int kPadKScalar = 4;   // the same for scalar (CSR-backend) operators
 constexpr int kKMax = 512;       // virtual columns staged in shared memory per pass
 constexpr int kPartialsCap = 1 << 16;
-// tensor-core precision modes (the values of their vbcsr_precision codes)
-constexpr int kTF32 = 2, kTF32X3 = 3, kBF16X2 = 4;
+// tensor-core precision modes (the values of their vbcsr_precision codes), and
+// the BF16X2 forward kernel on operands split once into packed bf16 (hi, lo)
+// words (an internal launch mode, not a precision code)
+constexpr int kTF32 = 2, kTF32X3 = 3, kBF16X2 = 4, kBF16X2Presplit = 16;
 // below this many columns the tensor-core modes of an FP64 operator run their
 // piece products on the CUDA cores (an MMA tile would be mostly padding)
 constexpr int kSplitFmaMaxK = 2;
@@ -174,6 +176,10 @@ cudaError_t launch_permute_values(int esize, bool to_panel, int64_t nblk, const 
                                   const int64_t *pbase, const int32_t *kp, const int32_t *bi,
                                   const int32_t *bj, const void *user, void *panel, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
+// FP64 -> FP32 v -> one 32-bit word: bf16_rn(v) in the low half, bf16_rn(v - that) in the high half
+cudaError_t launch_split_bf16(const double *in, uint32_t *out, int64_t n, cudaStream_t s);
+cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, int64_t ld, uint32_t *out,
+                                    cudaStream_t s);
 // out[rows, k] (leading dimension k) = FP32 of the FP64 panel in (leading dimension ld)
 cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
                                             cudaStream_t s);

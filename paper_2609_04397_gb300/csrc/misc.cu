@@ -1,5 +1,7 @@
 // Pattern-sampled product (SDDMM), value permutation between packed order and
 // panels, and the fixed-order FP64 reductions used by the Chebyshev moments.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace vbcsr {
@@ -183,6 +185,43 @@ cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, c
     if (n == 0) return cudaSuccess;
     int64_t need = (n + 255) / 256;
     convert_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+// the operand pieces of the BF16X2 mode, formed once per value as the kernel
+// would form them (FP32 value v, hi = bf16_rn(v), lo = bf16_rn(v - hi))
+__device__ __forceinline__ uint32_t bf16_pieces(double x) {
+    const float v = (float)x;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+}
+
+__global__ void split_bf16_kernel(const double *in, uint32_t *out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = bf16_pieces(in[i]);
+}
+
+__global__ void split_bf16_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, uint32_t *out) {
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        out[e] = bf16_pieces(in[r * ld + c]);
+    }
+}
+
+cudaError_t launch_split_bf16(const double *in, uint32_t *out, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t need = (n + 255) / 256;
+    split_bf16_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, int64_t ld, uint32_t *out,
+                                    cudaStream_t s) {
+    if (rows * k == 0) return cudaSuccess;
+    int64_t need = (rows * k + 255) / 256;
+    split_bf16_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, in, ld, out);
     return cudaGetLastError();
 }
 

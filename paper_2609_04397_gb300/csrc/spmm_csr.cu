@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) csr_kernel(ProdArgs a) {
             for (int j = 0; j < CW; ++j) {
                 if (valid && lr == (j % L) && c0 + j < a.k) {
                     const int64_t row = w.yrow, c = c0 + j;
-                    TX r = a.alpha == 1.0 ? (TX)acc[j] : alpha * (TX)acc[j];
+                    TX r = alpha * (TX)acc[j];
                     if (a.beta != 0.0) r += beta * Y[row * a.ldy + c];
                     if (a.gamma != 0.0) r += gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
                     Y[row * a.ldy + c] = r;

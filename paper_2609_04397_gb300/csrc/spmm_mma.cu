@@ -62,7 +62,16 @@ struct Pieces {
 
 template <int MODE>
 __device__ __forceinline__ void split4(const float (&v)[4], Pieces &p) {
-    if (MODE == kBF16X2) {
+    if (MODE == kBF16X2Presplit) {
+        // operands already split into words (hi bf16 low half, lo bf16 high half):
+        // pair the halves of columns (c0, c1) and (c2, c3)
+        const uint32_t w0 = __float_as_uint(v[0]), w1 = __float_as_uint(v[1]);
+        const uint32_t w2 = __float_as_uint(v[2]), w3 = __float_as_uint(v[3]);
+        p.bh[0] = __byte_perm(w0, w1, 0x5410);
+        p.bh[1] = __byte_perm(w2, w3, 0x5410);
+        p.bl[0] = __byte_perm(w0, w1, 0x7632);
+        p.bl[1] = __byte_perm(w2, w3, 0x7632);
+    } else if (MODE == kBF16X2) {
         float h[4], l[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -85,7 +94,7 @@ __device__ __forceinline__ void split4(const float (&v)[4], Pieces &p) {
 // acc += A(rows g, g+8; 16 columns) * B(16 columns; 8 output columns)
 template <int MODE>
 __device__ __forceinline__ void step(float (&acc)[4], const Pieces &ag, const Pieces &ag8, const Pieces &b) {
-    if (MODE == kBF16X2) {
+    if (MODE == kBF16X2 || MODE == kBF16X2Presplit) {
         mma_bf16(acc, ag.bh[0], ag8.bh[0], ag.bh[1], ag8.bh[1], b.bh[0], b.bh[1]);
         mma_bf16(acc, ag.bh[0], ag8.bh[0], ag.bh[1], ag8.bh[1], b.bl[0], b.bl[1]);
         mma_bf16(acc, ag.bl[0], ag8.bl[0], ag.bl[1], ag8.bl[1], b.bh[0], b.bh[1]);
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdA
                     if (r < w.B && col < a.k) {
                         const int64_t row = w.yrow + r;
                         TX *yp = Y + row * a.ldy + col;
-                        TX v = a.alpha == 1.0 ? (TX)acc[n][j] : alpha * (TX)acc[n][j];
+                        TX v = alpha * (TX)acc[n][j];
                         if (a.beta != 0.0) v += beta * *yp;
                         if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                         *yp = v;
@@ -518,7 +527,7 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
                         if (r < wc.B && col < a.k) {
                             const int64_t row = wc.yrow + r;
                             TX *yp = Y + row * a.ldy + col;
-                            TX v = a.alpha == 1.0 ? (TX)acc[n][j] : alpha * (TX)acc[n][j];
+                            TX v = alpha * (TX)acc[n][j];
                             if (a.beta != 0.0) v += beta * *yp;
                             if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                             *yp = v;
@@ -617,6 +626,11 @@ const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int6
     VBCSR_PTR(kBF16X2)
 #undef VBCSR_PTR
 #undef VBCSR_PTR_NT
+    if (mode == kBF16X2Presplit && xdouble && !trans && !staged) {
+        if (nt == 1) return (const void *)mma_product_kernel<kBF16X2Presplit, false, double, 1>;
+        if (nt == 2) return (const void *)mma_product_kernel<kBF16X2Presplit, false, double, 2>;
+        return (const void *)mma_product_kernel<kBF16X2Presplit, false, double, 4>;
+    }
     return nullptr;
 }
 
@@ -625,6 +639,10 @@ cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cu
         case kTF32: return launch_mode<kTF32>(xdouble, trans, a, s);
         case kTF32X3: return launch_mode<kTF32X3>(xdouble, trans, a, s);
         case kBF16X2: return launch_mode<kBF16X2>(xdouble, trans, a, s);
+        case kBF16X2Presplit:
+            // forward, plain kernel, FP64 X / Y only (the split copies belong to FP64 operators)
+            if (!xdouble || trans || a.mma_staged) return cudaErrorInvalidValue;
+            return launch_nt<kBF16X2Presplit, false, double>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

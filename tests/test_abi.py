@@ -101,3 +101,27 @@ def test_product_failure_modes_are_compiled_in(L):
     with pytest.raises(VBCSRError) as ei:
         check(L.vbcsr_set_tuning(None, 8, 4), "vbcsr_set_tuning")
     assert "INVALID_ARG" in str(ei.value)
+
+
+def test_kspace_host_validation(L):
+    """vbcsr_create_kspace rejects bad edges on the host; vbcsr_set_kpoint
+    rejects NULL handles and k-points."""
+    from paper_2609_04397_gb300._lib import SIGNATURES  # noqa: F401 (signatures set on load)
+    h = ctypes.c_void_p()
+    bs = np.array([2, 3], np.int32)
+    ei, ej = np.array([0, 1], np.int32), np.array([1, 2], np.int32)     # atom 2 does not exist
+    eR = np.zeros((2, 3), np.int32)
+    ev = np.ones(12)
+    rc = L.vbcsr_create_kspace(ctypes.byref(h), 2, bs.ctypes.data, 2, ei.ctypes.data, ej.ctypes.data,
+                               eR.ctypes.data, ev.ctypes.data, None, None)
+    assert rc == -2 and not h.value
+    assert b"outside" in L.vbcsr_last_error_detail()
+    bad = np.array([2, 0], np.int32)                                    # block size 0
+    ej_ok = np.array([1, 0], np.int32)
+    rc = L.vbcsr_create_kspace(ctypes.byref(h), 2, bad.ctypes.data, 2, ei.ctypes.data, ej_ok.ctypes.data,
+                               eR.ctypes.data, ev.ctypes.data, None, None)
+    assert rc == -2
+    rc = L.vbcsr_create_kspace(ctypes.byref(h), 2, bs.ctypes.data, 2, None, ej_ok.ctypes.data,
+                               eR.ctypes.data, ev.ctypes.data, None, None)
+    assert rc == -1
+    assert L.vbcsr_set_kpoint(None, None, None) == -1
