@@ -45,12 +45,16 @@ def _peaks():
 # measured 1.19 TFLOP/s on this machine's GB300.
 FP64_SMS, FP64_FMA_PER_CLK, SM_MAX_GHZ = 152, 2, 2.07
 FP64_PEAK_TFLOPS = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
+FP64_PROBE_TFLOPS = 1.19
 
 
-# DRAM bytes (read + write) of one FP64 k = 32 product on this workload, from
-# one ncu capture of its two launches (row heights 9 and 13); see
-# profiles/fma_product_f64_zincblende50k.md. Algorithmic bytes are 1.62 GB.
-TRAFFIC_F64_K32 = 806001408 + 54032384 + 1060621568 + 76182784
+# DRAM bytes (read + write) of one FP64 k = 32 product on the 50k-atom workload
+# (one persistent launch): the median over its 11 launches in one ncu launch
+# list with dram__bytes_read.sum / dram__bytes_write.sum (see
+# profiles/fma_persistent_f64_zincblende50k.md). Algorithmic bytes are 1.62 GB;
+# the excess is X (141 MB at k = 32, above what L2 keeps beside the value
+# stream) fetched about 3.7 times.
+TRAFFIC_F64_K32 = 1906235904 + 131890432
 
 
 def _workload(n_atoms=N_ATOMS):
@@ -448,8 +452,10 @@ def run_ours(args):
     by_dom = _alg_bytes(pat, kdom)
     roofline = {"bound": "alu", "achieved": fl_dom / t_dom / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": fl_dom / t_dom / 1e12 / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_F64_K32 if kdom == 32 else None, "algorithmic_bytes": by_dom,
-                "kernel": f"fma_product_kernel<B, false, double, double, double>, k = {kdom}",
+                "traffic": TRAFFIC_F64_K32 if (kdom == 32 and pat.n_brows == 49955) else None,
+                "algorithmic_bytes": by_dom,
+                "kernel": f"fma_persistent_kernel<false, double, double, double, double>, k = {kdom}",
+                "frac_of_dfma_probe": fl_dom / t_dom / 1e12 / FP64_PROBE_TFLOPS,
                 "peak_source": "unit counts x clock (152 SM x 2 FP64 FMA/clk x 2.07 GHz)",
                 "hbm_gbs": by_dom / t_dom / 1e9, "hbm_frac": by_dom / t_dom / 1e9 / hbm_peak,
                 "hbm_peak": hbm_peak, "hbm_peak_source": peak_src}
@@ -535,7 +541,7 @@ def run_ours(args):
             "config": {"workload": f"zincblende_nanoparticle_{pat.n_brows}_atoms", "atoms": pat.n_brows,
                        "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk, "ks": list(KS),
                        "alpha": 1.0, "beta": 0.0, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: inputs larger than L2 (1.33 GB of values per product)"},
+                       "l2": f"no flush: inputs larger than L2 ({8 * pat.nnz / 1e9:.2f} GB of values per product)"},
             "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
             **({"domains": domains} if domains is not None else {}),
             **({"kspace": kspace} if kspace is not None else {}),
