@@ -95,12 +95,14 @@ def test_thin_products_cuda_core_form_matches_tensor_core_form(mode):
         assert rel_fro(Y2, ref[:, :2]) <= TOL_MIXED
 
 
+@pytest.mark.parametrize("k", [8, 16, 33])
 @pytest.mark.parametrize("mode", ["native", "tf32x3", "bf16x2"])
-def test_fp32_operator_modes(mode):
+def test_fp32_operator_modes(mode, k):
+    """FP32 operators in every mode, one to three column tiles (k = 8, 16, 33)."""
     pat = syn.random_pattern(30, 30, (4, 9, 13), 0.2, 9)
     vals = syn.random_values(pat, 9).astype(np.float32)
     H = _handle(pat, vals, torch.float32)
-    X = np.random.default_rng(2).standard_normal((pat.n_cols, 8)).astype(np.float32)
+    X = np.random.default_rng(2).standard_normal((pat.n_cols, k)).astype(np.float32)
     got = H.spmm(_dev(X, torch.float32), precision=mode).cpu().numpy().astype(np.float64)
     ref, scale = forward_ref(pat, vals.astype(np.float64), X.astype(np.float64), 1.0, 0.0, None)
     assert rel_fro(got, ref) <= TOL_MIXED
