@@ -266,7 +266,9 @@ int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop, int64_t ld
  * already shifted and scaled to H~ with spectrum inside [-1, 1]:
  *   t_0 = R,  t_1 = H~ R,  t_{n+1} = 2 H~ t_n - t_{n-1},
  *   moments[n] = sum(R .* t_n) / (n_rows * k),   n = 0 .. n_moments - 1.
- * The recurrence and the moments are FP64 (matrix dtype F64 required); the
+ * The recurrence and the moments are FP64 (matrix dtype F64, or C128 for a
+ * complex Hermitian operator: R, work and the checkpoints are then complex,
+ * the moment is Re sum(conj(R) .* t_n) / (n_rows * k), NATIVE precision); the
  * block products use `precision`.
  *  R        device [n_rows, k], ldr >= k (square operator: n_rows == n_cols)
  *  moments  device, n_moments doubles
@@ -313,7 +315,8 @@ int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ld
  *   mu_0 = <R, R> / (N k),  mu_1 = <t_1, R> / (N k),
  *   mu_{2n} = 2 <t_n, t_n> / (N k) - mu_0,  mu_{2n+1} = 2 <t_{n+1}, t_n> / (N k) - mu_1,
  * from T_{2n} = 2 T_n^2 - T_0 and T_{2n+1} = 2 T_{n+1} T_n - T_1 (these need
- * H~ = H~^T; for a non-symmetric operator use vbcsr_chebyshev). Arguments as
+ * H~ = H~^T, or H~ = H~^dagger for a C128 operator; for a non-symmetric operator
+ * use vbcsr_chebyshev). Arguments as
  * vbcsr_chebyshev: R device [n_rows, k] (ldr), moments device [M], work device
  * 2 * n_rows * k doubles; recurrence and moments FP64, products in `precision`.
  */
@@ -337,7 +340,8 @@ int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kernel, const do
  * that its spectrum lies in [-1, 1]): Gershgorin discs over scalar rows,
  *   bounds[0] = min_r (H_rr - sum_{c != r} |H_rc|),
  *   bounds[1] = max_r (H_rr + sum_{c != r} |H_rc|),
- * written to the device array `bounds` (2 doubles). Square FP64 operator.
+ * written to the device array `bounds` (2 doubles). Square FP64 operator, or
+ * C128 for a complex Hermitian one (H_rr its real part, |H_rc| the modulus).
  */
 int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream);
 
@@ -345,8 +349,9 @@ int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream);
  * Replaces the stored values by those of H~ = (H - c I) / d (c subtracted on
  * the scalar diagonal, every entry divided by d), in place, for the Chebyshev
  * recurrence; with c = (E+ + E-)/2 and d slightly above (E+ - E-)/2 from
- * vbcsr_gershgorin the spectrum of H~ lies inside [-1, 1]. Square FP64
- * operator; d must be nonzero and finite.
+ * vbcsr_gershgorin the spectrum of H~ lies inside [-1, 1]. Square FP64 or
+ * C128 operator (c comes off the real part of the diagonal); d must be
+ * nonzero and finite.
  */
 int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream);
 

@@ -471,3 +471,50 @@ def spmm_adjoint_complex(pat, values, X, alpha=1.0, beta=0.0, Y=None) -> np.ndar
     """Y = alpha H^dagger X + beta Y: Y_j += H_ij^dagger X_i (Eq. 1), the
     dagger a conjugate transpose."""
     return _block_loop(pat, values, X, alpha, beta, Y, adjoint=True)
+
+
+def gershgorin_bounds_complex(pat, values):
+    """(E_min, E_max) of a complex Hermitian operator from Gershgorin discs
+    over scalar rows: [min_p (Re H_pp - R_p), max_p (Re H_pp + R_p)], R_p the
+    sum of the moduli |H_pq| over q != p."""
+    rb = np.asarray(pat.row_bsize, np.int64)
+    cb = np.asarray(pat.col_bsize, np.int64)
+    r = np.concatenate([[0], np.cumsum(rb)])
+    c = np.concatenate([[0], np.cumsum(cb)])
+    diag = np.zeros(r[-1])
+    off = np.zeros(r[-1])
+    o = 0
+    for i in range(len(rb)):
+        for b in range(pat.block_row_ptr[i], pat.block_row_ptr[i + 1]):
+            j = int(pat.block_col_idx[b])
+            blk = np.asarray(values[o:o + rb[i] * cb[j]], np.complex128).reshape(rb[i], cb[j])
+            o += rb[i] * cb[j]
+            for p in range(rb[i]):
+                for q in range(cb[j]):
+                    if r[i] + p == c[j] + q:
+                        diag[r[i] + p] += blk[p, q].real
+                    else:
+                        off[r[i] + p] += abs(blk[p, q])
+    return float(np.min(diag - off)), float(np.max(diag + off))
+
+
+def shift_scale_values_complex(pat, values, c, d) -> np.ndarray:
+    """Packed values of H~ = (H - c I) / d for a complex operator: c subtracted
+    from the scalar diagonal, every entry divided by d."""
+    out = np.array(values, dtype=np.complex128, copy=True)
+    re = shift_scale_values(pat, out.real.copy(), c, d)
+    return re + 1j * (out.imag / d)
+
+
+def chebyshev_moments_complex(pat, values_t, R, n_moments) -> np.ndarray:
+    """mu_n = Re <R, t_n> / (N * n_vec), t_0 = R, t_1 = H~ R,
+    t_{n+1} = 2 H~ t_n - t_{n-1}, for a complex (Hermitian) H~ and complex R."""
+    R = np.asarray(R, dtype=np.complex128)
+    mu = [float(np.vdot(R, R).real)]
+    if n_moments > 1:
+        prev, cur = R, spmm_complex(pat, values_t, R)
+        mu.append(float(np.vdot(R, cur).real))
+        for n in range(1, n_moments - 1):
+            prev, cur = cur, spmm_complex(pat, values_t, cur, 2.0, -1.0, prev)
+            mu.append(float(np.vdot(R, cur).real))
+    return np.array(mu) / R.size

@@ -1092,18 +1092,23 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
                                double *moments, double *work, double *ckpt, int64_t ckpt_every, int precision,
                                void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
+    if (A->dtype != VBCSR_F64 && A->dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 or complex operator");
     if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
     if (k < 1 || n_moments < 1) return fail(VBCSR_ERR_INVALID_ARG, "k and n_moments must be >= 1");
     if (!R || !moments || !work || ldr < k) return fail(VBCSR_ERR_INVALID_ARG, "R / moments / work / ldr");
     if (ckpt && ckpt_every < 1) return fail(VBCSR_ERR_INVALID_ARG, "ckpt_every must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = A->n_rows, panel = N * k;
+    // complex panels are handled by the real copy and dot kernels as cw = 2 real
+    // columns per complex one (the dot of interleaved pairs is Re sum(conj(R) t))
+    const int64_t cw = A->dtype == VBCSR_C128 ? 2 : 1;
+    const int64_t N = A->n_rows, panel = N * k * cw;
     const double scale = 1.0 / ((double)N * (double)k);
     double *buf[2] = {work, work + panel};
 
     int64_t used = 0;
-    CUDA_TRY(launch_dot_panels(true, N, k, R, ldr, R, ldr, A->partials, kPartialsCap, &used, s), "dot");
+    CUDA_TRY(launch_dot_panels(true, N, k * cw, R, ldr * cw, R, ldr * cw, A->partials, kPartialsCap, &used, s),
+             "dot");
     CUDA_TRY(launch_finalize_dot(A->partials, used, scale, moments, s), "dot");
     if (n_moments == 1) return VBCSR_OK;
 
@@ -1118,13 +1123,13 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     auto store_pair = [&](int64_t m, const double *tm, int64_t ldm, const double *tm1) -> int {
         if (!ckpt || m % ckpt_every) return VBCSR_OK;
         double *slot = ckpt + (m / ckpt_every) * 2 * panel;
-        CUDA_TRY(launch_copy_panel(N, k, tm, ldm, slot, k, s), "checkpoint");
-        CUDA_TRY(launch_copy_panel(N, k, tm1, k, slot + panel, k, s), "checkpoint");
+        CUDA_TRY(launch_copy_panel(N, k * cw, tm, ldm * cw, slot, k * cw, s), "checkpoint");
+        CUDA_TRY(launch_copy_panel(N, k * cw, tm1, k * cw, slot + panel, k * cw, s), "checkpoint");
         return VBCSR_OK;
     };
     if ((rc = store_pair(0, R, ldr, buf[1]))) return rc;
     if (n_moments == 2) return VBCSR_OK;
-    CUDA_TRY(launch_copy_panel(N, k, R, ldr, buf[0], k, s), "copy R");
+    CUDA_TRY(launch_copy_panel(N, k * cw, R, ldr * cw, buf[0], k * cw, s), "copy R");
     // t_{n+1} = 2 H~ t_n - t_{n-1}: t_n in buf[n & 1], t_{n-1} (overwritten by t_{n+1}) in buf[(n+1) & 1]
     for (int64_t n = 1; n + 1 < n_moments; ++n) {
         double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
@@ -1215,17 +1220,20 @@ extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, 
 extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t M, double *moments,
                                  double *work, int precision, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
+    if (A->dtype != VBCSR_F64 && A->dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 or complex operator");
     if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
     if (k < 1 || M < 1) return fail(VBCSR_ERR_INVALID_ARG, "k and n_moments must be >= 1");
     if (!R || !moments || !work || ldr < k) return fail(VBCSR_ERR_INVALID_ARG, "R / moments / work / ldr");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = A->n_rows, panel = N * k;
+    const int64_t cw = A->dtype == VBCSR_C128 ? 2 : 1;   // real columns per (complex) column
+    const int64_t N = A->n_rows, panel = N * k * cw;
     const double scale = 1.0 / ((double)N * (double)k);
     double *buf[2] = {work, work + panel};
     int64_t used = 0;
     auto self_dot = [&](const double *t, int64_t ld, double *out) -> int {
-        CUDA_TRY(launch_dot_panels(true, N, k, t, ld, t, ld, A->partials, kPartialsCap, &used, s), "dot");
+        CUDA_TRY(launch_dot_panels(true, N, k * cw, t, ld * cw, t, ld * cw, A->partials, kPartialsCap, &used, s),
+                 "dot");
         CUDA_TRY(launch_finalize_dot(A->partials, used, scale, out, s), "dot");
         return VBCSR_OK;
     };
@@ -1237,7 +1245,7 @@ extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t
     epi.ldr = ldr;
     epi.dot_out = moments + 1;                                             // mu_1 = <t_1, t_0>
     if ((rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale))) return rc;
-    CUDA_TRY(launch_copy_panel(N, k, R, ldr, buf[0], k, s), "copy R");
+    CUDA_TRY(launch_copy_panel(N, k * cw, R, ldr * cw, buf[0], k * cw, s), "copy R");
     // t_n in buf[n & 1]; raw dots <t_n, t_n> -> moments[2n], <t_{n+1}, t_n> -> moments[2n+1]
     for (int64_t n = 1;; ++n) {
         double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
@@ -1266,10 +1274,11 @@ extern "C" int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kerne
 
 extern "C" int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream) {
     if (!A || !bounds) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
-    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "Gershgorin bounds need an FP64 operator");
+    if (A->dtype != VBCSR_F64 && A->dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_UNSUPPORTED, "Gershgorin bounds need an FP64 or complex operator");
     if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
     if (A->n_rows == 0) return fail(VBCSR_ERR_INVALID_ARG, "empty operator");
-    CUDA_TRY(launch_gershgorin(A->fwd_items, A->n_fwd_items, (const double *)A->panel, A->fl_xrow, A->fl_pcol,
+    CUDA_TRY(launch_gershgorin(A->dtype == VBCSR_C128, A->fwd_items, A->n_fwd_items, A->panel, A->fl_xrow, A->fl_pcol,
                                A->fl_w, A->partials, kPartialsCap, bounds, (cudaStream_t)stream),
              "gershgorin");
     return VBCSR_OK;
@@ -1277,11 +1286,13 @@ extern "C" int vbcsr_gershgorin(vbcsr_t *A, double *bounds, void *stream) {
 
 extern "C" int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
-    if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "shift/scale needs an FP64 operator");
+    if (A->dtype != VBCSR_F64 && A->dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_UNSUPPORTED, "shift/scale needs an FP64 or complex operator");
     if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
     if (!(d != 0.0) || d != d || c != c) return fail(VBCSR_ERR_INVALID_ARG, "c = %g, d = %g", c, d);
     cudaStream_t s = (cudaStream_t)stream;
-    CUDA_TRY(launch_shift_scale(A->fwd_items, A->n_fwd_items, (double *)A->panel, A->fl_xrow, A->fl_pcol, A->fl_w, c,
+    CUDA_TRY(launch_shift_scale(A->dtype == VBCSR_C128, A->fwd_items, A->n_fwd_items, A->panel, A->fl_xrow,
+                                A->fl_pcol, A->fl_w, c,
                                 d, s),
              "shift_scale");
     if (A->panel32) {

@@ -194,11 +194,12 @@ cudaError_t launch_dot_panels(bool f64, int64_t rows, int64_t k, const void *A, 
 cudaError_t launch_axpby(int64_t rows, int64_t k, double alpha, const double *X, int64_t ldx, double beta,
                          double *Y, int64_t ldy, cudaStream_t s);
 // Gershgorin bounds over the forward items: out[0] = min, out[1] = max (device)
-cudaError_t launch_gershgorin(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
-                              const int32_t *pcol, const int32_t *wd, double *partials, int64_t cap, double *out,
-                              cudaStream_t s);
+// real (FP64) or complex Hermitian (cplx) operators
+cudaError_t launch_gershgorin(bool cplx, const WorkItem *items, int64_t n_items, const void *panel,
+                              const int32_t *xrow, const int32_t *pcol, const int32_t *wd, double *partials,
+                              int64_t cap, double *out, cudaStream_t s);
 // panel <- (panel - c I) / d in place
-cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+cudaError_t launch_shift_scale(bool cplx, const WorkItem *items, int64_t n_items, void *panel, const int32_t *xrow,
                                const int32_t *pcol, const int32_t *wd, double c, double d, cudaStream_t s);
 // kernel polynomial method
 cudaError_t launch_kpm_fixup(double *mu, int64_t M, cudaStream_t s);

@@ -349,7 +349,18 @@ __device__ __forceinline__ void stage_x_rows(const WorkItem &w, const int32_t *x
     __syncwarp();
 }
 
-__global__ void gershgorin_kernel(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
+// real and complex (Hermitian) operators: the diagonal's real part, entry moduli
+__device__ __forceinline__ double re_part(double v) { return v; }
+__device__ __forceinline__ double re_part(double2 v) { return v.x; }
+__device__ __forceinline__ double modulus(double v) { return fabs(v); }
+__device__ __forceinline__ double modulus(double2 v) { return hypot(v.x, v.y); }
+__device__ __forceinline__ double shifted(double v, bool diag, double c, double d) { return (diag ? v - c : v) / d; }
+__device__ __forceinline__ double2 shifted(double2 v, bool diag, double c, double d) {
+    return make_double2((diag ? v.x - c : v.x) / d, v.y / d);
+}
+
+template <typename T>
+__global__ void gershgorin_kernel(const WorkItem *items, int64_t n_items, const T *panel, const int32_t *xrow,
                                   const int32_t *pcol, const int32_t *wd, double *partials, int warps) {
     extern __shared__ int32_t s_mem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -363,9 +374,9 @@ __global__ void gershgorin_kernel(const WorkItem *items, int64_t n_items, const 
                 const int tn = min(kKMax, w.K - t0);
                 if (p == 0 || w.K > kKMax) stage_x_rows(w, xrow, pcol, wd, t0, tn, s_x, lane);
                 for (int t = lane; t < tn; t += 32) {
-                    const double v = panel[w.vbase + (int64_t)p * w.Kp + t0 + t];
-                    if (s_x[t] == w.yrow + p) dg += v;
-                    else off += fabs(v);
+                    const T v = panel[w.vbase + (int64_t)p * w.Kp + t0 + t];
+                    if (s_x[t] == w.yrow + p) dg += re_part(v);
+                    else off += modulus(v);
                 }
             }
             for (int m = 16; m > 0; m >>= 1) {
@@ -402,20 +413,26 @@ __global__ void minmax_finalize_kernel(const double *partials, int n, double *ou
     out[1] = hi;
 }
 
-cudaError_t launch_gershgorin(const WorkItem *items, int64_t n_items, const double *panel, const int32_t *xrow,
-                              const int32_t *pcol, const int32_t *wd, double *partials, int64_t cap, double *out,
-                              cudaStream_t s) {
+cudaError_t launch_gershgorin(bool cplx, const WorkItem *items, int64_t n_items, const void *panel,
+                              const int32_t *xrow, const int32_t *pcol, const int32_t *wd, double *partials,
+                              int64_t cap, double *out, cudaStream_t s) {
     const int warps = 4;
     int64_t need = (n_items + warps - 1) / warps;
     int grid = (int)(need < cap / 2 ? (need > 0 ? need : 1) : cap / 2);
     if (grid > 2048) grid = 2048;
-    gershgorin_kernel<<<grid, warps * 32, warps * kKMax * sizeof(int32_t), s>>>(items, n_items, panel, xrow, pcol,
-                                                                              wd, partials, warps);
+    const size_t smem = warps * kKMax * sizeof(int32_t);
+    if (cplx)
+        gershgorin_kernel<double2><<<grid, warps * 32, smem, s>>>(items, n_items, (const double2 *)panel, xrow,
+                                                                  pcol, wd, partials, warps);
+    else
+        gershgorin_kernel<double><<<grid, warps * 32, smem, s>>>(items, n_items, (const double *)panel, xrow,
+                                                                 pcol, wd, partials, warps);
     minmax_finalize_kernel<<<1, 1, 0, s>>>(partials, grid, out);
     return cudaGetLastError();
 }
 
-__global__ void shift_scale_kernel(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+template <typename T>
+__global__ void shift_scale_kernel(const WorkItem *items, int64_t n_items, T *panel, const int32_t *xrow,
                                    const int32_t *pcol, const int32_t *wd, double c, double d, int warps) {
     extern __shared__ int32_t s_mem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -427,23 +444,26 @@ __global__ void shift_scale_kernel(const WorkItem *items, int64_t n_items, doubl
             stage_x_rows(w, xrow, pcol, wd, t0, tn, s_x, lane);
             for (int p = 0; p < w.B; ++p)
                 for (int t = lane; t < tn; t += 32) {
-                    double *v = panel + w.vbase + (int64_t)p * w.Kp + t0 + t;
-                    double x = *v;
-                    if (s_x[t] == w.yrow + p) x -= c;
-                    *v = x / d;
+                    T *v = panel + w.vbase + (int64_t)p * w.Kp + t0 + t;
+                    *v = shifted(*v, s_x[t] == w.yrow + p, c, d);
                 }
         }
     }
 }
 
-cudaError_t launch_shift_scale(const WorkItem *items, int64_t n_items, double *panel, const int32_t *xrow,
+cudaError_t launch_shift_scale(bool cplx, const WorkItem *items, int64_t n_items, void *panel, const int32_t *xrow,
                                const int32_t *pcol, const int32_t *wd, double c, double d, cudaStream_t s) {
     const int warps = 4;
     int64_t need = (n_items + warps - 1) / warps;
     if (need == 0) return cudaSuccess;
     const int grid = (int)(need < 65536 ? need : 65536);
-    shift_scale_kernel<<<grid, warps * 32, warps * kKMax * sizeof(int32_t), s>>>(items, n_items, panel, xrow, pcol,
-                                                                               wd, c, d, warps);
+    const size_t smem = warps * kKMax * sizeof(int32_t);
+    if (cplx)
+        shift_scale_kernel<double2><<<grid, warps * 32, smem, s>>>(items, n_items, (double2 *)panel, xrow, pcol, wd,
+                                                                   c, d, warps);
+    else
+        shift_scale_kernel<double><<<grid, warps * 32, smem, s>>>(items, n_items, (double *)panel, xrow, pcol, wd, c,
+                                                                  d, warps);
     return cudaGetLastError();
 }
 

@@ -338,17 +338,18 @@ class VBCSR:
         return D
 
     def chebyshev(self, R, n_moments: int, ckpt_every: int = 0, precision="native"):
-        """Moments mu_n = <R, T_n(H) R> / (N k) of an operator already scaled to
-        [-1, 1]; returns (moments, checkpoints or None)."""
+        """Moments mu_n = Re <R, T_n(H) R> / (N k) of an operator already scaled
+        to [-1, 1] (R in the operator's dtype: complex for a complex Hermitian
+        operator); returns (moments, checkpoints or None)."""
         R, ldr = self._panel(R, self.shape[0], "R")
         k = R.shape[1]
         N = self.shape[0]
         mom = torch.empty(n_moments, dtype=torch.float64, device=self.device)
-        work = torch.empty(2 * N * k, dtype=torch.float64, device=self.device)
+        work = torch.empty(2 * N * k, dtype=self.dtype, device=self.device)
         ck = None
         if ckpt_every:
             npairs = max(0, -(-(n_moments - 1) // ckpt_every))
-            ck = torch.empty((npairs, 2, N, k), dtype=torch.float64, device=self.device)
+            ck = torch.empty((npairs, 2, N, k), dtype=self.dtype, device=self.device)
         check(lib().vbcsr_chebyshev(self._h, k, ctypes.c_void_p(R.data_ptr()), ldr, n_moments,
                                     ctypes.c_void_p(mom.data_ptr()), ctypes.c_void_p(work.data_ptr()),
                                     ctypes.c_void_p(ck.data_ptr() if ck is not None else None),
@@ -356,12 +357,13 @@ class VBCSR:
         return mom, ck
 
     def kpm_moments(self, R, n_moments: int, precision="native"):
-        """KPM moments of a symmetric operator scaled to [-1, 1], by the
-        doubling identities (about half the products of chebyshev())."""
+        """KPM moments of a symmetric (or complex Hermitian) operator scaled to
+        [-1, 1], by the doubling identities (about half the products of
+        chebyshev())."""
         R, ldr = self._panel(R, self.shape[0], "R")
         k = R.shape[1]
         mom = torch.empty(n_moments, dtype=torch.float64, device=self.device)
-        work = torch.empty(2 * self.shape[0] * k, dtype=torch.float64, device=self.device)
+        work = torch.empty(2 * self.shape[0] * k, dtype=self.dtype, device=self.device)
         check(lib().vbcsr_kpm_moments(self._h, k, ctypes.c_void_p(R.data_ptr()), ldr, n_moments,
                                       ctypes.c_void_p(mom.data_ptr()), ctypes.c_void_p(work.data_ptr()),
                                       _prec(precision), _stream(self.device)), "vbcsr_kpm_moments")

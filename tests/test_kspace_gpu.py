@@ -136,3 +136,28 @@ def test_complex_operator_rejects_what_it_does_not_support():
                               torch.float64, "cuda:0")
     with pytest.raises(VBCSRError, match="INVALID_ARG"):
         real.set_kpoint([0.0, 0.0, 0.0])
+
+
+def test_kpm_moments_of_a_kpoint():
+    """The kernel-polynomial pipeline at a reciprocal-space point: Gershgorin
+    bounds of the Hermitian O(k), the shift and scale, the Chebyshev moments
+    with random-phase vectors and the doubling moments, against the oracle."""
+    w = syn.zincblende_crystal(2)
+    kp = [0.21, -0.13, 0.34]
+    H = _kspace(w)
+    H.set_kpoint(kp)
+    pat, vals = _oracle_blocks(w, kp)
+    lo, hi = oracle.gershgorin_bounds_complex(pat, vals)
+    glo, ghi = H.gershgorin()
+    assert abs(glo - lo) <= 1e-12 * abs(lo) and abs(ghi - hi) <= 1e-12 * abs(hi)
+    c, d = 0.5 * (hi + lo), 1.01 * 0.5 * (hi - lo)
+    H.shift_scale(c, d)
+    vt = oracle.shift_scale_values_complex(pat, vals, c, d)
+    assert np.abs(H.get_values().cpu().numpy() - vt).max() <= 1e-14 * np.abs(vt).max()
+    rng = np.random.default_rng(11)
+    R = np.exp(2j * np.pi * rng.random((pat.n_rows, 4)))
+    ref = oracle.chebyshev_moments_complex(pat, vt, R, 24)
+    mom, _ = H.chebyshev(_dev(R), 24)
+    assert np.abs(mom.cpu().numpy() - ref).max() <= 1e-12
+    mom2 = H.kpm_moments(_dev(R), 24)
+    assert np.abs(mom2.cpu().numpy() - ref).max() <= 1e-12

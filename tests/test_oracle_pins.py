@@ -485,3 +485,40 @@ def test_complex_block_products_against_dense():
     lhs = np.vdot(Yv, oracle.spmm_complex(pat, vals, Xv))
     rhs = np.vdot(oracle.spmm_adjoint_complex(pat, vals, Yv), Xv)
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_complex_chebyshev_moments_and_gershgorin():
+    """For a Hermitian O(k): the Gershgorin interval holds the spectrum; the
+    scaled moments equal sum_i |<v_i, R>|^2 T_n(lambda_i) / (N k) from a dense
+    eigendecomposition (T_n(x) = cos(n arccos x)); at k = 0 with real vectors
+    they equal the real recurrence's moments."""
+    w = syn.zincblende_crystal(1)
+    args = (w.bsize, w.edge_i, w.edge_j, w.edge_R, w.edge_values)
+    rb, cb, ptr, cols, vals = oracle.kspace_blocks(*args, [0.21, -0.13, 0.34])
+    pat = BlockPattern(rb, cb, ptr, cols)
+    lo, hi = oracle.gershgorin_bounds_complex(pat, vals)
+    D = oracle.to_dense(pat, vals.real) + 1j * oracle.to_dense(pat, vals.imag)
+    ev = np.linalg.eigvalsh(D)
+    assert lo <= ev.min() and ev.max() <= hi
+    c, d = 0.5 * (hi + lo), 1.01 * 0.5 * (hi - lo)
+    vt = oracle.shift_scale_values_complex(pat, vals, c, d)
+    Dt = oracle.to_dense(pat, vt.real) + 1j * oracle.to_dense(pat, vt.imag)
+    assert np.allclose(Dt, (D - c * np.eye(len(D))) / d, atol=1e-15)
+    lam, V = np.linalg.eigh(Dt)
+    rng = np.random.default_rng(0)
+    R = np.exp(2j * np.pi * rng.random((len(D), 3)))          # random phases
+    mu = oracle.chebyshev_moments_complex(pat, vt, R, 12)
+    w2 = np.abs(V.conj().T @ R) ** 2                           # |<v_i, R_c>|^2
+    th = np.arccos(np.clip(lam, -1, 1))
+    ref = np.array([np.sum(w2 * np.cos(n * th)[:, None]) for n in range(12)]) / R.size
+    assert np.allclose(mu, ref, atol=1e-12)
+    # k = 0 sums real images: the complex recurrence with real vectors is the real one
+    rb0, cb0, ptr0, cols0, v0 = oracle.kspace_blocks(*args, [0.0, 0.0, 0.0])
+    p0 = BlockPattern(rb0, cb0, ptr0, cols0)
+    assert np.abs(v0.imag).max() == 0.0
+    assert np.allclose(oracle.gershgorin_bounds_complex(p0, v0), oracle.gershgorin_bounds(p0, v0.real), atol=1e-12)
+    Rr = rng.choice([-1.0, 1.0], size=(len(D), 2))
+    c0, d0 = oracle.cheb_scale(p0, v0.real)
+    vt0 = oracle.shift_scale_values(p0, v0.real, c0, d0)
+    assert np.allclose(oracle.chebyshev_moments_complex(p0, vt0.astype(np.complex128), Rr, 10),
+                       oracle.chebyshev_moments(p0, vt0, Rr, 10), atol=1e-13)
