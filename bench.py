@@ -346,6 +346,55 @@ def kspace_section(dev, steps, n_cells):
     return res
 
 
+def spgemm_section(dev):
+    """The thresholded block product C = H H (Eqs. 2-3) of two operators: the
+    5k-atom zinc-blende nanoparticle and the variable-block domain at 1/8 of
+    its benchmark size, at eps = 0 and at a threshold that drops blocks.
+    Wall time of the whole call (host symbolic stage with the Eq. 3 bound,
+    GPU numeric stage, final filter and compaction, result handle), and the
+    rate of its numeric flops (2 b_i b_k b_j per retained block product)."""
+    import torch
+    import synthetic as syn
+    from paper_2609_04397_gb300 import VBCSR
+    out = {}
+    for name, w in (("zincblende_5k", syn.zincblende(5000)), ("vbcsr_domain_62MiB", syn.domain("vbcsr", 62.5 * 2 ** 20))):
+        pat = w.pattern
+        H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
+        rows = np.repeat(np.arange(pat.n_brows), np.diff(pat.block_row_ptr))
+        bi, bk = pat.row_bsize[rows].astype(np.float64), pat.col_bsize[pat.block_col_idx].astype(np.float64)
+        res = {"atoms": pat.n_brows, "blocks": pat.nblk, "nnz": pat.nnz}
+        # a threshold that keeps about half the blocks: the median block norm of C = H H
+        C0 = H.spgemm(H, 0.0)
+        crb, ccb, crp, cci = C0.pattern
+        crows = np.repeat(np.arange(len(crb)), np.diff(crp))
+        csz = crb[crows].astype(np.int64) * ccb[cci].astype(np.int64)
+        cv = C0.get_values().cpu().numpy()
+        cn = np.sqrt(np.add.reduceat(cv * cv, np.concatenate([[0], np.cumsum(csz)[:-1]])))
+        eps_half = float(np.median(cn))
+        del C0, cv
+        for eps in (0.0, eps_half):
+            C = H.spgemm(H, eps)              # warm-up (and the output size)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                C = H.spgemm(H, eps)
+            torch.cuda.synchronize(dev)
+            ms = (time.perf_counter() - t0) / reps * 1e3
+            # product flops: every (i, k) block of A meets every (k, j) block of B
+            # (eps drops candidates before the numeric stage only where the bound allows)
+            rowsum_bj = np.bincount(rows, weights=bk, minlength=pat.n_brows)   # sum_j b_j over row k of B
+            flops = 2.0 * float(np.sum(bi * bk * rowsum_bj[pat.block_col_idx]))
+            res["eps_0" if eps == 0.0 else "eps_median_norm"] = {
+                "eps": eps, "ms": ms, "out_blocks": int(C.info.nblk), "out_nnz": int(C.nnz),
+                "gflops_all_products": flops / ms / 1e6}
+            del C
+        out[name] = res
+        del H
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
     world, rank, _ = _dist()
@@ -558,6 +607,7 @@ def run_ours(args):
     batched = batched_section(dev, args.steps) if not args.no_batched else None
     domains = domains_section(dev, args.steps) if args.domains else None
     kspace = kspace_section(dev, args.steps, max(1, round((args.atoms / 8) ** (1 / 3)))) if args.kspace else None
+    spg = spgemm_section(dev) if args.spgemm else None
     H.check()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -569,6 +619,7 @@ def run_ours(args):
             "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
             **({"domains": domains} if domains is not None else {}),
             **({"kspace": kspace} if kspace is not None else {}),
+            **({"spgemm": spg} if spg is not None else {}),
             "gpu_launches": launches_per_product * len(KS) * args.steps, "clocks": clocks}
     if rank == 0:
         if not args.no_cpu_baseline:
@@ -588,6 +639,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--spgemm", action="store_true",
+                    help="also measure the thresholded block product C = H H")
     ap.add_argument("--kspace", action="store_true",
                     help="also measure a periodic crystal sampled in reciprocal space (complex products)")
     ap.add_argument("--atoms", type=int, default=N_ATOMS,

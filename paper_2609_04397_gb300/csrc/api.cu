@@ -5,10 +5,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -1353,70 +1355,115 @@ extern "C" int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcs
             if (B->nblk) CUDA_TRY(cudaMemcpyAsync(nB.data(), dB.p, B->nblk * 8, cudaMemcpyDeviceToHost, s), "copy");
             CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
         }
-        // symbolic stage: candidates, Eq. 3 bounds, product lists
+        // symbolic stage: candidates, Eq. 3 bounds, product lists. Block rows are
+        // independent: contiguous row ranges run on host threads with their own
+        // lists, concatenated in row order afterwards (the result does not depend
+        // on the thread count).
         const int64_t nbr = A->n_brows, nbc = B->n_bcols;
-        std::vector<int64_t> mark(nbc, -1);
-        std::vector<int64_t> touched;
-        std::vector<double> bound;
+        struct Part {
+            std::vector<int64_t> row_n;                   // output blocks of every row of the range
+            std::vector<int32_t> col, bi, bj;             // output blocks
+            std::vector<int64_t> nprod;                   // products of every output block
+            std::vector<int64_t> pa, pb;
+            std::vector<int32_t> kpa, kpb, bk;
+        };
+        struct Prod { int64_t o; int32_t k; int64_t a, b; };
+        auto symbolic = [&](int64_t r0, int64_t r1, Part &P) {
+            std::vector<int32_t> mark(nbc, -1);
+            std::vector<int32_t> touched, kept;
+            std::vector<double> bound;
+            std::vector<Prod> row_prods;
+            for (int64_t i = r0; i < r1; ++i) {
+                touched.clear();
+                bound.clear();
+                for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
+                    const int32_t k = A->h_pcol[a];
+                    for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
+                        const int32_t j = B->h_pcol[b];
+                        if (mark[j] < 0) {
+                            mark[j] = (int32_t)touched.size();
+                            touched.push_back(j);
+                            bound.push_back(0.0);
+                        }
+                        bound[mark[j]] += nA[a] * nB[b];
+                    }
+                }
+                kept.clear();
+                for (size_t t = 0; t < touched.size(); ++t)
+                    if (bound[t] >= eps) kept.push_back(touched[t]);
+                std::sort(kept.begin(), kept.end());
+                for (int32_t j : touched) mark[j] = -1;
+                for (size_t t = 0; t < kept.size(); ++t) mark[kept[t]] = (int32_t)t;
+                row_prods.clear();
+                for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
+                    const int32_t k = A->h_pcol[a];
+                    for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
+                        const int32_t o = mark[B->h_pcol[b]];
+                        if (o >= 0) row_prods.push_back({o, A->col_b[k], a, b});
+                    }
+                }
+                // products of one output block together, equal inner sizes b_k adjacent
+                std::stable_sort(row_prods.begin(), row_prods.end(), [](const Prod &x, const Prod &y) {
+                    return x.o != y.o ? x.o < y.o : x.k < y.k;
+                });
+                size_t u = 0;
+                for (size_t t = 0; t < kept.size(); ++t) {
+                    const int32_t j = kept[t];
+                    P.col.push_back(j);
+                    P.bi.push_back(A->row_b[i]);
+                    P.bj.push_back(B->col_b[j]);
+                    const size_t u0 = u;
+                    for (; u < row_prods.size() && row_prods[u].o == (int64_t)t; ++u) {
+                        P.pa.push_back(A->h_pbase[row_prods[u].a]);
+                        P.kpa.push_back(A->h_kp[row_prods[u].a]);
+                        P.pb.push_back(B->h_pbase[row_prods[u].b]);
+                        P.kpb.push_back(B->h_kp[row_prods[u].b]);
+                        P.bk.push_back(row_prods[u].k);
+                    }
+                    P.nprod.push_back((int64_t)(u - u0));
+                }
+                for (int32_t j : kept) mark[j] = -1;
+                P.row_n.push_back((int64_t)kept.size());
+            }
+        };
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int64_t nthr = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, nbr / 64 + 1}));
+        std::vector<Part> parts(nthr);
+        {
+            std::vector<std::thread> pool;
+            std::vector<std::exception_ptr> errs(nthr);
+            for (int64_t t = 0; t < nthr; ++t)
+                pool.emplace_back([&, t]() {
+                    try {
+                        symbolic(nbr * t / nthr, nbr * (t + 1) / nthr, parts[t]);
+                    } catch (...) {
+                        errs[t] = std::current_exception();
+                    }
+                });
+            for (auto &th : pool) th.join();
+            for (auto &e : errs)
+                if (e) std::rethrow_exception(e);
+        }
         std::vector<int64_t> out_ptr(1, 0), out_pbeg(1, 0), out_uoff(1, 0);
         std::vector<int32_t> out_col, out_bi, out_bj;
         std::vector<int64_t> pa, pb;
         std::vector<int32_t> kpa, kpb, bk;
-        struct Prod { int64_t o; int32_t k; int64_t a, b; };
-        std::vector<Prod> row_prods;
-        for (int64_t i = 0; i < nbr; ++i) {
-            touched.clear();
-            bound.clear();
-            for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
-                const int32_t k = A->h_pcol[a];
-                for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
-                    const int32_t j = B->h_pcol[b];
-                    if (mark[j] < 0) {
-                        mark[j] = (int64_t)touched.size();
-                        touched.push_back(j);
-                        bound.push_back(0.0);
-                    }
-                    bound[mark[j]] += nA[a] * nB[b];
-                }
+        for (const Part &P : parts) {
+            for (int64_t n : P.row_n) out_ptr.push_back(out_ptr.back() + n);
+            out_col.insert(out_col.end(), P.col.begin(), P.col.end());
+            out_bi.insert(out_bi.end(), P.bi.begin(), P.bi.end());
+            out_bj.insert(out_bj.end(), P.bj.begin(), P.bj.end());
+            for (size_t t = 0; t < P.col.size(); ++t) {
+                out_uoff.push_back(out_uoff.back() + (int64_t)P.bi[t] * P.bj[t]);
+                out_pbeg.push_back(out_pbeg.back() + P.nprod[t]);
             }
-            std::vector<int64_t> kept;
-            for (size_t t = 0; t < touched.size(); ++t)
-                if (bound[t] >= eps) kept.push_back(touched[t]);
-            std::sort(kept.begin(), kept.end());
-            for (int64_t j : touched) mark[j] = -1;
-            const int64_t obase = (int64_t)out_col.size();
-            for (size_t t = 0; t < kept.size(); ++t) mark[kept[t]] = obase + (int64_t)t;
-            row_prods.clear();
-            for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
-                const int32_t k = A->h_pcol[a];
-                for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
-                    const int64_t o = mark[B->h_pcol[b]];
-                    if (o >= 0) row_prods.push_back({o, A->col_b[k], a, b});
-                }
-            }
-            // products of one output block together, equal inner sizes b_k adjacent
-            std::stable_sort(row_prods.begin(), row_prods.end(), [](const Prod &x, const Prod &y) {
-                return x.o != y.o ? x.o < y.o : x.k < y.k;
-            });
-            size_t u = 0;
-            for (size_t t = 0; t < kept.size(); ++t) {
-                const int64_t o = obase + (int64_t)t, j = kept[t];
-                out_col.push_back((int32_t)j);
-                out_bi.push_back(A->row_b[i]);
-                out_bj.push_back(B->col_b[j]);
-                out_uoff.push_back(out_uoff.back() + (int64_t)A->row_b[i] * B->col_b[j]);
-                for (; u < row_prods.size() && row_prods[u].o == o; ++u) {
-                    pa.push_back(A->h_pbase[row_prods[u].a]);
-                    kpa.push_back(A->h_kp[row_prods[u].a]);
-                    pb.push_back(B->h_pbase[row_prods[u].b]);
-                    kpb.push_back(B->h_kp[row_prods[u].b]);
-                    bk.push_back(row_prods[u].k);
-                }
-                out_pbeg.push_back((int64_t)pa.size());
-            }
-            for (int64_t j : kept) mark[j] = -1;
-            out_ptr.push_back((int64_t)out_col.size());
+            pa.insert(pa.end(), P.pa.begin(), P.pa.end());
+            pb.insert(pb.end(), P.pb.begin(), P.pb.end());
+            kpa.insert(kpa.end(), P.kpa.begin(), P.kpa.end());
+            kpb.insert(kpb.end(), P.kpb.begin(), P.kpb.end());
+            bk.insert(bk.end(), P.bk.begin(), P.bk.end());
         }
+        parts.clear();
         // numeric stage
         const int64_t n_out = (int64_t)out_col.size(), n_val = out_uoff.back();
         const size_t es = A->esize;
