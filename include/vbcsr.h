@@ -243,7 +243,8 @@ int vbcsr_spmm_adjoint(vbcsr_t *A, int64_t k, double alpha, const void *X, int64
  *   Y = alpha * op(H) X + beta * Y + gamma * Z,   *dot_out = sum(R .* Y)
  * This is one step of the Chebyshev recurrence and of its reverse (adjoint)
  * recurrence in the kernel polynomial method of Sec. V. The dot product is
- * reduced in a fixed order (deterministic for a given launch configuration).
+ * reduced in a fixed order (per work item under the persistent schedule, per
+ * CTA otherwise), so repeated calls with the same tuning give the same bits.
  */
 int vbcsr_spmm_ex(vbcsr_t *A, int transpose, int64_t k, double alpha, const void *X,
                   int64_t ldx, double beta, void *Y, int64_t ldy,

@@ -136,6 +136,7 @@ struct vbcsr_matrix {
     int64_t *prow_ptr = nullptr, *d_row_off = nullptr;
     int32_t *d_row_b = nullptr;
     double *partials = nullptr;
+    double *item_partials = nullptr;   // one dot share per work item (persistent launches)
     int *err = nullptr;
     int64_t device_bytes = 0;
 
@@ -453,6 +454,8 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
         CUDA_TRY(upload(A, &A->tl_xrow, tl_xrow, s), "upload");
         CUDA_TRY(upload(A, &A->tl_vcol, tl_vcol, s), "upload");
     }
+    CUDA_TRY(A->alloc(&A->item_partials, (size_t)std::max(A->n_fwd_items, A->n_adj_items)),
+             "alloc per-item dot shares");
 
     A->h_rowptr = prow_ptr;
     A->h_ucol.assign(block_col_idx, block_col_idx + nblk);
@@ -941,6 +944,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
     int64_t used = 0;
+    bool per_item_dot = false;   // the persistent CUDA-core launch writes one dot share per item
     // one launch of `kern` over items[0..n) with `warps` warps per CTA
     auto launch = [&](int B, const WorkItem *items, int64_t n, int warps, const void *kern, size_t smem) -> int {
         a.items = items;
@@ -953,7 +957,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         const int64_t need = (n + warps - 1) / warps;
         a.grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
         a.partials = nullptr;
-        if (want_dot) {
+        a.item_partials = nullptr;
+        if (want_dot && per_item_dot) {
+            a.item_partials = A->item_partials;
+        } else if (want_dot) {
             if (used + a.grid > kPartialsCap) return fail(VBCSR_ERR_UNSUPPORTED, "too many CTAs for the dot");
             a.partials = A->partials + used;
             used += a.grid;
@@ -1020,6 +1027,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             a.kc_log2_by_b |= (uint64_t)l << (3 * B);
         }
         a.queue = A->queue;
+        per_item_dot = true;
         CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         const int warps = A->persist_warps ? A->persist_warps : 4;
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps,
@@ -1035,7 +1043,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         }
     }
     if (rc) return rc;
-    if (want_dot) CUDA_TRY(launch_finalize_dot(A->partials, used, dot_scale, epi->dot_out, s), "dot finalize");
+    if (want_dot)
+        CUDA_TRY(launch_finalize_dot(per_item_dot ? A->item_partials : A->partials, per_item_dot ? n_all : used,
+                                     dot_scale, epi->dot_out, s),
+                 "dot finalize");
     return VBCSR_OK;
 }
 

@@ -70,7 +70,7 @@ __device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_
     if (a.beta != 0.0) r += (TX)a.beta * *yp;
     if (a.gamma != 0.0) r += (TX)a.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
     *yp = r;
-    if (a.partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
+    if (a.partials || a.item_partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
 }
 
 // complex Y (interleaved re, im): real alpha, beta, gamma; the dot is the real
@@ -91,7 +91,7 @@ __device__ __forceinline__ void write_out<double2>(const ProdArgs &a, int64_t ro
         r.y += a.gamma * z.y;
     }
     *yp = r;
-    if (a.partials) {
+    if (a.partials || a.item_partials) {
         const double2 q = static_cast<const double2 *>(a.R)[row * a.ldr + c];
         dot += q.x * r.x + q.y * r.y;
     }
@@ -303,6 +303,13 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
             default: break;
         }
 #undef VBCSR_ITEM_CASE
+        if (a.item_partials) {
+            // the item's share of the fused dot, at the item's index: the sum over
+            // items then runs in a fixed order, whichever warp took which item
+            for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+            if (lane == 0) a.item_partials[it] = dot;
+            dot = 0.0;
+        }
         if (!a.queue) it += (int64_t)gridDim.x * warps;
     }
     if (a.partials) finish_dot(a, dot, warp, lane, warps);

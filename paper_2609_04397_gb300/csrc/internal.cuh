@@ -81,6 +81,8 @@ struct ProdArgs {
     const void *Z; int64_t ldz;
     const void *R; int64_t ldr;
     double *partials;       // per-CTA dot partials (NULL: no dot)
+    double *item_partials;  // persistent launch: each item's dot written at its index (fixed-order
+                            // reduction afterwards, whatever order the warps took the items in)
     int64_t x_rows;         // rows of X (bounds check)
     int *err;               // device error word
     int debug_checks;
