@@ -47,7 +47,7 @@ typedef enum {
                                      block in a row, block size < 1 or too large     */
     VBCSR_ERR_CUDA = -3,          /* a CUDA runtime call failed                       */
     VBCSR_ERR_NO_MEMORY = -4,     /* device or host allocation failed                 */
-    VBCSR_ERR_UNSUPPORTED = -5,   /* valid request outside what this build supports   */
+    VBCSR_ERR_UNSUPPORTED = -5,   /* valid request outside what the library supports */
     VBCSR_ERR_DEVICE_CHECK = -6,  /* a kernel's self-check recorded an error          */
     VBCSR_ERR_ALIAS = -7          /* output overlaps an input that it may not alias   */
 } vbcsr_status;
