@@ -993,6 +993,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         // tensor-core kernel: the row count is a runtime mask, one launch serves every item
         const bool staged = !trans && (A->schedule & VBCSR_SCHED_MMA_STAGED);
         a.mma_staged = staged ? 1 : 0;
+        if (!staged) {
+            // the plain kernel takes items in descending cost from the work counter
+            a.queue = A->queue;
+            per_item_dot = true;
+            CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
+        }
         const void *kern = mma_kernel_ptr(mma_mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));

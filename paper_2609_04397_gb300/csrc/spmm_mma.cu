@@ -129,7 +129,16 @@ __global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdA
     const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
 
-    for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
+    // items (in descending cost) come from the device counter a.queue when given,
+    // else round-robin
+    int64_t it = (int64_t)blockIdx.x * warps + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long q = 0;
+            if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+        }
+        if (it >= a.n_items) break;
         const WorkItem w = a.items[it];
         for (int64_t n0 = 0; n0 < a.k; n0 += 8 * NT) {
             float acc[NT][4];
@@ -265,11 +274,19 @@ __global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdA
                         if (a.beta != 0.0) v += beta * *yp;
                         if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                         *yp = v;
-                        if (a.partials) dot += (double)R[row * a.ldr + col] * (double)v;
+                        if (a.partials || a.item_partials) dot += (double)R[row * a.ldr + col] * (double)v;
                     }
                 }
             }
         }
+        if (a.item_partials) {
+            // the item's share of the fused dot at the item's index (summed in a fixed
+            // order afterwards, whichever warp took the item)
+            for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+            if (lane == 0) a.item_partials[it] = dot;
+            dot = 0.0;
+        }
+        if (!a.queue) it += (int64_t)gridDim.x * warps;
     }
 
     if (a.partials) {
