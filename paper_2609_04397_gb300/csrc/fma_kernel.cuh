@@ -189,6 +189,31 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                     }
                     continue;
                 }
+                if (!TRANS && sizeof(TV) == 8) {
+                    // 8-byte values (FP64, double-FP32 pairs): two consecutive panel columns
+                    // per lane and step, one 16-byte load per row (rows start 32-byte
+                    // aligned and Kp is a multiple of 4, so the pair never leaves the row):
+                    // twice the bytes per load instruction in flight
+                    for (int t = 2 * tg; t < tn; t += 2 * TG) {
+                        TA x[2];
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int xr = (t + j < tn) ? s_x[t + j] : -1;
+                            x[j] = (cv && xr >= 0) ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
+                        }
+                        const TV *v = vals + w.vbase + t0 + t;
+                        const int64_t kp = w.Kp;
+#pragma unroll
+                        for (int p = 0; p < B; ++p) {
+                            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(v + p * kp));
+                            TV v2[2];
+                            memcpy(v2, &q, sizeof(v2));
+                            acc[p] = fmat((TA)v2[0], x[0], acc[p]);
+                            acc[p] = fmat((TA)v2[1], x[1], acc[p]);
+                        }
+                    }
+                    continue;
+                }
                 for (int t = tg; t < tn; t += TG) {
                     const int xr = s_x[t];
                     if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
