@@ -190,14 +190,16 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                     continue;
                 }
                 if (!TRANS && sizeof(TV) == 8) {
-                    // 8-byte values (FP64, double-FP32 pairs): two consecutive panel columns
-                    // per lane and step, one 16-byte load per row (rows start 32-byte
-                    // aligned and Kp is a multiple of 4, so the pair never leaves the row):
-                    // twice the bytes per load instruction in flight
-                    for (int t = 2 * tg; t < tn; t += 2 * TG) {
-                        TA x[2];
+                    // 8-byte values (FP64, double-FP32 pairs): CPL consecutive panel columns
+                    // per lane and step (2 for FP64, 4 for the FP32-pipe double-FP32
+                    // arithmetic), 16-byte loads (rows start 32-byte aligned and Kp is a
+                    // multiple of 4, so the columns never leave the row): more bytes per
+                    // load instruction and more independent multiply-adds in flight
+                    constexpr int CPL = sizeof(TA) == 8 && alignof(TA) == 8 ? 2 : 4;
+                    for (int t = CPL * tg; t < tn; t += CPL * TG) {
+                        TA x[CPL];
 #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
+                        for (int j = 0; j < CPL; ++j) {
                             const int xr = (t + j < tn) ? s_x[t + j] : -1;
                             x[j] = (cv && xr >= 0) ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
                         }
@@ -205,11 +207,14 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                         const int64_t kp = w.Kp;
 #pragma unroll
                         for (int p = 0; p < B; ++p) {
-                            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(v + p * kp));
-                            TV v2[2];
-                            memcpy(v2, &q, sizeof(v2));
-                            acc[p] = fmat((TA)v2[0], x[0], acc[p]);
-                            acc[p] = fmat((TA)v2[1], x[1], acc[p]);
+#pragma unroll
+                            for (int h = 0; h < CPL; h += 2) {
+                                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(v + p * kp + h));
+                                TV v2[2];
+                                memcpy(v2, &q, sizeof(v2));
+                                acc[p] = fmat((TA)v2[0], x[h], acc[p]);
+                                acc[p] = fmat((TA)v2[1], x[h + 1], acc[p]);
+                            }
                         }
                     }
                     continue;
