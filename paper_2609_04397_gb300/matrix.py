@@ -25,6 +25,18 @@ def _np(a, dt):
     return np.ascontiguousarray(np.asarray(a), dtype=dt)
 
 
+def _cuda_device(device) -> torch.device:
+    """The CUDA device a new operator lives on, with its index made explicit
+    ("cuda" means the current device), so that tensors created on it compare
+    equal to it."""
+    dev = torch.device(device or "cuda")
+    if dev.type != "cuda":
+        raise ValueError(f"operators live on a CUDA device, not {dev}")
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    return dev
+
+
 def _prec(precision) -> int:
     if isinstance(precision, int):
         return precision
@@ -50,7 +62,7 @@ class VBCSR:
                     dtype: torch.dtype = torch.float64, device=None) -> "VBCSR":
         """Build from host pattern arrays and packed values (numpy array or
         torch tensor, host or device), blocks row-major in pattern order."""
-        device = torch.device(device or "cuda")
+        device = _cuda_device(device)
         dt = _CODE[dtype]
         rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
         rp, ci = _np(block_row_ptr, np.int64), _np(block_col_idx, np.int32)
@@ -73,7 +85,7 @@ class VBCSR:
                      block_row_ptr, local_block_col_idx, values, dtype=torch.float64, device=None) -> "VBCSR":
         """One operator over independent structures; column indices local to
         each structure (see vbcsr_create_batched)."""
-        device = torch.device(device or "cuda")
+        device = _cuda_device(device)
         dt = _CODE[dtype]
         so, co = _np(struct_brow_offsets, np.int64), _np(struct_bcol_offsets, np.int64)
         rb, cb = _np(row_bsize, np.int32), _np(col_bsize, np.int32)
@@ -98,7 +110,7 @@ class VBCSR:
         their real b_i x b_j blocks packed row-major in edge order (numpy);
         tau: fractional atom positions for the R+tau convention, or None.
         The result is complex128 and zero until set_kpoint."""
-        device = torch.device(device or "cuda")
+        device = _cuda_device(device)
         bs = _np(bsize, np.int32)
         ei, ej = _np(edge_i, np.int32), _np(edge_j, np.int32)
         eR = _np(edge_R, np.int32).reshape(-1, 3)
