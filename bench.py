@@ -50,11 +50,11 @@ FP64_PROBE_TFLOPS = 1.19
 
 # DRAM bytes (read + write) of one FP64 k = 32 product on the 50k-atom workload
 # (one persistent launch): the median over its 11 launches in one ncu launch
-# list with dram__bytes_read.sum / dram__bytes_write.sum (see
-# profiles/fma_persistent_f64_zincblende50k.md). Algorithmic bytes are 1.62 GB;
-# the excess is X (141 MB at k = 32, above what L2 keeps beside the value
-# stream) fetched about 3.7 times.
-TRAFFIC_F64_K32 = 1906235904 + 131890432
+# list with dram__bytes_read.sum / dram__bytes_write.sum (summary under
+# profiles/, FP64 product on the 50k-atom zinc-blende operator). Algorithmic
+# bytes are 1.62 GB; the excess is X (141 MB at k = 32, above what L2 keeps
+# beside the value stream) fetched about 4.4 times.
+TRAFFIC_F64_K32 = 2107894016
 
 
 def _workload(n_atoms=N_ATOMS):

@@ -294,26 +294,61 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
         }
     }
 
-    // shape-class registry (Sec. III.B): every distinct (b_i, b_j)
+    // shape-class registry (Sec. III.B): every distinct (b_i, b_j), in increasing
+    // (b_i, b_j) order. Block sizes are at most kMaxBlockSize, so the counts go
+    // to a dense table over the distinct row and column sizes (one pass over the
+    // blocks); an ordered map serves the rare pattern with very many sizes.
     {
-        std::map<std::pair<int32_t, int32_t>, int64_t> reg;
+        std::vector<int32_t> ridx(kMaxBlockSize + 1, -1), cidx(kMaxBlockSize + 1, -1);
+        std::vector<int32_t> rs, cs;
         for (int64_t i = 0; i < n_brows; ++i)
-            for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u)
-                reg[{row_bsize[i], col_bsize[block_col_idx[u]]}] += 1;
-        for (auto &kv : reg) {
-            A->cls_bi.push_back(kv.first.first);
-            A->cls_bj.push_back(kv.first.second);
-            A->cls_count.push_back(kv.second);
+            if (ridx[row_bsize[i]] < 0) { ridx[row_bsize[i]] = 0; rs.push_back(row_bsize[i]); }
+        for (int64_t j = 0; j < n_bcols; ++j)
+            if (cidx[col_bsize[j]] < 0) { cidx[col_bsize[j]] = 0; cs.push_back(col_bsize[j]); }
+        std::sort(rs.begin(), rs.end());
+        std::sort(cs.begin(), cs.end());
+        for (size_t t = 0; t < rs.size(); ++t) ridx[rs[t]] = (int32_t)t;
+        for (size_t t = 0; t < cs.size(); ++t) cidx[cs[t]] = (int32_t)t;
+        if (rs.size() * cs.size() <= ((size_t)1 << 20)) {
+            std::vector<int64_t> cnt(rs.size() * cs.size(), 0);
+            for (int64_t i = 0; i < n_brows; ++i) {
+                int64_t *row = cnt.data() + (size_t)ridx[row_bsize[i]] * cs.size();
+                for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u)
+                    row[cidx[col_bsize[block_col_idx[u]]]] += 1;
+            }
+            for (size_t r = 0; r < rs.size(); ++r)
+                for (size_t c = 0; c < cs.size(); ++c)
+                    if (cnt[r * cs.size() + c]) {
+                        A->cls_bi.push_back(rs[r]);
+                        A->cls_bj.push_back(cs[c]);
+                        A->cls_count.push_back(cnt[r * cs.size() + c]);
+                    }
+        } else {
+            std::map<std::pair<int32_t, int32_t>, int64_t> reg;
+            for (int64_t i = 0; i < n_brows; ++i)
+                for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u)
+                    reg[{row_bsize[i], col_bsize[block_col_idx[u]]}] += 1;
+            for (auto &kv : reg) {
+                A->cls_bi.push_back(kv.first.first);
+                A->cls_bj.push_back(kv.first.second);
+                A->cls_count.push_back(kv.second);
+            }
         }
     }
 
-    // plan order: blocks of every row sorted by column
+    // plan order: blocks of every row sorted by column (rows given sorted keep
+    // their order without a sort)
     std::vector<int32_t> perm(nblk);   // plan block -> user block
     for (int64_t i = 0; i < n_brows; ++i) {
         const int64_t b0 = block_row_ptr[i], b1 = block_row_ptr[i + 1];
-        for (int64_t u = b0; u < b1; ++u) perm[u] = (int32_t)u;
-        std::sort(perm.begin() + b0, perm.begin() + b1,
-                  [&](int32_t x, int32_t y) { return block_col_idx[x] < block_col_idx[y]; });
+        bool sorted = true;
+        for (int64_t u = b0; u < b1; ++u) {
+            perm[u] = (int32_t)u;
+            if (u > b0 && block_col_idx[u] < block_col_idx[u - 1]) sorted = false;
+        }
+        if (!sorted)
+            std::sort(perm.begin() + b0, perm.begin() + b1,
+                      [&](int32_t x, int32_t y) { return block_col_idx[x] < block_col_idx[y]; });
     }
 
     // panel widths; pages ordered by row height
@@ -798,7 +833,7 @@ namespace vbcsr {
 const void *fma_f64_kernel(bool trans, bool persistent, int B);
 const void *fma_f32_kernel(bool trans, bool persistent, int B);
 const void *fma_f32_on_f64_kernel(bool trans, bool persistent, int B);
-const void *fma_df_kernel(bool trans, bool persistent, int B);
+const void *fma_df_kernel(bool trans, bool persistent, int B, bool narrow);
 const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int64_t k);
 }  // namespace vbcsr
 
@@ -943,6 +978,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const int kc_auto = auto_kc(k);
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
+    // the double-FP32 persistent forward kernel in its narrow form when the
+    // operator has more than two row counts (the wide form's larger code then
+    // runs slower, see process_item)
+    const bool df_narrow = A->fwd_buckets.size() > 2;
     int64_t used = 0;
     bool per_item_dot = false;   // the persistent CUDA-core launch writes one dot share per item
     // one launch of `kern` over items[0..n) with `warps` warps per CTA
@@ -972,7 +1011,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         else if (mode == VBCSR_PREC_F32)
             e = launch_fma_f32_on_f64(B, trans, a, s);
         else if (mode == VBCSR_PREC_DF32)
-            e = launch_fma_df(B, trans, a, s);
+            e = launch_fma_df(B, trans, a, s, df_narrow);
         else if (split)
             e = launch_fma_split(mode, a, s);
         else
@@ -982,7 +1021,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     };
     auto fma_kern = [&](bool persistent, int B) {
         if (cplx) return fma_c128_kernel(trans, persistent, B);
-        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B);
+        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B, df_narrow);
         return (mode == VBCSR_PREC_NATIVE)
                    ? (f64 ? fma_f64_kernel(trans, persistent, B) : fma_f32_kernel(trans, persistent, B))
                    : fma_f32_on_f64_kernel(trans, persistent, B);
@@ -1358,145 +1397,141 @@ extern "C" int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcs
     cudaStream_t s = (cudaStream_t)stream;
     const bool f64 = A->dtype == VBCSR_F64;
     try {
-        // block norms of both operands
-        std::vector<double> nA(A->nblk), nB(B->nblk);
-        {
-            DevVec<double> dA, dB;
-            CUDA_TRY(dA.alloc(A->nblk), "alloc norms");
-            CUDA_TRY(dB.alloc(B->nblk), "alloc norms");
-            CUDA_TRY(launch_block_norms(f64, A->nblk, A->panel, A->fl_pbase, A->fl_kp, A->fl_bi, A->fl_w, dA.p, s),
-                     "block norms");
-            CUDA_TRY(launch_block_norms(f64, B->nblk, B->panel, B->fl_pbase, B->fl_kp, B->fl_bi, B->fl_w, dB.p, s),
-                     "block norms");
-            if (A->nblk) CUDA_TRY(cudaMemcpyAsync(nA.data(), dA.p, A->nblk * 8, cudaMemcpyDeviceToHost, s), "copy");
-            if (B->nblk) CUDA_TRY(cudaMemcpyAsync(nB.data(), dB.p, B->nblk * 8, cudaMemcpyDeviceToHost, s), "copy");
+        // block norms of both operands (plan order)
+        const int64_t nbr = A->n_brows, nbc = B->n_bcols;
+        DevVec<double> dA, dB;
+        CUDA_TRY(dA.alloc(A->nblk), "alloc norms");
+        CUDA_TRY(dB.alloc(B->nblk), "alloc norms");
+        CUDA_TRY(launch_block_norms(f64, A->nblk, A->panel, A->fl_pbase, A->fl_kp, A->fl_bi, A->fl_w, dA.p, s),
+                 "block norms");
+        CUDA_TRY(launch_block_norms(f64, B->nblk, B->panel, B->fl_pbase, B->fl_kp, B->fl_bi, B->fl_w, dB.p, s),
+                 "block norms");
+        // symbolic stage on the device: pass 1 counts every block row (rows whose
+        // candidates overflow the shared-memory table are counted again with a
+        // workspace in device memory), the host scans the counts into row
+        // offsets, pass 2 writes the kept pattern and the product lists
+        DevVec<int32_t> d_acol, d_bcol, d_bcs, d_ovf;
+        DevVec<int64_t> d_cnt;
+        CUDA_TRY(d_acol.put(A->h_pcol, s), "upload");
+        CUDA_TRY(d_bcol.put(B->h_pcol, s), "upload");
+        CUDA_TRY(d_bcs.put(B->col_b, s), "upload");
+        CUDA_TRY(d_ovf.alloc(nbr), "alloc");
+        CUDA_TRY(d_cnt.alloc(3 * (size_t)nbr), "alloc");
+        SymArgs y;
+        memset(&y, 0, sizeof(y));
+        y.n_rows = nbr;
+        y.a_rowptr = A->prow_ptr;
+        y.b_rowptr = B->prow_ptr;
+        y.a_col = d_acol.p;
+        y.b_col = d_bcol.p;
+        y.a_norm = dA.p;
+        y.b_norm = dB.p;
+        y.a_w = A->fl_w;
+        y.a_pbase = A->fl_pbase;
+        y.b_pbase = B->fl_pbase;
+        y.a_kp = A->fl_kp;
+        y.b_kp = B->fl_kp;
+        y.a_rowsize = A->d_row_b;
+        y.b_colsize = d_bcs.p;
+        y.eps = eps;
+        y.overflow = d_ovf.p;
+        y.cnt_out = d_cnt.p;
+        y.cnt_prod = d_cnt.p + nbr;
+        y.cnt_val = d_cnt.p + 2 * nbr;
+        CUDA_TRY(launch_spgemm_symbolic(1, y, s), "symbolic stage");
+        std::vector<int64_t> cnt(3 * (size_t)nbr);
+        std::vector<int32_t> ovf(nbr);
+        if (nbr) {
+            CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_cnt.p, cnt.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
+            CUDA_TRY(cudaMemcpyAsync(ovf.data(), d_ovf.p, ovf.size() * 4, cudaMemcpyDeviceToHost, s), "copy");
+        }
+        CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
+        // rows beyond the shared-memory table: a workspace sized by their product count
+        std::vector<int64_t> big, ws_off(1, 0);
+        std::vector<int32_t> ws_h, ws_cap;
+        for (int64_t i = 0; i < nbr; ++i) {
+            if (!ovf[i]) continue;
+            int64_t np = 0;
+            for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
+                const int32_t k = A->h_pcol[a];
+                np += B->h_rowptr[k + 1] - B->h_rowptr[k];
+            }
+            int64_t cap = 32;
+            while (cap < np) cap <<= 1;
+            if (cap > (1LL << 28)) return fail(VBCSR_ERR_UNSUPPORTED, "block row %lld: %lld candidate products",
+                                               (long long)i, (long long)np);
+            big.push_back(i);
+            ws_cap.push_back((int32_t)cap);
+            ws_h.push_back((int32_t)(2 * cap));
+            ws_off.push_back(ws_off.back() + (int64_t)sym_ws_bytes((int)(2 * cap), (int)cap));
+        }
+        DevVec<int64_t> d_big, d_wsoff;
+        DevVec<int32_t> d_wsh, d_wscap;
+        DevVec<unsigned char> d_ws;
+        SymArgs yb = y;
+        if (!big.empty()) {
+            CUDA_TRY(d_big.put(big, s), "upload");
+            CUDA_TRY(d_wsoff.put(ws_off, s), "upload");
+            CUDA_TRY(d_wsh.put(ws_h, s), "upload");
+            CUDA_TRY(d_wscap.put(ws_cap, s), "upload");
+            CUDA_TRY(d_ws.alloc((size_t)ws_off.back()), "alloc symbolic workspace");
+            yb.n_rows = (int64_t)big.size();
+            yb.rows = d_big.p;
+            yb.global_ws = 1;
+            yb.ws = d_ws.p;
+            yb.ws_off = d_wsoff.p;
+            yb.ws_h = d_wsh.p;
+            yb.ws_cap = d_wscap.p;
+            CUDA_TRY(launch_spgemm_symbolic(1, yb, s), "symbolic stage");
+            CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_cnt.p, cnt.size() * 8, cudaMemcpyDeviceToHost, s), "copy");
             CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
         }
-        // symbolic stage: candidates, Eq. 3 bounds, product lists. Block rows are
-        // independent: contiguous row ranges run on host threads with their own
-        // lists, concatenated in row order afterwards (the result does not depend
-        // on the thread count).
-        const int64_t nbr = A->n_brows, nbc = B->n_bcols;
-        struct Part {
-            std::vector<int64_t> row_n;                   // output blocks of every row of the range
-            std::vector<int32_t> col, bi, bj;             // output blocks
-            std::vector<int64_t> nprod;                   // products of every output block
-            std::vector<int64_t> pa, pb;
-            std::vector<int32_t> kpa, kpb, bk;
-        };
-        struct Prod { int64_t o; int32_t k; int64_t a, b; };
-        auto symbolic = [&](int64_t r0, int64_t r1, Part &P) {
-            std::vector<int32_t> mark(nbc, -1);
-            std::vector<int32_t> touched, kept;
-            std::vector<double> bound;
-            std::vector<Prod> row_prods;
-            for (int64_t i = r0; i < r1; ++i) {
-                touched.clear();
-                bound.clear();
-                for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
-                    const int32_t k = A->h_pcol[a];
-                    for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
-                        const int32_t j = B->h_pcol[b];
-                        if (mark[j] < 0) {
-                            mark[j] = (int32_t)touched.size();
-                            touched.push_back(j);
-                            bound.push_back(0.0);
-                        }
-                        bound[mark[j]] += nA[a] * nB[b];
-                    }
-                }
-                kept.clear();
-                for (size_t t = 0; t < touched.size(); ++t)
-                    if (bound[t] >= eps) kept.push_back(touched[t]);
-                std::sort(kept.begin(), kept.end());
-                for (int32_t j : touched) mark[j] = -1;
-                for (size_t t = 0; t < kept.size(); ++t) mark[kept[t]] = (int32_t)t;
-                row_prods.clear();
-                for (int64_t a = A->h_rowptr[i]; a < A->h_rowptr[i + 1]; ++a) {
-                    const int32_t k = A->h_pcol[a];
-                    for (int64_t b = B->h_rowptr[k]; b < B->h_rowptr[k + 1]; ++b) {
-                        const int32_t o = mark[B->h_pcol[b]];
-                        if (o >= 0) row_prods.push_back({o, A->col_b[k], a, b});
-                    }
-                }
-                // products of one output block together, equal inner sizes b_k adjacent
-                std::stable_sort(row_prods.begin(), row_prods.end(), [](const Prod &x, const Prod &y) {
-                    return x.o != y.o ? x.o < y.o : x.k < y.k;
-                });
-                size_t u = 0;
-                for (size_t t = 0; t < kept.size(); ++t) {
-                    const int32_t j = kept[t];
-                    P.col.push_back(j);
-                    P.bi.push_back(A->row_b[i]);
-                    P.bj.push_back(B->col_b[j]);
-                    const size_t u0 = u;
-                    for (; u < row_prods.size() && row_prods[u].o == (int64_t)t; ++u) {
-                        P.pa.push_back(A->h_pbase[row_prods[u].a]);
-                        P.kpa.push_back(A->h_kp[row_prods[u].a]);
-                        P.pb.push_back(B->h_pbase[row_prods[u].b]);
-                        P.kpb.push_back(B->h_kp[row_prods[u].b]);
-                        P.bk.push_back(row_prods[u].k);
-                    }
-                    P.nprod.push_back((int64_t)(u - u0));
-                }
-                for (int32_t j : kept) mark[j] = -1;
-                P.row_n.push_back((int64_t)kept.size());
-            }
-        };
-        const unsigned hw = std::thread::hardware_concurrency();
-        const int64_t nthr = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, nbr / 64 + 1}));
-        std::vector<Part> parts(nthr);
-        {
-            std::vector<std::thread> pool;
-            std::vector<std::exception_ptr> errs(nthr);
-            for (int64_t t = 0; t < nthr; ++t)
-                pool.emplace_back([&, t]() {
-                    try {
-                        symbolic(nbr * t / nthr, nbr * (t + 1) / nthr, parts[t]);
-                    } catch (...) {
-                        errs[t] = std::current_exception();
-                    }
-                });
-            for (auto &th : pool) th.join();
-            for (auto &e : errs)
-                if (e) std::rethrow_exception(e);
+        // row offsets of the kept blocks, their products and their values
+        std::vector<int64_t> out_ptr(nbr + 1, 0), off_prod(nbr + 1, 0), off_val(nbr + 1, 0);
+        for (int64_t i = 0; i < nbr; ++i) {
+            out_ptr[i + 1] = out_ptr[i] + cnt[i];
+            off_prod[i + 1] = off_prod[i] + cnt[nbr + i];
+            off_val[i + 1] = off_val[i] + cnt[2 * nbr + i];
         }
-        std::vector<int64_t> out_ptr(1, 0), out_pbeg(1, 0), out_uoff(1, 0);
-        std::vector<int32_t> out_col, out_bi, out_bj;
-        std::vector<int64_t> pa, pb;
-        std::vector<int32_t> kpa, kpb, bk;
-        for (const Part &P : parts) {
-            for (int64_t n : P.row_n) out_ptr.push_back(out_ptr.back() + n);
-            out_col.insert(out_col.end(), P.col.begin(), P.col.end());
-            out_bi.insert(out_bi.end(), P.bi.begin(), P.bi.end());
-            out_bj.insert(out_bj.end(), P.bj.begin(), P.bj.end());
-            for (size_t t = 0; t < P.col.size(); ++t) {
-                out_uoff.push_back(out_uoff.back() + (int64_t)P.bi[t] * P.bj[t]);
-                out_pbeg.push_back(out_pbeg.back() + P.nprod[t]);
-            }
-            pa.insert(pa.end(), P.pa.begin(), P.pa.end());
-            pb.insert(pb.end(), P.pb.begin(), P.pb.end());
-            kpa.insert(kpa.end(), P.kpa.begin(), P.kpa.end());
-            kpb.insert(kpb.end(), P.kpb.begin(), P.kpb.end());
-            bk.insert(bk.end(), P.bk.begin(), P.bk.end());
-        }
-        parts.clear();
-        // numeric stage
-        const int64_t n_out = (int64_t)out_col.size(), n_val = out_uoff.back();
+        const int64_t n_out = out_ptr[nbr], n_prod = off_prod[nbr], n_val = off_val[nbr];
         const size_t es = A->esize;
-        DevVec<int64_t> d_pbeg, d_uoff, d_pa, d_pb;
-        DevVec<int32_t> d_bi, d_bj, d_kpa, d_kpb, d_bk;
+        DevVec<int64_t> d_optr, d_oprod, d_oval, d_pbeg, d_uoff, d_pa, d_pb;
+        DevVec<int32_t> d_col, d_bi, d_bj, d_kpa, d_kpb, d_bk;
         DevVec<double> d_norm;
         DevVec<unsigned char> d_val;
-        CUDA_TRY(d_pbeg.put(out_pbeg, s), "upload");
-        CUDA_TRY(d_uoff.put(out_uoff, s), "upload");
-        CUDA_TRY(d_pa.put(pa, s), "upload");
-        CUDA_TRY(d_pb.put(pb, s), "upload");
-        CUDA_TRY(d_bi.put(out_bi, s), "upload");
-        CUDA_TRY(d_bj.put(out_bj, s), "upload");
-        CUDA_TRY(d_kpa.put(kpa, s), "upload");
-        CUDA_TRY(d_kpb.put(kpb, s), "upload");
-        CUDA_TRY(d_bk.put(bk, s), "upload");
+        CUDA_TRY(d_optr.put(out_ptr, s), "upload");
+        CUDA_TRY(d_oprod.put(off_prod, s), "upload");
+        CUDA_TRY(d_oval.put(off_val, s), "upload");
+        CUDA_TRY(d_pbeg.alloc(n_out + 1), "alloc");
+        CUDA_TRY(d_uoff.alloc(n_out), "alloc");
+        CUDA_TRY(d_col.alloc(n_out), "alloc");
+        CUDA_TRY(d_bi.alloc(n_out), "alloc");
+        CUDA_TRY(d_bj.alloc(n_out), "alloc");
+        CUDA_TRY(d_pa.alloc(n_prod), "alloc product lists");
+        CUDA_TRY(d_pb.alloc(n_prod), "alloc product lists");
+        CUDA_TRY(d_kpa.alloc(n_prod), "alloc product lists");
+        CUDA_TRY(d_kpb.alloc(n_prod), "alloc product lists");
+        CUDA_TRY(d_bk.alloc(n_prod), "alloc product lists");
+        CUDA_TRY(cudaMemcpyAsync(d_pbeg.p + n_out, &off_prod[nbr], 8, cudaMemcpyHostToDevice, s), "upload");
+        for (SymArgs *q : {&y, &yb}) {
+            q->off_out = d_optr.p;
+            q->off_prod = d_oprod.p;
+            q->off_val = d_oval.p;
+            q->out_col = d_col.p;
+            q->out_bi = d_bi.p;
+            q->out_bj = d_bj.p;
+            q->out_uoff = d_uoff.p;
+            q->out_pbeg = d_pbeg.p;
+            q->pa = d_pa.p;
+            q->pb = d_pb.p;
+            q->kpa = d_kpa.p;
+            q->kpb = d_kpb.p;
+            q->bk = d_bk.p;
+        }
+        CUDA_TRY(launch_spgemm_symbolic(2, y, s), "symbolic stage");
+        if (!big.empty()) CUDA_TRY(launch_spgemm_symbolic(2, yb, s), "symbolic stage");
+
+        // numeric stage
         CUDA_TRY(d_norm.alloc(n_out), "alloc norms");
         CUDA_TRY(d_val.alloc((size_t)n_val * es), "alloc product values");
         SpgemmArgs g;
@@ -1515,19 +1550,32 @@ extern "C" int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcs
         g.C = d_val.p;
         g.norms = d_norm.p;
         CUDA_TRY(launch_spgemm_numeric(f64, g, s), "numeric stage");
-        // final filter on the computed block norms
+        // final filter on the computed block norms (Eq. 2)
         std::vector<double> norms(n_out);
-        if (n_out) CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm.p, n_out * 8, cudaMemcpyDeviceToHost, s), "copy");
+        std::vector<int32_t> out_col(n_out);
+        if (n_out) {
+            CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm.p, n_out * 8, cudaMemcpyDeviceToHost, s), "copy");
+            CUDA_TRY(cudaMemcpyAsync(out_col.data(), d_col.p, n_out * 4, cudaMemcpyDeviceToHost, s), "copy");
+        }
         CUDA_TRY(cudaStreamSynchronize(s), "synchronize");
         std::vector<int64_t> c_ptr(1, 0), keep_src, dst_off(1, 0);
         std::vector<int32_t> c_col, keep_size;
+        c_ptr.reserve(nbr + 1);
+        c_col.reserve(n_out);
+        keep_src.reserve(n_out);
+        keep_size.reserve(n_out);
+        dst_off.reserve(n_out + 1);
         for (int64_t i = 0; i < nbr; ++i) {
+            int64_t u = off_val[i];   // the block's offset in the unfiltered values
             for (int64_t o = out_ptr[i]; o < out_ptr[i + 1]; ++o) {
-                if (norms[o] < eps) continue;
-                c_col.push_back(out_col[o]);
-                keep_src.push_back(out_uoff[o]);
-                keep_size.push_back(out_bi[o] * out_bj[o]);
-                dst_off.push_back(dst_off.back() + keep_size.back());
+                const int32_t size = A->row_b[i] * B->col_b[out_col[o]];
+                if (!(norms[o] < eps)) {
+                    c_col.push_back(out_col[o]);
+                    keep_src.push_back(u);
+                    keep_size.push_back(size);
+                    dst_off.push_back(dst_off.back() + size);
+                }
+                u += size;
             }
             c_ptr.push_back((int64_t)c_col.size());
         }

@@ -144,7 +144,7 @@ __device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
     return r;
 }
 
-template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI>
+template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true>
 __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &w, int KC, int32_t *s_x,
                                              int64_t *s_a, int lane, double &dot) {
     const int TG = 32 / KC;
@@ -191,11 +191,15 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                 }
                 if (!TRANS && sizeof(TV) == 8) {
                     // 8-byte values (FP64, double-FP32 pairs): CPL consecutive panel columns
-                    // per lane and step (2 for FP64, 4 for the FP32-pipe double-FP32
-                    // arithmetic), 16-byte loads (rows start 32-byte aligned and Kp is a
-                    // multiple of 4, so the columns never leave the row): more bytes per
-                    // load instruction and more independent multiply-adds in flight
-                    constexpr int CPL = sizeof(TA) == 8 && alignof(TA) == 8 ? 2 : 4;
+                    // per lane and step, 16-byte loads (rows start 32-byte aligned and Kp is
+                    // a multiple of 4, so the columns never leave the row): more bytes per
+                    // load instruction and more independent multiply-adds in flight. FP64
+                    // takes 2. The FP32-pipe double-FP32 arithmetic takes 4 for items of up
+                    // to 13 rows when WIDE, else 2: the wide form is twice the code per row
+                    // count, and a persistent launch that runs many row counts at once
+                    // (measured: nine on a variable-block operator with b in [9, 20]) ran
+                    // 1.4x slower with it, while one or two row counts ran 3-10 % faster.
+                    constexpr int CPL = sizeof(TA) == 8 && alignof(TA) == 8 ? 2 : (WIDE && B <= 13 ? 4 : 2);
                     for (int t = CPL * tg; t < tn; t += CPL * TG) {
                         TA x[CPL];
 #pragma unroll
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
 // order (the planner sorts them by descending cost); warps take the next
 // item from a device counter (a.queue, zeroed before the launch) or, without
 // a queue, round-robin. a.kc_of(B) is the column tile of row count B.
-template <bool TRANS, typename TV, typename TA, typename TX, typename TXI>
+template <bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true>
 __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
         const WorkItem w = a.items[it];
         const int kc = a.kc_of(w.B);
 #define VBCSR_ITEM_CASE(NB) \
-    case NB: process_item<NB, TRANS, TV, TA, TX, TXI>(a, w, kc, s_x, s_a, lane, dot); break;
+    case NB: process_item<NB, TRANS, TV, TA, TX, TXI, WIDE>(a, w, kc, s_x, s_a, lane, dot); break;
         switch (w.B) {
             VBCSR_ITEM_CASE(1) VBCSR_ITEM_CASE(2) VBCSR_ITEM_CASE(3) VBCSR_ITEM_CASE(4)
             VBCSR_ITEM_CASE(5) VBCSR_ITEM_CASE(6) VBCSR_ITEM_CASE(7) VBCSR_ITEM_CASE(8)
@@ -353,8 +357,10 @@ inline cudaError_t launch_smem_opt_in(K kernel, size_t smem) {
     return cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 1024);
 }
 
+// narrow: the persistent forward kernel in its narrow form (process_item's
+// WIDE = false), for operators with many row counts.
 template <typename TV, typename TA, typename TX, typename TXI>
-cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s) {
+cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s, bool narrow = false) {
     const int threads = a.warps * 32;
     const size_t smem = fma_smem_bytes(trans, a.warps);
     cudaError_t e;
@@ -362,6 +368,10 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
         if (trans) {
             if ((e = launch_smem_opt_in(fma_persistent_kernel<true, TV, TA, TX, TXI>, smem)) != cudaSuccess) return e;
             fma_persistent_kernel<true, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);
+        } else if (narrow) {
+            auto k = fma_persistent_kernel<false, TV, TA, TX, TXI, false>;
+            if ((e = launch_smem_opt_in(k, smem)) != cudaSuccess) return e;
+            k<<<a.grid, threads, smem, s>>>(a);
         } else {
             if ((e = launch_smem_opt_in(fma_persistent_kernel<false, TV, TA, TX, TXI>, smem)) != cudaSuccess) return e;
             fma_persistent_kernel<false, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);
@@ -394,10 +404,11 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
 // The kernel a launch runs (persistent, or the bucket kernel of row count B),
 // for its occupancy-derived grid size.
 template <typename TV, typename TA, typename TX, typename TXI>
-const void *fma_kernel_ptr(bool trans, bool persistent, int B) {
+const void *fma_kernel_ptr(bool trans, bool persistent, int B, bool narrow = false) {
     if (persistent)
         return trans ? (const void *)fma_persistent_kernel<true, TV, TA, TX, TXI>
-                     : (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;
+               : narrow ? (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, false>
+                        : (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;
 #define VBCSR_PTR_CASE(NB)                                                                 \
     case NB:                                                                               \
         return trans ? (const void *)fma_product_kernel<NB, true, TV, TA, TX, TXI>         \

@@ -103,7 +103,9 @@ cudaError_t launch_fma_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s)
 cudaError_t launch_fma_f32(int B, bool trans, const ProdArgs &a, cudaStream_t s);
 cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStream_t s);
 // double-FP32 arithmetic on (hi, lo) FP32 pairs of an FP64 operator and X, FP64 epilogue
-cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s);
+// narrow: the persistent forward kernel with two columns per lane for every row
+// count (for operators with many row counts)
+cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s, bool narrow);
 cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t ld, float2 *out, cudaStream_t s);
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
@@ -132,6 +134,48 @@ struct SpgemmArgs {
     void *C;                    // packed-order output
     double *norms;              // [n_out] Frobenius norm of every output block
 };
+// Symbolic stage of the block product on the device (Eq. 3). Per block row i
+// of A, the candidates C_ij reached by A_ik B_kj, their norm bounds
+// sum_k |A_ik| |B_kj| accumulated in increasing plan order of k, the kept set
+// (bound >= eps, in increasing j), and for each kept block its product list
+// ordered by inner size b_k, then by k. Pass 1 counts (per row: kept blocks,
+// products, values); pass 2 writes at the row offsets the host scanned.
+struct SymArgs {
+    int64_t n_rows;             // rows to process: rows[t] when given, else t
+    const int64_t *rows;
+    const int64_t *a_rowptr, *b_rowptr;   // plan block range of every block row
+    const int32_t *a_col, *b_col;         // block column of every plan block
+    const double *a_norm, *b_norm;        // Frobenius norm of every plan block
+    const int32_t *a_w;                   // b_k of every plan block of A
+    const int64_t *a_pbase, *b_pbase;     // panel element [0, 0] of every plan block
+    const int32_t *a_kp, *b_kp;           // panel stride of every plan block
+    const int32_t *a_rowsize;             // b_i of every block row of A
+    const int32_t *b_colsize;             // b_j of every block column of B
+    double eps;
+    // workspace: a shared-memory table per warp (global == 0), or a global slice
+    // per listed row at ws_off[t] with table size ws_h[t] and capacity ws_cap[t]
+    int global_ws;
+    unsigned char *ws;
+    const int64_t *ws_off;
+    const int32_t *ws_h, *ws_cap;
+    // pass 1 outputs
+    int64_t *cnt_out, *cnt_prod, *cnt_val;   // per block row
+    int32_t *overflow;                       // per block row: more candidates than the table holds
+    // pass 2: row offsets (inputs) and the lists (outputs)
+    const int64_t *off_out, *off_prod, *off_val;
+    int32_t *out_col, *out_bi, *out_bj;
+    int64_t *out_uoff, *out_pbeg;
+    int64_t *pa, *pb;
+    int32_t *kpa, *kpb, *bk;
+};
+constexpr int kSymHash = 2048;   // shared-memory table slots per warp
+constexpr int kSymCap = 512;     // candidates per row the shared-memory table holds
+// workspace bytes of one row: bound (8 B), key and slot (4 B each) per table
+// slot, candidate, kept index and cursor (4 B each) per candidate
+__host__ __device__ constexpr size_t sym_ws_bytes(int h, int cap) {
+    return (size_t)8 * cap + (size_t)8 * h + (size_t)12 * cap;
+}
+cudaError_t launch_spgemm_symbolic(int pass, const SymArgs &g, cudaStream_t s);
 cudaError_t launch_block_norms(bool f64, int64_t nblk, const void *panel, const int64_t *pbase, const int32_t *kp,
                                const int32_t *bi, const int32_t *bj, double *out, cudaStream_t s);
 cudaError_t launch_spgemm_numeric(bool f64, const SpgemmArgs &g, cudaStream_t s);

@@ -153,3 +153,26 @@ def test_autotune_picks_a_tensor_core_variant():
     got = H.spmm(_dev(X), precision="bf16x2").cpu().numpy()
     ref, _ = forward_ref(w.pattern, w.values, X, 1.0, 0.0, None)
     assert rel_fro(got, ref) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("mode", ["tf32", "tf32x3", "bf16x2"])
+@pytest.mark.parametrize("staged", [False, True])
+def test_tensor_core_products_exact_on_small_integers(mode, staged):
+    """Small-integer values and X make every piece product and partial sum
+    exact in FP32, so the tensor-core result in FP64 must equal the oracle bit
+    for bit: at alpha = 1, at alpha = 3, at alpha = 0.1 (not an FP32 number)
+    and with beta = -1. Zero blocks give exactly zero rows."""
+    pat = syn.random_pattern(37, 37, (4, 9, 13, 16), 0.3, 5, empty_rows=3)
+    rng = np.random.default_rng(5)
+    vals = rng.integers(-4, 5, pat.nnz).astype(np.float64)
+    vals[: pat.nnz // 7] = 0.0
+    H = _handle(pat, vals)
+    H.set_schedule("persistent", mma_staged=staged)
+    for k in (8, 17, 32):
+        X = rng.integers(-4, 5, (pat.n_cols, k)).astype(np.float64)
+        Y0 = rng.integers(-8, 9, (pat.n_rows, k)).astype(np.float64)
+        for alpha, beta in ((1.0, 0.0), (3.0, 0.0), (0.1, 0.0), (2.0, -1.0)):
+            Yd = _dev(Y0)
+            H.spmm(_dev(X), alpha, beta, Yd, precision=mode)
+            ref, _ = forward_ref(pat, vals, X, alpha, beta, Y0)
+            np.testing.assert_array_equal(Yd.cpu().numpy(), ref)

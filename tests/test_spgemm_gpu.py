@@ -77,3 +77,42 @@ def test_spgemm_rejects_mismatched_inner_sizes():
     pb = syn.random_pattern(4, 3, (3,), 0.5, 2)
     with pytest.raises(VBCSRError):
         _h(pa, syn.random_values(pa, 1)).spgemm(_h(pb, syn.random_values(pb, 2)))
+
+
+def test_spgemm_row_beyond_the_shared_table():
+    """A block row with more candidate blocks than the symbolic stage's
+    shared-memory table holds goes through its device-memory workspace and
+    gives the same result."""
+    rng = np.random.default_rng(65)
+    na, nk, nj = 6, 700, 1500
+    # row 0 of A is dense; B is sparse with ~3 blocks per row: row 0 of C has ~1300 candidates
+    a_ptr = [0, nk] + [nk + 3 * r for r in range(1, na)]
+    a_col = list(range(nk)) + [int(c) for r in range(1, na) for c in sorted(rng.choice(nk, 3, replace=False))]
+    b_ptr = [3 * r for r in range(nk + 1)]
+    b_col = [int(c) for r in range(nk) for c in sorted(rng.choice(nj, 3, replace=False))]
+    pa = BlockPattern(np.array([2, 1, 3, 2, 1, 2], np.int32), np.ones(nk, np.int32),
+                      np.array(a_ptr, np.int64), np.array(a_col, np.int32))
+    pb = BlockPattern(np.ones(nk, np.int32), rng.integers(1, 3, nj).astype(np.int32),
+                      np.array(b_ptr, np.int64), np.array(b_col, np.int32))
+    va, vb = syn.random_values(pa, 65), syn.random_values(pb, 66)
+    for eps in (0.0, 0.5):
+        C = _h(pa, va).spgemm(_h(pb, vb), eps)
+        _check(C, oracle.spgemm(pa, va, pb, vb, eps))
+
+
+def test_spgemm_zincblende_and_repeatable():
+    """Square of a small zinc-blende operator at a threshold that drops about
+    half of the blocks; a second call gives the identical pattern and values."""
+    w = syn.zincblende(150)
+    H = _h(w.pattern, w.values)
+    ref = oracle.spgemm(w.pattern, w.values, w.pattern, w.values, 0.0)
+    _check(H.spgemm(H, 0.0), ref)
+    rb, cb, ptr, cols, vals = ref
+    rows = np.repeat(np.arange(len(rb)), np.diff(ptr))
+    sz = rb[rows].astype(np.int64) * cb[cols]
+    norms = np.sqrt(np.add.reduceat(vals * vals, np.concatenate([[0], np.cumsum(sz)[:-1]])))
+    eps = float(np.median(norms))
+    C1, C2 = H.spgemm(H, eps), H.spgemm(H, eps)
+    _check(C1, oracle.spgemm(w.pattern, w.values, w.pattern, w.values, eps))
+    assert all(np.array_equal(x, y) for x, y in zip(C1.pattern, C2.pattern))
+    assert torch.equal(C1.get_values(), C2.get_values())

@@ -258,10 +258,12 @@ def test_fused_epilogue_gamma_z_and_dot(transpose, sizes, precision):
     assert abs(dot.item() - np.sum(R * got)) <= 1e-12 * np.sum(np.abs(R * got))
 
 
-@pytest.mark.parametrize("sizes", SIZES)
+@pytest.mark.parametrize("sizes", SIZES + [(3, 16), (8,)])
 @pytest.mark.parametrize("k", [1, 8, 33])
 def test_df32_mode_meets_fp64_tolerance(sizes, k):
-    """FP64 operands in double-FP32 arithmetic: held to the FP64 tolerance."""
+    """FP64 operands in double-FP32 arithmetic: held to the FP64 tolerance.
+    Operators with one or two row counts run the persistent kernel's wide
+    form (four columns per lane up to 13 rows), the others its narrow form."""
     seed = 7 + k
     pat = syn.random_pattern(37, 29, sizes, 0.15, seed, empty_rows=3, unsorted=True)
     vals = syn.random_values(pat, seed)
