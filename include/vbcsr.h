@@ -385,14 +385,18 @@ int vbcsr_chebyshev_noalloc(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr
  * handle in *C. A's block columns must be B's block rows (same count and
  * sizes); same dtype. With Frobenius block norms:
  *  symbolic stage  a candidate block (i, j) is kept when the bound
- *                  sum_k ||A_ik|| ||B_kj|| (Eq. 3) is >= eps;
+ *                  sum_k ||A_ik|| ||B_kj|| (Eq. 3, summed over k in
+ *                  increasing column order) is >= eps; on the GPU, one warp
+ *                  per block row;
  *  numeric stage   C_ij = sum_k A_ik B_kj over every k with both blocks stored
  *                  (products grouped by output block, equal inner sizes b_k
  *                  adjacent), on the GPU;
  *  final filter    blocks with ||C_ij|| < eps are removed.
- * eps = 0 keeps every block reached by a product path. The block norms, the
- * candidate lists and the filtered pattern pass through host memory; the
- * call synchronises `stream`. Errors: INVALID_ARG, NO_MEMORY, CUDA.
+ * eps = 0 keeps every block reached by a product path. The per-row counts of
+ * the symbolic stage, the block columns and norms of the candidates and the
+ * filtered pattern pass through host memory; the call synchronises `stream`.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA; UNSUPPORTED when one block row has
+ * more than 2^28 candidate products.
  */
 int vbcsr_spgemm(const vbcsr_t *A, const vbcsr_t *B, double eps, vbcsr_t **C, void *stream);
 

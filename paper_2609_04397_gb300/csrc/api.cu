@@ -222,11 +222,16 @@ static int validate_pattern(int64_t n_brows, int64_t n_bcols, const int32_t *row
     if (nblk >= (1LL << 31)) return fail(VBCSR_ERR_PATTERN, "%lld blocks reach 2^31", (long long)nblk);
     std::vector<int32_t> tmp;
     for (int64_t i = 0; i < n_brows; ++i) {
-        tmp.assign(block_col_idx + block_row_ptr[i], block_col_idx + block_row_ptr[i + 1]);
-        for (int32_t c : tmp)
+        bool increasing = true;   // strictly increasing columns: in range and free of duplicates
+        for (int64_t u = block_row_ptr[i]; u < block_row_ptr[i + 1]; ++u) {
+            const int32_t c = block_col_idx[u];
             if (c < 0 || c >= n_bcols)
                 return fail(VBCSR_ERR_PATTERN, "column %d of block row %lld outside [0, %lld)", c, (long long)i,
                             (long long)n_bcols);
+            if (u > block_row_ptr[i] && c <= block_col_idx[u - 1]) increasing = false;
+        }
+        if (increasing) continue;
+        tmp.assign(block_col_idx + block_row_ptr[i], block_col_idx + block_row_ptr[i + 1]);
         std::sort(tmp.begin(), tmp.end());
         for (size_t e = 1; e < tmp.size(); ++e)
             if (tmp[e] == tmp[e - 1])

@@ -61,6 +61,8 @@ def _create(L, rb, cb, rp, ci, vals, dtype=0):
     (dict(rp=[0, 2, 1]), -2, "decreases"),
     (dict(ci=[0, 2, 1]), -2, "outside"),
     (dict(ci=[0, 0, 1]), -2, "duplicate"),
+    (dict(rp=[0, 3, 4], ci=[1, 0, 1, 1]), -2, "duplicate"),   # unsorted row with a duplicate
+    (dict(rp=[0, 3, 4], ci=[1, 0, 2, 1]), -2, "outside"),
     (dict(ci=[0, -1, 1]), -2, "outside"),
     (dict(rb=[0, 2]), -2, "row_bsize"),
     (dict(cb=[1, 5000]), -2, "col_bsize"),

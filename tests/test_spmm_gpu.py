@@ -179,6 +179,15 @@ def test_shape_class_registry():
         expect[(int(bi), int(bj))] = expect.get((int(bi), int(bj)), 0) + 1
     assert {(a, b): c for a, b, c in cls} == expect
     assert len(cls) == 4
+    assert [(a, b) for a, b, _ in cls] == sorted(expect)          # increasing (b_i, b_j)
+    # rectangular, unsorted rows, many sizes on both sides
+    pat = syn.random_pattern(60, 45, (1, 2, 5, 7, 13, 16, 20), 0.2, 9, empty_rows=3, unsorted=True)
+    H = _handle(pat, syn.random_values(pat, 9))
+    cls = H.shape_classes()
+    expect = {}
+    for bi, bj in zip(pat.row_bsize[pat.block_rows()], pat.col_bsize[pat.block_col_idx]):
+        expect[(int(bi), int(bj))] = expect.get((int(bi), int(bj)), 0) + 1
+    assert [(a, b, c) for a, b, c in cls] == [(a, b, expect[(a, b)]) for a, b in sorted(expect)]
 
 
 def test_fp32_operator():
