@@ -395,6 +395,68 @@ def spgemm_section(dev):
     return out
 
 
+def ops_section(H, pat, values, dev, steps):
+    """The other products of the method on the bench operator, FP64: the
+    adjoint (Eq. 1) and the pattern-sampled product dH_ij = A_i B_j^T at
+    k = 1, 8, 32 (2 flop per stored entry and column each), and the Chebyshev
+    recurrence (Sec. V) on the operator scaled to [-1, 1]: 30 moments of 16
+    vectors (29 products with the fused moment dot, checkpoints every 10
+    steps), then the same through the differentiable moments with the reverse
+    recurrence (adjoint products, recomputed segments, pattern-sampled
+    products)."""
+    import torch
+    from paper_2609_04397_gb300 import VBCSR, chebyshev_moments
+    reps = max(5, steps // 10)
+
+    def timed(fn, n=reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n
+
+    def rate(flops, ms):
+        return {"ms": ms, "gflops": flops / ms / 1e6, "fp64_alu_frac": flops / ms / 1e9 / FP64_PEAK_TFLOPS}
+
+    res = {}
+    for k in KS:
+        X = torch.randn(pat.n_rows, k, dtype=torch.float64, device=dev)
+        Y = torch.empty(pat.n_cols, k, dtype=torch.float64, device=dev)
+        res[f"adjoint_k{k}"] = rate(2.0 * pat.nnz * k, timed(lambda: H.spmm_adjoint(X, 1.0, 0.0, Y)))
+    for k in KS:
+        A = torch.randn(pat.n_rows, k, dtype=torch.float64, device=dev)
+        B = torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev)
+        D = torch.empty(pat.nnz, dtype=torch.float64, device=dev)
+        ms = timed(lambda: H.sddmm(A, B, 1.0, 0.0, D))
+        res[f"sddmm_k{k}"] = {**rate(2.0 * pat.nnz * k, ms),
+                              "gbs": (8.0 * pat.nnz + 8.0 * k * (pat.n_rows + pat.n_cols)) / ms / 1e6}
+    Ht = VBCSR.from_pattern(pat, values, torch.float64, dev)
+    lo, hi = Ht.gershgorin()
+    Ht.shift_scale((hi + lo) / 2, 1.01 * (hi - lo) / 2)
+    k, M = 16, 30
+    g = torch.Generator(device=dev).manual_seed(0)
+    R = torch.randint(0, 2, (pat.n_rows, k), generator=g, device=dev).to(torch.float64) * 2 - 1
+    fwd = timed(lambda: Ht.chebyshev(R, M, ckpt_every=10), n=3)
+    res["chebyshev_k16_m30"] = {**rate(2.0 * pat.nnz * k * (M - 1), fwd), "ms_per_product": fwd / (M - 1)}
+    vt = Ht.get_values().requires_grad_(True)
+
+    def fwd_bwd():
+        mu = chebyshev_moments(Ht, vt, R, M, ckpt_every=10)
+        (mu * mu).sum().backward()
+        vt.grad = None
+
+    res["chebyshev_k16_m30_with_gradient"] = {"ms": timed(fwd_bwd, n=3)}
+    del Ht, vt
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
     world, rank, _ = _dist()
@@ -605,6 +667,7 @@ def run_ours(args):
            "d2h_bytes_per_step": int(sum(8 * pat.n_rows * k for k in KS)), "ms_per_step": e2e_ms}
 
     batched = batched_section(dev, args.steps) if not args.no_batched else None
+    ops = ops_section(H, pat, w.values, dev, args.steps) if not args.no_ops else None
     domains = domains_section(dev, args.steps) if args.domains else None
     kspace = kspace_section(dev, args.steps, max(1, round((args.atoms / 8) ** (1 / 3)))) if args.kspace else None
     spg = spgemm_section(dev) if args.spgemm else None
@@ -617,6 +680,7 @@ def run_ours(args):
                        "alpha": 1.0, "beta": 0.0, "parallelism": f"replicas x{world}",
                        "l2": f"no flush: inputs larger than L2 ({8 * pat.nnz / 1e9:.2f} GB of values per product)"},
             "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
+            **({"ops": ops} if ops is not None else {}),
             **({"domains": domains} if domains is not None else {}),
             **({"kspace": kspace} if kspace is not None else {}),
             **({"spgemm": spg} if spg is not None else {}),
@@ -639,6 +703,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-ops", action="store_true",
+                    help="skip the adjoint, pattern-sampled and Chebyshev timings")
     ap.add_argument("--spgemm", action="store_true",
                     help="also measure the thresholded block product C = H H")
     ap.add_argument("--kspace", action="store_true",

@@ -1117,6 +1117,21 @@ extern "C" int vbcsr_spmm_ex(vbcsr_t *A, int transpose, int64_t k, double alpha,
     return run_product(A, transpose == 1, k, alpha, X, ldx, beta, Y, ldy, epi, precision, (cudaStream_t)stream);
 }
 
+// the pattern fields of a pattern-sampled product over the handle's forward items
+static SddmmArgs sddmm_args(vbcsr_t *A) {
+    SddmmArgs a;
+    memset(&a, 0, sizeof(a));
+    a.items = A->fwd_lpt;
+    a.n_items = A->n_fwd_items;
+    a.queue = A->queue;
+    a.fl_xrow = A->fl_xrow;
+    a.fl_pcol = A->fl_pcol;
+    a.fl_w = A->fl_w;
+    a.fl_uoff = A->fl_uoff;
+    a.fl_pbase = A->fl_pbase;
+    return a;
+}
+
 extern "C" int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop, int64_t lda, const void *Bop,
                            int64_t ldb, double beta, void *D, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
@@ -1128,14 +1143,7 @@ extern "C" int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop,
         if (!Aop || !Bop) return fail(VBCSR_ERR_INVALID_ARG, "operand is NULL");
         if (lda < k || ldb < k) return fail(VBCSR_ERR_INVALID_ARG, "leading dimension below k");
     }
-    SddmmArgs a;
-    a.n_brows = A->n_brows;
-    a.prow_ptr = A->prow_ptr;
-    a.row_off = A->d_row_off;
-    a.row_b = A->d_row_b;
-    a.fl_xrow = A->fl_xrow;
-    a.fl_w = A->fl_w;
-    a.fl_uoff = A->fl_uoff;
+    SddmmArgs a = sddmm_args(A);
     a.k = alpha != 0.0 ? k : 0;
     a.alpha = alpha;
     a.beta = beta;
@@ -1258,14 +1266,7 @@ extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, 
                 std::swap(cur, nxt);
             }
         }
-        SddmmArgs a;
-        a.n_brows = A->n_brows;
-        a.prow_ptr = A->prow_ptr;
-        a.row_off = A->d_row_off;
-        a.row_b = A->d_row_b;
-        a.fl_xrow = A->fl_xrow;
-        a.fl_w = A->fl_w;
-        a.fl_uoff = A->fl_uoff;
+        SddmmArgs a = sddmm_args(A);
         a.k = cnt * k;
         a.alpha = 1.0;
         a.beta = first ? 0.0 : 1.0;

@@ -194,13 +194,14 @@ size_t mma_smem_bytes(bool trans, bool staged, int warps);
 
 // Misc kernels (misc.cu).
 struct SddmmArgs {
-    int64_t n_brows;
-    const int64_t *prow_ptr;    // plan block range of every block row
-    const int64_t *row_off;     // r_i
-    const int32_t *row_b;       // b_i
+    const WorkItem *items;      // the forward work items (rows of a block row), in descending cost
+    int64_t n_items;
+    long long *queue;           // device work counter (zeroed by the launch)
     const int32_t *fl_xrow;     // c_j
+    const int32_t *fl_pcol;     // first panel column of the block
     const int32_t *fl_w;        // b_j
     const int64_t *fl_uoff;     // packed-order offset of the block
+    const int64_t *fl_pbase;    // panel element [0, 0] of the block
     int64_t k;
     double alpha, beta;
     const void *A; int64_t lda;

@@ -24,58 +24,143 @@ int max_resident_ctas(const void *kernel, int threads, size_t smem) {
 
 // ---------------------------------------------------------------------------
 // SDDMM: D_ij[p, q] = alpha * <A[r_i + p, :], B[c_j + q, :]> + beta * D_ij[p, q].
-// One warp per block row; lanes own output entries of the current block, so
-// the block's packed-order output is written contiguously.
+//
+// The forward product's work decomposition read the other way round: one warp
+// per work item (B <= 16 rows of a block row, taken in descending cost from a
+// device counter); its virtual columns t (the stored blocks' columns c_j + q
+// side by side) are staged in shared memory with the packed-order address of
+// (row r0 + p, column q) of their block. Lane t keeps the B sums of column t
+// in registers, reads its own row of B (contiguous in c) and the item's rows
+// of A from shared memory (a broadcast; alpha folded in when they are staged),
+// kSdCK columns of c at a time: B FMAs per value read from B, the packed
+// output written once per entry.
+
+constexpr int kSdCK = 32;   // columns c of A staged per chunk
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <typename T>
-__global__ void sddmm_kernel(SddmmArgs a, int warps) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+template <int B, typename T>
+__device__ __forceinline__ void sddmm_item(const SddmmArgs &a, const WorkItem &w, int32_t *s_x, int64_t *s_u,
+                                           int32_t *s_w, T *s_a, int lane) {
     const T *__restrict__ A = static_cast<const T *>(a.A);
     const T *__restrict__ Bm = static_cast<const T *>(a.B);
     T *__restrict__ D = static_cast<T *>(a.D);
     const T alpha = (T)a.alpha, beta = (T)a.beta;
-    for (int64_t i = (int64_t)blockIdx.x * warps + warp; i < a.n_brows; i += (int64_t)gridDim.x * warps) {
-        const int64_t ri = a.row_off[i];
-        const int bi = a.row_b[i];
-        for (int64_t l = a.prow_ptr[i]; l < a.prow_ptr[i + 1]; ++l) {
-            const int bj = a.fl_w[l];
-            const int64_t cj = a.fl_xrow[l];
-            T *d = D + a.fl_uoff[l];
-            const int ne = bi * bj;
-            for (int e = lane; e < ne; e += 32) {
-                const int p = e / bj, q = e - (e / bj) * bj;
-                const T *ar = A + (ri + p) * a.lda;
-                const T *br = Bm + (cj + q) * a.ldb;
-                T s = (T)0;
-                for (int64_t c = 0; c < a.k; ++c) s = fma_t(__ldg(ar + c), __ldg(br + c), s);
-                T r = alpha * s;
-                if (a.beta != 0.0) r += beta * d[e];
-                d[e] = r;
+    if (w.nlist == 0) return;
+    // the item's first row inside its block row (items split rows taller than 16)
+    const int64_t r0 = (w.vbase - a.fl_pbase[w.lbegin]) / w.Kp;
+    const int nck = (int)((a.k + kSdCK - 1) / kSdCK);
+    for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+        const int tn = min(kKMax, w.K - t0);
+        __syncwarp();
+        for (int e = lane; e < w.nlist; e += 32) {
+            const int64_t l = w.lbegin + e;
+            const int xr = a.fl_xrow[l], pc = a.fl_pcol[l], wd = a.fl_w[l];
+            const int64_t u = a.fl_uoff[l] + r0 * wd;
+            const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
+            for (int t = lo; t < hi; ++t) {
+                s_x[t - t0] = xr + (t - pc);
+                s_u[t - t0] = u + (t - pc);
+                s_w[t - t0] = wd;
+            }
+        }
+        __syncwarp();
+        for (int tb = 0; tb < tn; tb += 32) {
+            const int t = tb + lane;
+            const bool tv = t < tn;
+            T acc[B];
+#pragma unroll
+            for (int p = 0; p < B; ++p) acc[p] = (T)0;
+            for (int ck = 0; ck < nck; ++ck) {
+                const int64_t c0 = (int64_t)ck * kSdCK;
+                const int cn = (int)min((int64_t)kSdCK, a.k - c0);
+                if (nck > 1 || tb == 0) {   // alpha times the item's rows of A, columns c0 .. c0 + cn
+                    __syncwarp();
+                    for (int e = lane; e < B * cn; e += 32) {
+                        const int p = e / cn, c = e - p * cn;
+                        const T v = __ldg(A + (w.yrow + p) * a.lda + c0 + c);
+                        s_a[p * kSdCK + c] = a.alpha == 1.0 ? v : alpha * v;
+                    }
+                    __syncwarp();
+                }
+                if (tv) {
+                    const T *br = Bm + (int64_t)s_x[t] * a.ldb + c0;
+                    for (int c = 0; c < cn; ++c) {
+                        const T b = __ldg(br + c);
+#pragma unroll
+                        for (int p = 0; p < B; ++p) acc[p] = fma_t(s_a[p * kSdCK + c], b, acc[p]);
+                    }
+                }
+            }
+            if (tv) {
+                const int64_t u = s_u[t];
+                const int wd = s_w[t];
+#pragma unroll
+                for (int p = 0; p < B; ++p) {
+                    T *d = D + u + (int64_t)p * wd;
+                    *d = a.beta != 0.0 ? fma_t(beta, *d, acc[p]) : acc[p];
+                }
             }
         }
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) sddmm_kernel(SddmmArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *s_a = reinterpret_cast<T *>(smem_raw) + (size_t)warp * 16 * kSdCK;
+    int64_t *s_u = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * 16 * kSdCK * sizeof(T)) + warp * kKMax;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw + (size_t)warps * (16 * kSdCK * sizeof(T) +
+                                                                            kKMax * sizeof(int64_t))) +
+                   warp * 2 * kKMax;
+    int32_t *s_w = s_x + kKMax;
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+        const int64_t it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+#define VBCSR_SDDMM_CASE(NB) \
+    case NB: sddmm_item<NB, T>(a, w, s_x, s_u, s_w, s_a, lane); break;
+        switch (w.B) {
+            VBCSR_SDDMM_CASE(1) VBCSR_SDDMM_CASE(2) VBCSR_SDDMM_CASE(3) VBCSR_SDDMM_CASE(4)
+            VBCSR_SDDMM_CASE(5) VBCSR_SDDMM_CASE(6) VBCSR_SDDMM_CASE(7) VBCSR_SDDMM_CASE(8)
+            VBCSR_SDDMM_CASE(9) VBCSR_SDDMM_CASE(10) VBCSR_SDDMM_CASE(11) VBCSR_SDDMM_CASE(12)
+            VBCSR_SDDMM_CASE(13) VBCSR_SDDMM_CASE(14) VBCSR_SDDMM_CASE(15) VBCSR_SDDMM_CASE(16)
+            default: break;
+        }
+#undef VBCSR_SDDMM_CASE
+    }
+}
+
 cudaError_t launch_sddmm(bool f64, const SddmmArgs &a, cudaStream_t s) {
-    if (a.n_brows == 0) return cudaSuccess;
-    const int warps = 8, threads = warps * 32;
+    if (a.n_items == 0) return cudaSuccess;
+    const int warps = 4, threads = warps * 32;
+    const size_t esz = f64 ? sizeof(double) : sizeof(float);
+    const size_t smem = (size_t)warps * (16 * kSdCK * esz + kKMax * (sizeof(int64_t) + 2 * sizeof(int32_t)));
     static int cap64 = 0, cap32 = 0;
     int &cap = f64 ? cap64 : cap32;
+    const void *k = f64 ? (const void *)sddmm_kernel<double> : (const void *)sddmm_kernel<float>;
     if (!cap) {
-        cap = max_resident_ctas(f64 ? (const void *)sddmm_kernel<double> : (const void *)sddmm_kernel<float>,
-                                threads, 0);
+        cap = max_resident_ctas(k, threads, smem);
         if (cap < 0) {
             cap = 0;
             return cudaGetLastError();
         }
     }
-    int64_t need = (a.n_brows + warps - 1) / warps;
-    int grid = (int)(need < cap ? need : cap);
-    if (f64) sddmm_kernel<double><<<grid, threads, 0, s>>>(a, warps);
-    else sddmm_kernel<float><<<grid, threads, 0, s>>>(a, warps);
+    if (smem + 1024 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem + 1024);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (a.n_items + warps - 1) / warps;
+    const int grid = (int)(need < cap ? need : cap);
+    if (f64) sddmm_kernel<double><<<grid, threads, smem, s>>>(a);
+    else sddmm_kernel<float><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

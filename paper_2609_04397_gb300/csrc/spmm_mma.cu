@@ -110,8 +110,24 @@ __device__ __forceinline__ void step(float (&acc)[4], const Pieces &ag, const Pi
     }
 }
 
+// Resident CTAs (of 4 warps) per SM and the forward kernel's step group U, per
+// mode and column-tile count. Measured on GB300 (50k-atom zinc-blende operator,
+// one GPU, variants side by side): the pre-split BF16X2 kernel at NT = 4 runs
+// 6.6 % faster at 5 CTAs (96 registers, no spills) than at 4, at NT = 1 4 % faster
+// at 7 than at 6; TF32X3 at NT = 2 2.4 % faster with U = 2 at 5 CTAs; the
+// in-kernel BF16X2 and TF32X3 splits at NT = 4 would spill at 5 CTAs and stay at
+// 4. Everything else kept what ran best before: NT = 1 U = 2 at 6 CTAs, NT = 2
+// U = 4 at 4 CTAs, NT = 4 U = 2.
+template <int MODE, int NT>
+struct MmaShape {
+    static constexpr int CTAS = NT == 1 ? (MODE == kBF16X2Presplit ? 7 : 6)
+                              : NT == 2 ? (MODE == kTF32X3 ? 5 : 4)
+                                        : ((MODE == kTF32X3 || MODE == kBF16X2) ? 4 : 5);
+    static constexpr int U = NT == 2 && MODE != kTF32X3 ? 4 : 2;
+};
+
 template <int MODE, bool TRANS, typename TX, int NT>
-__global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdArgs a) {
+__global__ void __launch_bounds__(128, MmaShape<MODE, NT>::CTAS) mma_product_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
     const int warp = threadIdx.x >> 5;
@@ -172,14 +188,11 @@ __global__ void __launch_bounds__(128, NT == 1 ? 6 : 4) mma_product_kernel(ProdA
                         __syncwarp();
                     }
                     if (!TRANS) {
-                        // forward: groups of U steps; all value and X loads of a group are
-                        // issued before its MMAs, so each warp has U steps of loads in flight.
-                        // Measured on GB300 (50k-atom zinc-blende operator): k <= 8 runs best
-                        // with U = 2 at 6 CTAs per SM (77 registers), k <= 16 with U = 4 and
-                        // k <= 32 with U = 2 at 4 CTAs per SM (<= 128 registers, no spills).
-                        // A window holds kKMax = 512 columns, a multiple of 16 U, so a group
-                        // never straddles two windows.
-                        constexpr int U = NT == 1 ? 2 : (NT == 2 ? 4 : 2);
+                        // forward: groups of U steps (MmaShape); all value and X loads of a
+                        // group are issued before its MMAs, so each warp has U steps of loads
+                        // in flight. A window holds kKMax = 512 columns, a multiple of 16 U,
+                        // so a group never straddles two windows.
+                        constexpr int U = MmaShape<MODE, NT>::U;
                         for (int cg = 0; cg < tn; cg += 16 * U) {
                             float4 qa[U], qb[U];
                             float xv[U][NT][4];

@@ -111,6 +111,29 @@ def test_wide_rows_and_tall_blocks():
         got = H.spmm_adjoint(_dev(X)).cpu().numpy()
         ref, scale = adjoint_ref(pat, vals, X, 1.0, 0.0, None)
         check_elementwise(got, ref, scale, TOL_F64)
+    # the pattern-sampled product over the same rows (chunked rows, wide windows,
+    # several staged column chunks of A and B, leading dimensions above k)
+    for k in (1, 70):
+        rng = np.random.default_rng(k + 100)
+        A = rng.standard_normal((pat.n_rows, k + 3))
+        B = rng.standard_normal((pat.n_cols, k + 5))
+        D0 = rng.standard_normal(pat.nnz)
+        Dd = _dev(D0)
+        H.sddmm(_dev(A)[:, :k], _dev(B)[:, :k], 1.5, -0.5, Dd)
+        ref, scale = sddmm_ref(pat, A[:, :k], B[:, :k], 1.5, -0.5, D0)
+        check_elementwise(Dd.cpu().numpy(), ref, scale, TOL_F64)
+
+
+def test_sddmm_fp32_operator():
+    pat = syn.random_pattern(30, 30, (4, 9, 13), 0.2, 11)
+    H = _handle(pat, syn.random_values(pat, 11).astype(np.float32), torch.float32)
+    rng = np.random.default_rng(11)
+    for k in (1, 16, 40):
+        A = rng.standard_normal((pat.n_rows, k)).astype(np.float32)
+        B = rng.standard_normal((pat.n_cols, k)).astype(np.float32)
+        got = H.sddmm(_dev(A, torch.float32), _dev(B, torch.float32)).cpu().numpy().astype(np.float64)
+        ref, scale = sddmm_ref(pat, A.astype(np.float64), B.astype(np.float64), 1.0, 0.0, None)
+        check_elementwise(got, ref, scale, 1e-5)
 
 
 def test_beta_zero_and_alpha_zero_do_not_read():
