@@ -981,8 +981,6 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.err = A->err;
     a.debug_checks = A->debug_checks;
     const int kc_auto = auto_kc(k);
-    // the CUDA-core adjoint of a one-column product stages its values in shared memory
-    a.adj_stage = trans && kc_auto == 1 ? 1 : 0;
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
 
     // the double-FP32 persistent forward kernel in its narrow form when the
@@ -1083,15 +1081,14 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         const int warps = A->persist_warps ? A->persist_warps : 4;
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps,
-                    split ? fma_split_kernel(mode) : fma_kern(true, 0), fma_smem_bytes(trans, warps, a.adj_stage != 0));
+                    split ? fma_split_kernel(mode) : fma_kern(true, 0), fma_smem_bytes(trans, warps));
     } else {
         const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
         const WorkItem *items = trans ? A->adj_items : A->fwd_items;
         for (const Bucket &b : buckets) {
             a.kc = kc_for(b.B);
             const int warps = A->warps_b[b.B] ? A->warps_b[b.B] : 4;
-            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false, b.B),
-                        fma_smem_bytes(trans, warps, a.adj_stage != 0));
+            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false, b.B), fma_smem_bytes(trans, warps));
             if (rc) return rc;
         }
     }

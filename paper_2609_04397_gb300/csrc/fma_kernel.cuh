@@ -146,7 +146,7 @@ __device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
 
 template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true>
 __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &w, int KC, int32_t *s_x,
-                                             int64_t *s_a, unsigned char *s_stage, int lane, double &dot) {
+                                             int64_t *s_a, int lane, double &dot) {
     const int TG = 32 / KC;
     const int cl = lane % KC;
     const int tg = lane / KC;
@@ -223,36 +223,6 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                     }
                     continue;
                 }
-                if (TRANS && KC == 1 && a.adj_stage) {
-                    // one output column: lane t of a 32-column group owns virtual column
-                    // t, whose B values are contiguous but far from the next column's.
-                    // The lanes first copy the group's values into shared memory
-                    // together (consecutive lanes on consecutive values, about B
-                    // columns per load instruction instead of 32 columns of 32 lines);
-                    // the odd row stride keeps the reads free of extra bank conflicts.
-                    constexpr int SB = B | 1;
-                    TV *st = reinterpret_cast<TV *>(s_stage);
-                    for (int tb = 0; tb < tn; tb += 32) {
-                        const int nt = min(32, tn - tb);
-                        __syncwarp();
-                        for (int e = lane; e < nt * B; e += 32) {
-                            const int tt = e / B, p = e - tt * B;
-                            st[tt * SB + p] = ld_ro(vals + s_a[tb + tt] + p);
-                        }
-                        __syncwarp();
-                        if (lane < nt) {
-                            const int xr = s_x[tb + lane];
-                            if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
-                                atomicExch(a.err, 1);
-                                continue;
-                            }
-                            const TA x = cv ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
-#pragma unroll
-                            for (int p = 0; p < B; ++p) acc[p] = fmat(adj_val((TA)st[lane * SB + p]), x, acc[p]);
-                        }
-                    }
-                    continue;
-                }
                 for (int t = tg; t < tn; t += TG) {
                     const int xr = s_x[t];
                     if (a.debug_checks && (xr < 0 || xr >= a.x_rows)) {
@@ -325,12 +295,10 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
-    unsigned char *s_stage = smem_raw + (size_t)warps * kKMax * (sizeof(int32_t) + sizeof(int64_t)) +
-                             (size_t)warp * kAdjStage;
     double dot = 0.0;
     for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, s_stage, lane, dot);
+        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, lane, dot);
     }
     if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
@@ -348,8 +316,6 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
-    unsigned char *s_stage = smem_raw + (size_t)warps * kKMax * (sizeof(int32_t) + sizeof(int64_t)) +
-                             (size_t)warp * kAdjStage;
     double dot = 0.0;
     int64_t it = (int64_t)blockIdx.x * warps + warp;
     for (;;) {
@@ -362,7 +328,7 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
         const WorkItem w = a.items[it];
         const int kc = a.kc_of(w.B);
 #define VBCSR_ITEM_CASE(NB) \
-    case NB: process_item<NB, TRANS, TV, TA, TX, TXI, WIDE>(a, w, kc, s_x, s_a, s_stage, lane, dot); break;
+    case NB: process_item<NB, TRANS, TV, TA, TX, TXI, WIDE>(a, w, kc, s_x, s_a, lane, dot); break;
         switch (w.B) {
             VBCSR_ITEM_CASE(1) VBCSR_ITEM_CASE(2) VBCSR_ITEM_CASE(3) VBCSR_ITEM_CASE(4)
             VBCSR_ITEM_CASE(5) VBCSR_ITEM_CASE(6) VBCSR_ITEM_CASE(7) VBCSR_ITEM_CASE(8)
@@ -401,7 +367,7 @@ constexpr bool kHasNarrowForm = sizeof(TV) == 8 && !(sizeof(TA) == 8 && alignof(
 template <typename TV, typename TA, typename TX, typename TXI>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s, bool narrow = false) {
     const int threads = a.warps * 32;
-    const size_t smem = fma_smem_bytes(trans, a.warps, a.adj_stage != 0);
+    const size_t smem = fma_smem_bytes(trans, a.warps);
     cudaError_t e;
     if (B == 0) {   // persistent launch over every row count
         if (trans) {

@@ -92,7 +92,6 @@ struct ProdArgs {
     long long *queue;       // device work counter, zero at launch (NULL: round-robin)
     uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
     int mma_staged;         // tensor-core forward: 1 = value panels staged in shared memory
-    int adj_stage;          // CUDA-core adjoint: 1 = the launch has the per-warp staging buffer
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
@@ -187,10 +186,7 @@ cudaError_t launch_compact(bool f64, int64_t n, const int64_t *keep_src, const i
 // query failed (the error stays pending for the caller to read).
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
 
-// shared memory of the CUDA-core product kernels; adj_stage adds the adjoint's
-// per-warp staging buffer for one-column products (kAdjStage bytes per warp)
-constexpr int kAdjStage = 32 * 17 * 16;
-size_t fma_smem_bytes(bool trans, int warps, bool adj_stage = false);
+size_t fma_smem_bytes(bool trans, int warps);
 // forward products of an FP64 operator in a tensor-core mode on the CUDA cores
 cudaError_t launch_fma_split(int mode, const ProdArgs &a, cudaStream_t s);
 const void *fma_split_kernel(int mode);

@@ -6,9 +6,8 @@
 
 namespace vbcsr {
 
-size_t fma_smem_bytes(bool trans, int warps, bool adj_stage) {
-    return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0)) +
-           (trans && adj_stage ? (size_t)warps * kAdjStage : 0);
+size_t fma_smem_bytes(bool trans, int warps) {
+    return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0));
 }
 
 int max_resident_ctas(const void *kernel, int threads, size_t smem) {
