@@ -916,10 +916,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const bool csr_kernel =
         A->backend == VBCSR_BACKEND_CSR && !trans && !cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
     const bool split = !fma && f64 && !trans && (k <= kSplitFmaMaxK || csr_kernel);
-    // the BF16X2 forward kernel of an FP64 operator reads values and X split once
-    // into packed bf16 (hi, lo) words (the plain kernel; the staged one splits itself)
-    const bool presplit = f64 && mode == VBCSR_PREC_BF16X2 && !trans && !split &&
-                          !(A->schedule & VBCSR_SCHED_MMA_STAGED);
+    // the BF16X2 forward kernels of an FP64 operator (the plain tensor-core kernel
+    // and the CUDA-core form of thin products; the staged kernel splits itself, the
+    // scalar kernel reads FP32) read values and X split once into packed bf16
+    // (hi, lo) words
+    const bool presplit = f64 && mode == VBCSR_PREC_BF16X2 && !trans && !csr_kernel &&
+                          (split || !(A->schedule & VBCSR_SCHED_MMA_STAGED));
     const int mma_mode = presplit ? kBF16X2Presplit : mode;
     if (f64 && mode != VBCSR_PREC_NATIVE && mode != VBCSR_PREC_DF32 && !presplit && !A->panel32_valid) {
         int rc = refresh_panel32(A, s);
@@ -1018,7 +1020,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         else if (mode == VBCSR_PREC_DF32)
             e = launch_fma_df(B, trans, a, s, df_narrow);
         else if (split)
-            e = launch_fma_split(mode, a, s);
+            e = launch_fma_split(mma_mode, a, s);
         else
             e = launch_mma(mma_mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
@@ -1081,7 +1083,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         const int warps = A->persist_warps ? A->persist_warps : 4;
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, warps,
-                    split ? fma_split_kernel(mode) : fma_kern(true, 0), fma_smem_bytes(trans, warps));
+                    split ? fma_split_kernel(mma_mode) : fma_kern(true, 0), fma_smem_bytes(trans, warps));
     } else {
         const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
         const WorkItem *items = trans ? A->adj_items : A->fwd_items;

@@ -30,7 +30,12 @@ struct SplitF {
     __device__ __forceinline__ SplitF() {}
     __device__ __forceinline__ SplitF(int z) : hi((float)z), lo(0.f) {}
     __device__ __forceinline__ explicit SplitF(float v) {
-        if (MODE == kBF16X2) {
+        if (MODE == kBF16X2Presplit) {
+            // v carries a packed word split earlier: hi bf16 in the low half, lo in the high
+            const uint32_t w = __float_as_uint(v);
+            hi = __uint_as_float(w << 16);
+            lo = __uint_as_float(w & 0xffff0000u);
+        } else if (MODE == kBF16X2) {
             hi = round_bf16(v);
             lo = round_bf16(v - hi);
         } else {

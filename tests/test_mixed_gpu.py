@@ -120,6 +120,11 @@ def test_mixed_copy_follows_set_values():
     got = H.spmm(_dev(X), precision="bf16x2").cpu().numpy()
     ref, _ = forward_ref(pat, v2, X, 1.0, 0.0, None)
     assert rel_fro(got, ref) <= TOL_MIXED
+    # the CUDA-core form of a one-column product reads the same split copy
+    H.set_values(_dev(v1))
+    got = H.spmm(_dev(X[:, :1]), precision="bf16x2").cpu().numpy()
+    ref, _ = forward_ref(pat, v1, X[:, :1], 1.0, 0.0, None)
+    assert rel_fro(got, ref) <= TOL_MIXED
 
 
 @pytest.mark.parametrize("mode", ["tf32", "tf32x3", "bf16x2"])
