@@ -116,3 +116,19 @@ def test_spgemm_zincblende_and_repeatable():
     _check(C1, oracle.spgemm(w.pattern, w.values, w.pattern, w.values, eps))
     assert all(np.array_equal(x, y) for x, y in zip(C1.pattern, C2.pattern))
     assert torch.equal(C1.get_values(), C2.get_values())
+
+
+def test_spgemm_everything_dropped_and_empty_operands():
+    """A threshold above every bound keeps nothing; an operand without blocks
+    gives an empty product. Both results are valid operators."""
+    w = syn.tiny_multispecies(0)
+    H = _h(w.pattern, w.values)
+    C = H.spgemm(H, 1e30)
+    assert C.info.nblk == 0 and C.nnz == 0
+    X = torch.randn(C.shape[1], 3, dtype=torch.float64, device="cuda:0")
+    assert torch.count_nonzero(C.spmm(X)) == 0
+    pe = BlockPattern(w.pattern.row_bsize, w.pattern.col_bsize,
+                      np.zeros(len(w.pattern.row_bsize) + 1, np.int64), np.zeros(0, np.int32))
+    E = _h(pe, np.zeros(0))
+    for P in (E.spgemm(H), H.spgemm(E)):
+        assert P.info.nblk == 0
