@@ -101,10 +101,15 @@ typedef enum {
                                      per warp and dominates a launch of few waves)     */
     VBCSR_SCHED_MMA_STAGED = 2,   /* flag: the tensor-core forward kernel stages value
                                      panels in shared memory with bulk async copies   */
-    VBCSR_SCHED_NO_CSR = 4        /* flag: a CSR-backend operator uses the block-row
+    VBCSR_SCHED_NO_CSR = 4,       /* flag: a CSR-backend operator uses the block-row
                                      kernels instead of the scalar kernel (which
                                      otherwise serves its forward products under
                                      either schedule)                                  */
+    VBCSR_SCHED_NO_RING = 8       /* flag: the persistent CUDA-core forward kernel on
+                                     FP32 values (FP32 operators, the F32 mode) reads
+                                     them directly instead of through its ring of
+                                     asynchronous shared-memory copies, which it
+                                     otherwise uses at k >= 8                          */
 } vbcsr_schedule;
 
 /* Flags of vbcsr_autotune. */
@@ -454,7 +459,8 @@ int vbcsr_shape_classes(const vbcsr_t *A, int32_t *bi, int32_t *bj, int64_t *cou
  *  vbcsr_set_tuning         the same kc and warps for every bucket
  *  vbcsr_set_bucket_tuning  one bucket (B = 0: every bucket)
  *  vbcsr_set_schedule       VBCSR_SCHED_BUCKETED or VBCSR_SCHED_PERSISTENT, optionally
- *                           OR VBCSR_SCHED_MMA_STAGED, and the CTA width of the
+ *                           OR VBCSR_SCHED_MMA_STAGED, VBCSR_SCHED_NO_CSR and
+ *                           VBCSR_SCHED_NO_RING, and the CTA width of the
  *                           persistent launch (0 = 4)
  *  vbcsr_get_tuning         reads them back: kc_by_b[17], warps_by_b[17] (index = B;
  *                           any pointer may be NULL)

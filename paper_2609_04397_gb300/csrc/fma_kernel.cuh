@@ -28,6 +28,13 @@ namespace vbcsr {
 template <typename T>
 __device__ __forceinline__ T ld_ro(const T *p) { return __ldg(p); }
 
+// 16 bytes from global to shared memory, asynchronously (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
 __device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
 
@@ -144,9 +151,9 @@ __device__ __forceinline__ TA reduce_scatter32(const TA (&acc)[B], int lane) {
     return r;
 }
 
-template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true>
+template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true, bool RING = false>
 __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &w, int KC, int32_t *s_x,
-                                             int64_t *s_a, int lane, double &dot) {
+                                             int64_t *s_a, float *s_ring, int lane, double &dot) {
     const int TG = 32 / KC;
     const int cl = lane % KC;
     const int tg = lane / KC;
@@ -165,6 +172,71 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
             for (int t0 = 0; t0 < w.K; t0 += kKMax) {
                 const int tn = min(kKMax, w.K - t0);
                 if (c0 == 0 || w.K > kKMax) stage_columns<TRANS>(a, w, t0, tn, s_x, s_a, lane);
+                if constexpr (!TRANS && sizeof(TV) == 4 && RING) {
+                    if (KC >= 4) {
+                        // FP32 values through a ring of kRingStages stages of kRingCols
+                        // panel columns in shared memory, filled by asynchronous 16-byte
+                        // copies two stages ahead: with wide column tiles (the host picks
+                        // this form for k >= 8) each step covers few panel columns, and
+                        // loading the values in the step left too few bytes in flight to
+                        // cover the DRAM latency. Lanes read their four columns of every
+                        // row from the stage (lanes of one column group share the address).
+                        const int ncs = (tn + kRingCols - 1) / kRingCols;
+                        auto issue = [&](int si) {
+                            if (si < ncs) {
+                                float *dst = s_ring + (si % kRingStages) * (16 * kRingCols);
+                                for (int q = lane; q < B * (kRingCols / 4); q += 32) {
+                                    const int p = q / (kRingCols / 4), col = si * kRingCols + (q % (kRingCols / 4)) * 4;
+                                    float *d = dst + p * kRingCols + (col - si * kRingCols);
+                                    if (t0 + col < w.Kp)   // Kp is a multiple of 4: the chunk is inside the row
+                                        cp_async16(d, vals + w.vbase + (int64_t)p * w.Kp + t0 + col);
+                                    else
+                                        *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                                }
+                            }
+                            asm volatile("cp.async.commit_group;" ::: "memory");
+                        };
+                        // X of the lane's next four columns is loaded before the current
+                        // columns' multiply-adds (one group ahead, in registers)
+                        auto load_x = [&](int t, TA (&x)[4]) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const int xr = (t + j < tn) ? s_x[t + j] : -1;
+                                x[j] = (cv && xr >= 0) ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
+                            }
+                        };
+                        __syncwarp();
+                        issue(0);
+                        issue(1);
+                        TA x[4];
+                        load_x(4 * tg, x);
+                        for (int si = 0; si < ncs; ++si) {
+                            issue(si + 2);
+                            asm volatile("cp.async.wait_group 2;" ::: "memory");
+                            __syncwarp();
+                            const float *st = s_ring + (si % kRingStages) * (16 * kRingCols);
+                            for (int tt = 4 * tg; tt < kRingCols; tt += 4 * TG) {
+                                const int t = si * kRingCols + tt;
+                                TA xn[4];
+                                load_x(t + 4 * TG, xn);
+#pragma unroll
+                                for (int p = 0; p < B; ++p) {
+                                    const float4 q = *reinterpret_cast<const float4 *>(st + p * kRingCols + tt);
+                                    acc[p] = fmat((TA)q.x, x[0], acc[p]);
+                                    acc[p] = fmat((TA)q.y, x[1], acc[p]);
+                                    acc[p] = fmat((TA)q.z, x[2], acc[p]);
+                                    acc[p] = fmat((TA)q.w, x[3], acc[p]);
+                                }
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) x[j] = xn[j];
+                            }
+                            __syncwarp();
+                        }
+                        asm volatile("cp.async.wait_all;" ::: "memory");
+                        __syncwarp();
+                        continue;
+                    }
+                }
                 if (!TRANS && sizeof(TV) == 4) {
                     // FP32 values: four consecutive panel columns per lane and step, one
                     // 16-byte load per row (rows start 16-byte aligned; Kp is a multiple
@@ -298,7 +370,7 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     double dot = 0.0;
     for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, lane, dot);
+        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, nullptr, lane, dot);
     }
     if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
@@ -307,7 +379,7 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
 // order (the planner sorts them by descending cost); warps take the next
 // item from a device counter (a.queue, zeroed before the launch) or, without
 // a queue, round-robin. a.kc_of(B) is the column tile of row count B.
-template <bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true>
+template <bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool WIDE = true, bool RING = false>
 __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
@@ -316,6 +388,8 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
     int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
+    float *s_ring = reinterpret_cast<float *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
+                    (size_t)warp * (kRingBytes / sizeof(float));   // forward launches with RING only
     double dot = 0.0;
     int64_t it = (int64_t)blockIdx.x * warps + warp;
     for (;;) {
@@ -328,7 +402,7 @@ __global__ void __launch_bounds__(256, 2) fma_persistent_kernel(ProdArgs a) {
         const WorkItem w = a.items[it];
         const int kc = a.kc_of(w.B);
 #define VBCSR_ITEM_CASE(NB) \
-    case NB: process_item<NB, TRANS, TV, TA, TX, TXI, WIDE>(a, w, kc, s_x, s_a, lane, dot); break;
+    case NB: process_item<NB, TRANS, TV, TA, TX, TXI, WIDE, RING>(a, w, kc, s_x, s_a, s_ring, lane, dot); break;
         switch (w.B) {
             VBCSR_ITEM_CASE(1) VBCSR_ITEM_CASE(2) VBCSR_ITEM_CASE(3) VBCSR_ITEM_CASE(4)
             VBCSR_ITEM_CASE(5) VBCSR_ITEM_CASE(6) VBCSR_ITEM_CASE(7) VBCSR_ITEM_CASE(8)
@@ -361,18 +435,27 @@ inline cudaError_t launch_smem_opt_in(K kernel, size_t smem) {
 // narrow form distinct from the wide one.
 template <typename TV, typename TA>
 constexpr bool kHasNarrowForm = sizeof(TV) == 8 && !(sizeof(TA) == 8 && alignof(TA) == 8);
+// FP32 values have a form that reads them through a shared-memory ring
+template <typename TV>
+constexpr bool kHasRingForm = sizeof(TV) == 4;
 
 // narrow: the persistent forward kernel in its narrow form (process_item's
 // WIDE = false), for operators with many row counts.
 template <typename TV, typename TA, typename TX, typename TXI>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s, bool narrow = false) {
     const int threads = a.warps * 32;
-    const size_t smem = fma_smem_bytes(trans, a.warps);
+    const size_t smem = fma_smem_bytes(trans, a.warps, B == 0 && !trans && a.value_ring && kHasRingForm<TV>);
     cudaError_t e;
     if (B == 0) {   // persistent launch over every row count
         if (trans) {
             if ((e = launch_smem_opt_in(fma_persistent_kernel<true, TV, TA, TX, TXI>, smem)) != cudaSuccess) return e;
             fma_persistent_kernel<true, TV, TA, TX, TXI><<<a.grid, threads, smem, s>>>(a);
+        } else if (a.value_ring && kHasRingForm<TV>) {
+            if constexpr (kHasRingForm<TV>) {
+                auto k = fma_persistent_kernel<false, TV, TA, TX, TXI, true, true>;
+                if ((e = launch_smem_opt_in(k, smem)) != cudaSuccess) return e;
+                k<<<a.grid, threads, smem, s>>>(a);
+            }
         } else if (narrow && kHasNarrowForm<TV, TA>) {
             if constexpr (kHasNarrowForm<TV, TA>) {
                 auto k = fma_persistent_kernel<false, TV, TA, TX, TXI, false>;
@@ -411,9 +494,11 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
 // The kernel a launch runs (persistent, or the bucket kernel of row count B),
 // for its occupancy-derived grid size.
 template <typename TV, typename TA, typename TX, typename TXI>
-const void *fma_kernel_ptr(bool trans, bool persistent, int B, bool narrow = false) {
+const void *fma_kernel_ptr(bool trans, bool persistent, int B, bool narrow = false, bool ring = false) {
     if (persistent) {
         if (trans) return (const void *)fma_persistent_kernel<true, TV, TA, TX, TXI>;
+        if constexpr (kHasRingForm<TV>)
+            if (ring) return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, true, true>;
         if constexpr (kHasNarrowForm<TV, TA>)
             if (narrow) return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, false>;
         return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;

@@ -92,6 +92,7 @@ struct ProdArgs {
     long long *queue;       // device work counter, zero at launch (NULL: round-robin)
     uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
     int mma_staged;         // tensor-core forward: 1 = value panels staged in shared memory
+    int value_ring;         // CUDA-core forward, FP32 values, k >= 4: read them through the ring
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
@@ -186,7 +187,11 @@ cudaError_t launch_compact(bool f64, int64_t n, const int64_t *keep_src, const i
 // query failed (the error stays pending for the caller to read).
 int max_resident_ctas(const void *kernel, int threads, size_t smem);
 
-size_t fma_smem_bytes(bool trans, int warps);
+// value ring of the FP32-value forward kernel: stages of kRingCols panel columns
+// of up to 16 rows, per warp
+constexpr int kRingStages = 3, kRingCols = 32;
+constexpr int kRingBytes = kRingStages * 16 * kRingCols * 4;
+size_t fma_smem_bytes(bool trans, int warps, bool ring = false);
 // forward products of an FP64 operator in a tensor-core mode on the CUDA cores
 cudaError_t launch_fma_split(int mode, const ProdArgs &a, cudaStream_t s);
 const void *fma_split_kernel(int mode);

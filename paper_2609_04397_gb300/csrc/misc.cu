@@ -6,8 +6,9 @@
 
 namespace vbcsr {
 
-size_t fma_smem_bytes(bool trans, int warps) {
-    return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0));
+size_t fma_smem_bytes(bool trans, int warps, bool ring) {
+    return (size_t)warps * kKMax * (sizeof(int32_t) + (trans ? sizeof(int64_t) : 0)) +
+           (ring ? (size_t)warps * kRingBytes : 0);
 }
 
 int max_resident_ctas(const void *kernel, int threads, size_t smem) {

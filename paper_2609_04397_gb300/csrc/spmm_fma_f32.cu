@@ -13,11 +13,11 @@ cudaError_t launch_fma_f32_on_f64(int B, bool trans, const ProdArgs &a, cudaStre
     return launch_fma_family<float, float, double, float>(B, trans, a, s);
 }
 
-const void *fma_f32_kernel(bool trans, bool persistent, int B) {
-    return fma_kernel_ptr<float, float, float, float>(trans, persistent, B);
+const void *fma_f32_kernel(bool trans, bool persistent, int B, bool ring) {
+    return fma_kernel_ptr<float, float, float, float>(trans, persistent, B, false, ring);
 }
-const void *fma_f32_on_f64_kernel(bool trans, bool persistent, int B) {
-    return fma_kernel_ptr<float, float, double, float>(trans, persistent, B);
+const void *fma_f32_on_f64_kernel(bool trans, bool persistent, int B, bool ring) {
+    return fma_kernel_ptr<float, float, double, float>(trans, persistent, B, false, ring);
 }
 
 }  // namespace vbcsr

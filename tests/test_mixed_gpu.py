@@ -181,3 +181,24 @@ def test_tensor_core_products_exact_on_small_integers(mode, staged):
             H.spmm(_dev(X), alpha, beta, Yd, precision=mode)
             ref, _ = forward_ref(pat, vals, X, alpha, beta, Y0)
             np.testing.assert_array_equal(Yd.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("k", [8, 13, 32, 40])
+def test_fp32_value_ring_matches_direct_reads(k):
+    """The FP32-value CUDA-core forward kernel reads its values through a
+    shared-memory ring at k >= 8 (default) or directly (schedule flag): the
+    same arithmetic in the same order, so the results agree bit for bit, for an
+    FP32 operator and for the F32 mode of an FP64 operator, on rows taller than
+    16 and panels wider than one staged window."""
+    pat = syn.random_pattern(12, 14, (3, 9, 20, 60), 0.5, 31 + k, empty_rows=1)
+    vals = syn.random_values(pat, 31)
+    X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
+    for dtype, prec in ((torch.float32, "native"), (torch.float64, "f32")):
+        H = _handle(pat, vals.astype(np.float32) if dtype == torch.float32 else vals, dtype)
+        Xd = _dev(X, dtype)
+        got_ring = H.spmm(Xd, precision=prec).cpu().numpy()
+        H.set_schedule("persistent", value_ring=False)
+        got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
+        np.testing.assert_array_equal(got_ring, got_direct)
+        ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
+        check_elementwise(got_ring.astype(np.float64), ref, scale, 1e-4)
