@@ -983,13 +983,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.err = A->err;
     a.debug_checks = A->debug_checks;
     const int kc_auto = auto_kc(k);
-    // FP32 values in the persistent CUDA-core forward kernel with column tiles of
-    // 8 or more go through the shared-memory ring unless the schedule opts out
+    // FP32 values in the CUDA-core forward kernels with column tiles of 8 or more
+    // go through the shared-memory ring unless the schedule opts out
     // (measured on the 50k-atom operator: 10 / 20 / 18 % faster at k = 8 / 16 /
     // 32, 1.5 % slower at k = 4)
     a.value_ring = fma && !trans && !cplx && (mode == VBCSR_PREC_F32 || (!f64 && mode == VBCSR_PREC_NATIVE)) &&
-                           (A->schedule & VBCSR_SCHED_PERSISTENT) && !(A->schedule & VBCSR_SCHED_NO_RING) &&
-                           kc_auto >= 8
+                           !(A->schedule & VBCSR_SCHED_NO_RING) && kc_auto >= 8
                        ? 1
                        : 0;
     auto kc_for = [&](int B) { return A->kc_b[B] ? std::min(A->kc_b[B], kc_auto) : kc_auto; };
@@ -1036,7 +1035,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         return VBCSR_OK;
     };
     auto fma_kern = [&](bool persistent, int B) {
-        const bool ring = persistent && a.value_ring;
+        const bool ring = a.value_ring != 0;
         if (cplx) return fma_c128_kernel(trans, persistent, B);
         if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B, df_narrow);
         return (mode == VBCSR_PREC_NATIVE)
@@ -1101,7 +1100,8 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         for (const Bucket &b : buckets) {
             a.kc = kc_for(b.B);
             const int warps = A->warps_b[b.B] ? A->warps_b[b.B] : 4;
-            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false, b.B), fma_smem_bytes(trans, warps));
+            rc = launch(b.B, items + b.begin, b.count, warps, fma_kern(false, b.B),
+                        fma_smem_bytes(trans, warps, a.value_ring != 0));
             if (rc) return rc;
         }
     }

@@ -358,7 +358,7 @@ __device__ __forceinline__ void finish_dot(const ProdArgs &a, double dot, int wa
     }
 }
 
-template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI>
+template <int B, bool TRANS, typename TV, typename TA, typename TX, typename TXI, bool RING = false>
 __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warps = a.warps;
@@ -367,10 +367,12 @@ __global__ void __launch_bounds__(256, 2) fma_product_kernel(ProdArgs a) {
     int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw) + warp * kKMax;
     int64_t *s_a = reinterpret_cast<int64_t *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
                    warp * kKMax;
+    float *s_ring = reinterpret_cast<float *>(smem_raw + (size_t)warps * kKMax * sizeof(int32_t)) +
+                    (size_t)warp * (kRingBytes / sizeof(float));   // forward launches with RING only
     double dot = 0.0;
     for (int64_t it = (int64_t)blockIdx.x * warps + warp; it < a.n_items; it += (int64_t)gridDim.x * warps) {
         const WorkItem w = a.items[it];
-        process_item<B, TRANS, TV, TA, TX, TXI>(a, w, a.kc, s_x, s_a, nullptr, lane, dot);
+        process_item<B, TRANS, TV, TA, TX, TXI, true, RING>(a, w, a.kc, s_x, s_a, s_ring, lane, dot);
     }
     if (a.partials) finish_dot(a, dot, warp, lane, warps);
 }
@@ -444,7 +446,8 @@ constexpr bool kHasRingForm = sizeof(TV) == 4;
 template <typename TV, typename TA, typename TX, typename TXI>
 cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t s, bool narrow = false) {
     const int threads = a.warps * 32;
-    const size_t smem = fma_smem_bytes(trans, a.warps, B == 0 && !trans && a.value_ring && kHasRingForm<TV>);
+    const bool ring = !trans && a.value_ring && kHasRingForm<TV>;
+    const size_t smem = fma_smem_bytes(trans, a.warps, ring);
     cudaError_t e;
     if (B == 0) {   // persistent launch over every row count
         if (trans) {
@@ -470,6 +473,14 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
     }
 #define VBCSR_FMA_CASE(NB)                                                                               \
     case NB:                                                                                             \
+        if constexpr (kHasRingForm<TV>) {                                                                \
+            if (ring) {                                                                                  \
+                auto k = fma_product_kernel<NB, false, TV, TA, TX, TXI, true>;                           \
+                if ((e = launch_smem_opt_in(k, smem)) != cudaSuccess) return e;                          \
+                k<<<a.grid, threads, smem, s>>>(a);                                                      \
+                break;                                                                                   \
+            }                                                                                            \
+        }                                                                                                \
         if (trans) {                                                                                     \
             if ((e = launch_smem_opt_in(fma_product_kernel<NB, true, TV, TA, TX, TXI>, smem)) != cudaSuccess) \
                 return e;                                                                                \
@@ -505,6 +516,8 @@ const void *fma_kernel_ptr(bool trans, bool persistent, int B, bool narrow = fal
     }
 #define VBCSR_PTR_CASE(NB)                                                                 \
     case NB:                                                                               \
+        if constexpr (kHasRingForm<TV>)                                                    \
+            if (ring && !trans) return (const void *)fma_product_kernel<NB, false, TV, TA, TX, TXI, true>; \
         return trans ? (const void *)fma_product_kernel<NB, true, TV, TA, TX, TXI>         \
                      : (const void *)fma_product_kernel<NB, false, TV, TA, TX, TXI>;
     switch (B) {

@@ -196,9 +196,11 @@ def test_fp32_value_ring_matches_direct_reads(k):
     for dtype, prec in ((torch.float32, "native"), (torch.float64, "f32")):
         H = _handle(pat, vals.astype(np.float32) if dtype == torch.float32 else vals, dtype)
         Xd = _dev(X, dtype)
-        got_ring = H.spmm(Xd, precision=prec).cpu().numpy()
-        H.set_schedule("persistent", value_ring=False)
-        got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
-        np.testing.assert_array_equal(got_ring, got_direct)
         ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
-        check_elementwise(got_ring.astype(np.float64), ref, scale, 1e-4)
+        for sch in ("persistent", "bucketed"):
+            H.set_schedule(sch)
+            got_ring = H.spmm(Xd, precision=prec).cpu().numpy()
+            H.set_schedule(sch, value_ring=False)
+            got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
+            np.testing.assert_array_equal(got_ring, got_direct)
+            check_elementwise(got_ring.astype(np.float64), ref, scale, 1e-4)
