@@ -403,7 +403,7 @@ def ops_section(H, pat, values, dev, steps):
     vectors (29 products with the fused moment dot, checkpoints every 10
     steps), then the same through the differentiable moments with the reverse
     recurrence (adjoint products, recomputed segments, pattern-sampled
-    products)."""
+    products), and the 30 moments by the doubling identities (15 products)."""
     import torch
     from paper_2609_04397_gb300 import VBCSR, chebyshev_moments
     reps = max(5, steps // 10)
@@ -444,6 +444,10 @@ def ops_section(H, pat, values, dev, steps):
     R = torch.randint(0, 2, (pat.n_rows, k), generator=g, device=dev).to(torch.float64) * 2 - 1
     fwd = timed(lambda: Ht.chebyshev(R, M, ckpt_every=10), n=3)
     res["chebyshev_k16_m30"] = {**rate(2.0 * pat.nnz * k * (M - 1), fwd), "ms_per_product": fwd / (M - 1)}
+    # the same 30 moments by the doubling identities (Sec. V): 15 products
+    kpm = timed(lambda: Ht.kpm_moments(R, M), n=3)
+    res["kpm_moments_k16_m30"] = {**rate(2.0 * pat.nnz * k * (M // 2), kpm), "products": M // 2,
+                                  "speedup_vs_recurrence": fwd / kpm}
     vt = Ht.get_values().requires_grad_(True)
 
     def fwd_bwd():
