@@ -838,7 +838,7 @@ namespace vbcsr {
 const void *fma_f64_kernel(bool trans, bool persistent, int B);
 const void *fma_f32_kernel(bool trans, bool persistent, int B, bool ring);
 const void *fma_f32_on_f64_kernel(bool trans, bool persistent, int B, bool ring);
-const void *fma_df_kernel(bool trans, bool persistent, int B, bool narrow);
+const void *fma_df_kernel(bool trans, bool persistent, int B, bool narrow, bool ring);
 const void *mma_kernel_ptr(int mode, bool xdouble, bool trans, bool staged, int64_t k);
 }  // namespace vbcsr
 
@@ -983,11 +983,16 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.err = A->err;
     a.debug_checks = A->debug_checks;
     const int kc_auto = auto_kc(k);
-    // FP32 values in the CUDA-core forward kernels with column tiles of 8 or more
-    // go through the shared-memory ring unless the schedule opts out
-    // (measured on the 50k-atom operator: 10 / 20 / 18 % faster at k = 8 / 16 /
-    // 32, 1.5 % slower at k = 4)
-    a.value_ring = fma && !trans && !cplx && (mode == VBCSR_PREC_F32 || (!f64 && mode == VBCSR_PREC_NATIVE)) &&
+    // FP32 values and double-FP32 pairs in the CUDA-core forward kernels with
+    // column tiles of 8 or more go through the shared-memory ring unless the
+    // schedule opts out. Measured on the 50k-atom operator: FP32 10 / 20 / 18 %
+    // and double-FP32 8 / 8 / 5 % faster at k = 8 / 16 / 32 (FP32 1.5 % slower at
+    // k = 4); double-FP32 in one persistent launch over many row counts (nine on
+    // the variable-block domain) 6-18 % slower, so not there.
+    const bool many_heights = A->fwd_buckets.size() > 2 && (A->schedule & VBCSR_SCHED_PERSISTENT);
+    a.value_ring = fma && !trans && !cplx &&
+                           (mode == VBCSR_PREC_F32 || (mode == VBCSR_PREC_DF32 && !many_heights) ||
+                            (!f64 && mode == VBCSR_PREC_NATIVE)) &&
                            !(A->schedule & VBCSR_SCHED_NO_RING) && kc_auto >= 8
                        ? 1
                        : 0;
@@ -1037,7 +1042,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     auto fma_kern = [&](bool persistent, int B) {
         const bool ring = a.value_ring != 0;
         if (cplx) return fma_c128_kernel(trans, persistent, B);
-        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B, df_narrow);
+        if (mode == VBCSR_PREC_DF32) return fma_df_kernel(trans, persistent, B, df_narrow, ring);
         return (mode == VBCSR_PREC_NATIVE)
                    ? (f64 ? fma_f64_kernel(trans, persistent, B) : fma_f32_kernel(trans, persistent, B, ring))
                    : fma_f32_on_f64_kernel(trans, persistent, B, ring);

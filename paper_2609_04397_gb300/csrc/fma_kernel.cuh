@@ -21,6 +21,8 @@
 // on B per item) that takes items from a work queue in descending-cost order.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace vbcsr {
@@ -261,6 +263,72 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                     }
                     continue;
                 }
+                if constexpr (!TRANS && sizeof(TV) == 8 && RING) {
+                    if (KC >= 4) {
+                        // double-FP32 pairs through the ring (as the FP32 values above:
+                        // stages of kRingCols / 2 panel columns of 8-byte values filled
+                        // by asynchronous 16-byte copies two stages ahead), CPL columns per
+                        // lane as below, X one column group ahead
+                        constexpr int RC = kRingCols / 2;
+                        constexpr int CPL = (WIDE && B <= 13) ? 4 : 2;
+                        TV *ring = reinterpret_cast<TV *>(s_ring);
+                        const int ncs = (tn + RC - 1) / RC;
+                        auto issue = [&](int si) {
+                            if (si < ncs) {
+                                TV *dst = ring + (si % kRingStages) * (16 * RC);
+                                for (int q = lane; q < B * (RC / 2); q += 32) {
+                                    const int p = q / (RC / 2), col = si * RC + (q % (RC / 2)) * 2;
+                                    TV *d = dst + p * RC + (col - si * RC);
+                                    if (t0 + col < w.Kp)   // Kp is even: the pair is inside the row
+                                        cp_async16(d, vals + w.vbase + (int64_t)p * w.Kp + t0 + col);
+                                    else
+                                        *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
+                                }
+                            }
+                            asm volatile("cp.async.commit_group;" ::: "memory");
+                        };
+                        auto load_x = [&](int t, TA (&x)[CPL]) {
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j) {
+                                const int xr = (t + j < tn) ? s_x[t + j] : -1;
+                                x[j] = (cv && xr >= 0) ? (TA)ld_ro(X + (int64_t)xr * a.ldx + c) : (TA)0;
+                            }
+                        };
+                        __syncwarp();
+                        issue(0);
+                        issue(1);
+                        TA x[CPL];
+                        load_x(CPL * tg, x);
+                        for (int si = 0; si < ncs; ++si) {
+                            issue(si + 2);
+                            asm volatile("cp.async.wait_group 2;" ::: "memory");
+                            __syncwarp();
+                            const TV *st = ring + (si % kRingStages) * (16 * RC);
+                            for (int tt = CPL * tg; tt < RC; tt += CPL * TG) {
+                                const int t = si * RC + tt;
+                                TA xn[CPL];
+                                load_x(t + CPL * TG, xn);
+#pragma unroll
+                                for (int p = 0; p < B; ++p) {
+#pragma unroll
+                                    for (int h = 0; h < CPL; h += 2) {
+                                        const uint4 q = *reinterpret_cast<const uint4 *>(st + p * RC + tt + h);
+                                        TV v2[2];
+                                        memcpy(v2, &q, sizeof(v2));
+                                        acc[p] = fmat((TA)v2[0], x[h], acc[p]);
+                                        acc[p] = fmat((TA)v2[1], x[h + 1], acc[p]);
+                                    }
+                                }
+#pragma unroll
+                                for (int j = 0; j < CPL; ++j) x[j] = xn[j];
+                            }
+                            __syncwarp();
+                        }
+                        asm volatile("cp.async.wait_all;" ::: "memory");
+                        __syncwarp();
+                        continue;
+                    }
+                }
                 if (!TRANS && sizeof(TV) == 8) {
                     // 8-byte values (FP64, double-FP32 pairs): CPL consecutive panel columns
                     // per lane and step, 16-byte loads (rows start 32-byte aligned and Kp is
@@ -437,9 +505,10 @@ inline cudaError_t launch_smem_opt_in(K kernel, size_t smem) {
 // narrow form distinct from the wide one.
 template <typename TV, typename TA>
 constexpr bool kHasNarrowForm = sizeof(TV) == 8 && !(sizeof(TA) == 8 && alignof(TA) == 8);
-// FP32 values have a form that reads them through a shared-memory ring
+// FP32 values and double-FP32 pairs have a form that reads them through a
+// shared-memory ring (FP64 is bound by its arithmetic, not by the loads)
 template <typename TV>
-constexpr bool kHasRingForm = sizeof(TV) == 4;
+constexpr bool kHasRingForm = sizeof(TV) == 4 || std::is_same<TV, float2>::value;
 
 // narrow: the persistent forward kernel in its narrow form (process_item's
 // WIDE = false), for operators with many row counts.
@@ -456,6 +525,8 @@ cudaError_t launch_fma_family(int B, bool trans, const ProdArgs &a, cudaStream_t
         } else if (a.value_ring && kHasRingForm<TV>) {
             if constexpr (kHasRingForm<TV>) {
                 auto k = fma_persistent_kernel<false, TV, TA, TX, TXI, true, true>;
+                if constexpr (kHasNarrowForm<TV, TA>)
+                    if (narrow) k = fma_persistent_kernel<false, TV, TA, TX, TXI, false, true>;
                 if ((e = launch_smem_opt_in(k, smem)) != cudaSuccess) return e;
                 k<<<a.grid, threads, smem, s>>>(a);
             }
@@ -509,7 +580,11 @@ const void *fma_kernel_ptr(bool trans, bool persistent, int B, bool narrow = fal
     if (persistent) {
         if (trans) return (const void *)fma_persistent_kernel<true, TV, TA, TX, TXI>;
         if constexpr (kHasRingForm<TV>)
-            if (ring) return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, true, true>;
+            if (ring) {
+                if constexpr (kHasNarrowForm<TV, TA>)
+                    if (narrow) return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, false, true>;
+                return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, true, true>;
+            }
         if constexpr (kHasNarrowForm<TV, TA>)
             if (narrow) return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI, false>;
         return (const void *)fma_persistent_kernel<false, TV, TA, TX, TXI>;

@@ -12,8 +12,8 @@ cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s, 
     return launch_fma_family<float2, DF, double, float2>(B, trans, a, s, narrow);
 }
 
-const void *fma_df_kernel(bool trans, bool persistent, int B, bool narrow) {
-    return fma_kernel_ptr<float2, DF, double, float2>(trans, persistent, B, narrow);
+const void *fma_df_kernel(bool trans, bool persistent, int B, bool narrow, bool ring) {
+    return fma_kernel_ptr<float2, DF, double, float2>(trans, persistent, B, narrow, ring);
 }
 
 // hi/lo split of FP64 values into FP32 pairs

@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import synthetic as syn
-from _parity import TOL_MIXED, adjoint_ref, check_elementwise, forward_ref, rel_fro
+from _parity import TOL_F64, TOL_MIXED, adjoint_ref, check_elementwise, forward_ref, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -185,15 +185,16 @@ def test_tensor_core_products_exact_on_small_integers(mode, staged):
 
 @pytest.mark.parametrize("k", [8, 13, 32, 40])
 def test_fp32_value_ring_matches_direct_reads(k):
-    """The FP32-value CUDA-core forward kernel reads its values through a
-    shared-memory ring at k >= 8 (default) or directly (schedule flag): the
-    same arithmetic in the same order, so the results agree bit for bit, for an
-    FP32 operator and for the F32 mode of an FP64 operator, on rows taller than
-    16 and panels wider than one staged window."""
+    """The CUDA-core forward kernel on FP32 values or double-FP32 pairs reads
+    them through a shared-memory ring at k >= 8 (default) or directly
+    (schedule flag): the same arithmetic in the same order, so the results
+    agree bit for bit, for an FP32 operator and for the F32 and DF32 modes of
+    an FP64 operator, on rows taller than 16 and panels wider than one staged
+    window."""
     pat = syn.random_pattern(12, 14, (3, 9, 20, 60), 0.5, 31 + k, empty_rows=1)
     vals = syn.random_values(pat, 31)
     X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
-    for dtype, prec in ((torch.float32, "native"), (torch.float64, "f32")):
+    for dtype, prec in ((torch.float32, "native"), (torch.float64, "f32"), (torch.float64, "df32")):
         H = _handle(pat, vals.astype(np.float32) if dtype == torch.float32 else vals, dtype)
         Xd = _dev(X, dtype)
         ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
@@ -203,4 +204,4 @@ def test_fp32_value_ring_matches_direct_reads(k):
             H.set_schedule(sch, value_ring=False)
             got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
             np.testing.assert_array_equal(got_ring, got_direct)
-            check_elementwise(got_ring.astype(np.float64), ref, scale, 1e-4)
+            check_elementwise(got_ring.astype(np.float64), ref, scale, TOL_F64 if prec == "df32" else 1e-4)
