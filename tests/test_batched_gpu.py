@@ -125,3 +125,21 @@ def test_batched_rejects_bad_local_columns():
         VBCSR.from_batched([0, 1, 2], [0, 1, 2], pat.row_bsize, pat.col_bsize, pat.block_row_ptr,
                            np.array([0, 1]), np.ones(8), torch.float64, "cuda:0")
     assert ei.value.status == -2
+
+
+def test_schedule_flags_round_trip_and_validation():
+    """Every schedule flag reads back through get_tuning and survives
+    apply_tuning; an unknown bit or a bad CTA width is rejected."""
+    from paper_2609_04397_gb300 import VBCSR, lib
+    w = syn.tiny_multispecies(0)
+    H = VBCSR.from_pattern(w.pattern, w.values, torch.float64, "cuda:0")
+    H.set_schedule("bucketed", 2, mma_staged=True, scalar_kernel=False, value_ring=False)
+    t = H.get_tuning()
+    assert (t["schedule"], t["mma_staged"], t["scalar_kernel"], t["value_ring"]) == ("bucketed", True, False, False)
+    H.set_schedule("persistent")
+    H.apply_tuning(t)
+    assert H.get_tuning()["value_ring"] is False and H.get_tuning()["scalar_kernel"] is False
+    for bad in (16, -1):
+        assert lib().vbcsr_set_schedule(H.handle, bad, 0) != 0
+    assert lib().vbcsr_set_schedule(H.handle, 1, 3) != 0
+    assert lib().vbcsr_set_schedule(H.handle, 1 | 2 | 4 | 8, 4) == 0
