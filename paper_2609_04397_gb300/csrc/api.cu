@@ -520,9 +520,10 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
 
     // value pages
     unsigned char *panel = nullptr;
-    CUDA_TRY(A->alloc(&panel, (size_t)A->panel_elems * A->esize), "alloc value pages");
+    // two elements of slack after the pages: the adjoint reads 8-byte values in aligned pairs
+    CUDA_TRY(A->alloc(&panel, (size_t)(A->panel_elems + 2) * A->esize), "alloc value pages");
     A->panel = panel;
-    CUDA_TRY(cudaMemsetAsync(A->panel, 0, (size_t)A->panel_elems * A->esize, s), "memset");
+    CUDA_TRY(cudaMemsetAsync(A->panel, 0, (size_t)(A->panel_elems + 2) * A->esize, s), "memset");
     if (A->nnz > 0 && values) {
         const void *src = values;
         void *staged = nullptr;
@@ -745,7 +746,7 @@ static int refresh_panel32(vbcsr_t *A, cudaStream_t s) {
 }
 
 static int refresh_paneldf(vbcsr_t *A, cudaStream_t s) {
-    if (!A->paneldf) CUDA_TRY(A->alloc(&A->paneldf, (size_t)A->panel_elems), "alloc double-FP32 value copy");
+    if (!A->paneldf) CUDA_TRY(A->alloc(&A->paneldf, (size_t)A->panel_elems + 2), "alloc double-FP32 value copy");
     CUDA_TRY(launch_split_df(A->panel_elems, 1, (const double *)A->panel, 1, A->paneldf, s), "split values");
     A->paneldf_valid = true;
     return VBCSR_OK;

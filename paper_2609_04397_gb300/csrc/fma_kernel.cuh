@@ -375,6 +375,25 @@ __device__ __forceinline__ void process_item(const ProdArgs &a, const WorkItem &
                         const int64_t kp = w.Kp;
 #pragma unroll
                         for (int p = 0; p < B; ++p) acc[p] = fmat((TA)ld_ro(v + p * kp), x, acc[p]);
+                    } else if constexpr (sizeof(TV) == 8) {
+                        // 8-byte values: the B values of the column (contiguous, any
+                        // parity) come from the aligned 16-byte pairs that cover them, half
+                        // the load requests of one load per value; a select picks each
+                        // value by the start's parity (the pages carry two elements of
+                        // slack after their end for the last pair)
+                        const TV *v = vals + s_a[t];
+                        const bool odd = (reinterpret_cast<uintptr_t>(v) & 15) != 0;
+                        const uint4 *vp = reinterpret_cast<const uint4 *>(reinterpret_cast<uintptr_t>(v) &
+                                                                          ~static_cast<uintptr_t>(15));
+                        constexpr int NP = B / 2 + 1;
+                        TV e[2 * NP];
+#pragma unroll
+                        for (int m = 0; m < NP; ++m) {
+                            const uint4 q = __ldg(vp + m);
+                            memcpy(&e[2 * m], &q, sizeof(q));
+                        }
+#pragma unroll
+                        for (int p = 0; p < B; ++p) acc[p] = fmat(adj_val((TA)(odd ? e[p + 1] : e[p])), x, acc[p]);
                     } else {
                         const TV *v = vals + s_a[t];
 #pragma unroll
