@@ -377,3 +377,24 @@ def test_csr_backend_scalar_kernel(density, k):
         H.spmm(X, 2.0, -1.0, Yd, precision=mode)
         assert rel_fro(Yd.cpu().numpy(), ref) <= TOL_MIXED
         check_elementwise(Yd.cpu().numpy(), ref, scale, 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["native", "f32", "df32", "bf16x2", "tf32x3"])
+def test_many_column_passes(precision):
+    """k = 100: several passes of 32 output columns (the last one 4 wide) in
+    every kernel form (the value rings, the tensor-core tiles), forward and
+    adjoint, with leading dimensions above k."""
+    pat = syn.random_pattern(30, 26, (3, 9, 13, 17), 0.25, 91, empty_rows=2, unsorted=True)
+    vals = syn.random_values(pat, 91)
+    H = _handle(pat, vals)
+    rng = np.random.default_rng(91)
+    k = 100
+    X = rng.standard_normal((pat.n_cols, k + 3))
+    got = H.spmm(_dev(X)[:, :k], precision=precision).cpu().numpy()
+    ref, scale = forward_ref(pat, vals, X[:, :k], 1.0, 0.0, None)
+    tol = TOL_F64 if precision in ("native", "df32") else 1e-4
+    check_elementwise(got, ref, scale, tol)
+    Xa = rng.standard_normal((pat.n_rows, k))
+    got = H.spmm_adjoint(_dev(Xa), precision=precision).cpu().numpy()
+    ref, scale = adjoint_ref(pat, vals, Xa, 1.0, 0.0, None)
+    check_elementwise(got, ref, scale, tol)
