@@ -19,6 +19,11 @@
 // Two launch shapes share the per-item code: one launch per row count B over
 // the items of that count, and one persistent launch over all items (a switch
 // on B per item) that takes items from a work queue in descending-cost order.
+// Kernel forms (template flags): WIDE (double-FP32 pairs read four columns per
+// lane for items of up to 13 rows, else two) and RING (FP32 values and
+// double-FP32 pairs streamed through a ring of shared-memory stages filled by
+// asynchronous copies, for wide column tiles); the host picks them from the
+// operator's row counts and k.
 #pragma once
 
 #include <type_traits>
