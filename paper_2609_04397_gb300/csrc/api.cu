@@ -242,6 +242,23 @@ static int validate_pattern(int64_t n_brows, int64_t n_bcols, const int32_t *row
 
 static int ceil_to(int64_t v, int m) { return (int)((v + m - 1) / m * m); }
 
+// f(begin, end) over [0, n) split into contiguous ranges on up to 16 host
+// threads (one thread below `grain` items per thread); f must only write what
+// its own range owns
+template <typename F>
+static void host_parallel(int64_t n, int64_t grain, F f) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, n / grain}));
+    if (nt == 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < nt; ++t) pool.emplace_back([&, t]() { f(n * t / nt, n * (t + 1) / nt); });
+    f((int64_t)0, n / nt);
+    for (auto &th : pool) th.join();
+}
+
 // Longest-processing-time order for the persistent launch: the costliest
 // items (rows x virtual columns) first, so that the queue ends with small ones.
 static void sort_by_cost(std::vector<WorkItem> &items) {
@@ -383,21 +400,23 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     // plan block list
     std::vector<int32_t> fl_xrow(nblk), fl_pcol(nblk), fl_w(nblk), fl_kp(nblk), fl_bi(nblk);
     std::vector<int64_t> fl_uoff(nblk), fl_pbase(nblk), prow_ptr(block_row_ptr, block_row_ptr + n_brows + 1);
-    for (int64_t i = 0; i < n_brows; ++i) {
-        int64_t pc = 0;
-        for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
-            const int32_t u = perm[l];
-            const int32_t j = block_col_idx[u];
-            fl_xrow[l] = (int32_t)A->col_off[j];
-            fl_pcol[l] = (int32_t)pc;
-            fl_w[l] = col_bsize[j];
-            fl_kp[l] = (int32_t)Kp[i];
-            fl_bi[l] = row_bsize[i];
-            fl_uoff[l] = A->uoff[u];
-            fl_pbase[l] = poff[i] + pc;
-            pc += col_bsize[j];
+    host_parallel(n_brows, 4096, [&](int64_t i0, int64_t i1) {   // block rows own their list ranges
+        for (int64_t i = i0; i < i1; ++i) {
+            int64_t pc = 0;
+            for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
+                const int32_t u = perm[l];
+                const int32_t j = block_col_idx[u];
+                fl_xrow[l] = (int32_t)A->col_off[j];
+                fl_pcol[l] = (int32_t)pc;
+                fl_w[l] = col_bsize[j];
+                fl_kp[l] = (int32_t)Kp[i];
+                fl_bi[l] = row_bsize[i];
+                fl_uoff[l] = A->uoff[u];
+                fl_pbase[l] = poff[i] + pc;
+                pc += col_bsize[j];
+            }
         }
-    }
+    });
 
     // forward work items, bucketed by row count
     {
@@ -438,16 +457,21 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
         std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
         std::vector<int64_t> tl_pbase(nblk);
         std::vector<int32_t> tl_kp(nblk), tl_bi(nblk), tl_xrow(nblk), tl_vcol(nblk);
-        for (int64_t i = 0; i < n_brows; ++i) {           // rows increasing inside each column
-            for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
-                const int32_t j = block_col_idx[perm[l]];
-                const int64_t e = fill[j]++;
-                tl_pbase[e] = fl_pbase[l];
-                tl_kp[e] = (int32_t)Kp[i];
-                tl_bi[e] = row_bsize[i];
-                tl_xrow[e] = (int32_t)A->row_off[i];
+        // rows increasing inside each column: every thread walks all blocks in row
+        // order and places those of its own range of columns
+        host_parallel(n_bcols, 4096, [&](int64_t j0, int64_t j1) {
+            for (int64_t i = 0; i < n_brows; ++i) {
+                for (int64_t l = block_row_ptr[i]; l < block_row_ptr[i + 1]; ++l) {
+                    const int32_t j = block_col_idx[perm[l]];
+                    if (j < j0 || j >= j1) continue;
+                    const int64_t e = fill[j]++;
+                    tl_pbase[e] = fl_pbase[l];
+                    tl_kp[e] = (int32_t)Kp[i];
+                    tl_bi[e] = row_bsize[i];
+                    tl_xrow[e] = (int32_t)A->row_off[i];
+                }
             }
-        }
+        });
         std::vector<int64_t> Kt(n_bcols, 0);
         for (int64_t j = 0; j < n_bcols; ++j) {
             int64_t v = 0;
