@@ -398,3 +398,22 @@ def test_many_column_passes(precision):
     got = H.spmm_adjoint(_dev(Xa), precision=precision).cpu().numpy()
     ref, scale = adjoint_ref(pat, vals, Xa, 1.0, 0.0, None)
     check_elementwise(got, ref, scale, tol)
+
+
+def test_one_launch_per_product_under_the_persistent_schedule():
+    """The bench counts one kernel launch per FP64 product (the default
+    persistent schedule); a profiler trace of one product shows exactly one
+    kernel of the library."""
+    from torch.profiler import ProfilerActivity, profile
+    w = syn.tiny_multispecies(0)
+    H = _handle(w.pattern, w.values)
+    X = _dev(syn.normal_panel(w.pattern.n_cols, 8, 0))
+    Y = torch.empty(w.pattern.n_rows, 8, dtype=torch.float64, device="cuda:0")
+    H.spmm(X, 1.0, 0.0, Y)
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        H.spmm(X, 1.0, 0.0, Y)
+        torch.cuda.synchronize()
+    kernels = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+               and "vbcsr" in e.name]
+    assert len(kernels) == 1 and "fma_persistent_kernel" in kernels[0], kernels
