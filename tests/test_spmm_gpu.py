@@ -411,9 +411,13 @@ def test_one_launch_per_product_under_the_persistent_schedule():
     Y = torch.empty(w.pattern.n_rows, 8, dtype=torch.float64, device="cuda:0")
     H.spmm(X, 1.0, 0.0, Y)
     torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        H.spmm(X, 1.0, 0.0, Y)
-        torch.cuda.synchronize()
-    kernels = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
-               and "vbcsr" in e.name]
+    kernels = []
+    for _ in range(2):   # the first trace of a process can come back before its activity buffers fill
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            H.spmm(X, 1.0, 0.0, Y)
+            torch.cuda.synchronize()
+        kernels = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA
+                   and "vbcsr" in e.name]
+        if kernels:
+            break
     assert len(kernels) == 1 and "fma_persistent_kernel" in kernels[0], kernels
