@@ -64,12 +64,14 @@ typedef enum {
 
 /*
  * Arithmetic of the block products. X, Y, alpha, beta and the epilogue stay in
- * the matrix dtype in every mode; the mixed modes keep an FP32 copy of the
- * values (built on first use, refreshed by vbcsr_set_values) and, for an FP64
- * operator, convert X to FP32 once per call into a buffer the handle owns
- * (allocated on first use and grown when a call needs more; growing it
- * synchronises the stream). Mixed-mode calls on one handle therefore must not
- * overlap on the GPU.
+ * the matrix dtype in every mode; the mixed modes keep a copy of the values in
+ * their own format (FP32; for BF16X2 on an FP64 operator one 32-bit word per
+ * value holding its bf16 hi and lo pieces; for DF32 FP32 pairs), built on
+ * first use and refreshed by vbcsr_set_values and vbcsr_shift_scale, and, for
+ * an FP64 operator, convert X the same way once per call into a buffer the
+ * handle owns (allocated on first use and grown when a call needs more;
+ * growing it synchronises the stream). Mixed-mode calls on one handle
+ * therefore must not overlap on the GPU.
  *  NATIVE  products and accumulation in the matrix dtype (FP64 FMA / FP32 FMA)
  *  F32     values and X rounded to FP32, FP32 FMA, FP32 accumulation
  *  TF32    one TF32 tensor-core product per block product, FP32 accumulation
