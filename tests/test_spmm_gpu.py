@@ -421,3 +421,31 @@ def test_one_launch_per_product_under_the_persistent_schedule():
         if kernels:
             break
     assert len(kernels) == 1 and "fma_persistent_kernel" in kernels[0], kernels
+
+
+def test_registry_with_very_many_block_sizes():
+    """More than 2^20 (row size, column size) combinations take the planner's
+    ordered-map registry instead of its dense count table: 1100 distinct row
+    sizes, 1000 distinct column sizes, a few blocks among them."""
+    nr, nc = 1100, 1000
+    rb = np.arange(1, nr + 1, dtype=np.int32)
+    cb = np.arange(1, nc + 1, dtype=np.int32)
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(40, 12, replace=False))          # small rows and columns keep the values small
+    ptr = np.zeros(nr + 1, np.int64)
+    cols = []
+    for i in range(nr):
+        if i in rows:
+            cols.extend(sorted(rng.choice(30, 2, replace=False).tolist()))
+        ptr[i + 1] = len(cols)
+    pat = BlockPattern(rb, cb, ptr, np.array(cols, np.int32))
+    vals = syn.random_values(pat, 5)
+    H = _handle(pat, vals)
+    expect = {}
+    for bi, bj in zip(pat.row_bsize[pat.block_rows()], pat.col_bsize[pat.block_col_idx]):
+        expect[(int(bi), int(bj))] = expect.get((int(bi), int(bj)), 0) + 1
+    assert H.shape_classes() == [(a, b, expect[(a, b)]) for a, b in sorted(expect)]
+    X = np.random.default_rng(6).standard_normal((pat.n_cols, 2))
+    got = H.spmm(_dev(X)).cpu().numpy()
+    ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
+    check_elementwise(got, ref, scale, TOL_F64)
