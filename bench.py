@@ -350,9 +350,10 @@ def spgemm_section(dev):
     """The thresholded block product C = H H (Eqs. 2-3) of two operators: the
     5k-atom zinc-blende nanoparticle and the variable-block domain at 1/8 of
     its benchmark size, at eps = 0 and at a threshold that drops blocks.
-    Wall time of the whole call (host symbolic stage with the Eq. 3 bound,
-    GPU numeric stage, final filter and compaction, result handle), and the
-    rate of its numeric flops (2 b_i b_k b_j per retained block product)."""
+    Wall time of the whole call (block norms, symbolic stage with the Eq. 3
+    bound and numeric stage on the GPU, final filter and compaction, result
+    handle), and the rate of its numeric flops (2 b_i b_k b_j per retained
+    block product)."""
     import torch
     import synthetic as syn
     from paper_2609_04397_gb300 import VBCSR
