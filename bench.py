@@ -1,14 +1,24 @@
 """Benchmark of the VBCSR hot path on GB300.
 
-Workload (default): the ~50k-atom spherical zinc-blende cluster (a = 5.87 A,
-cation b = 13, anion b = 9, blocks to the third neighbour shell plus self,
-entries exp(-r / 2 A) N(0,1), symmetric; 549,607 rows, 1.67e8 stored
-entries, 1.33 GB of FP64 values), seeded and synthetic. One step is the FP64
-product Y = H X (alpha = 1, beta = 0) for each of k = 1, 8 and 32. Inputs
-(values 1.33 GB) are larger than the 129 MB L2, so no flush is needed.
+Headline workload (default): the ~1e6-atom spherical zinc-blende nanoparticle
+(a = 5.87 A, cation b = 13, anion b = 9, blocks to the third neighbour shell
+plus self, entries exp(-r / 2 A) N(0,1), symmetric; 999,935 atoms,
+10,999,859 rows, 3.44e9 stored entries, 27.5 GB of FP64 values), seeded and
+synthetic, shifted and scaled on the GPU to H~ = (H - c) / d with its spectrum
+inside [-1, 1] (Gershgorin bounds). One step is one step of the Chebyshev
+recurrence of the kernel polynomial method (Sec. V) on 16 Rademacher vectors:
+t_{n+1} = 2 H~ t_n - t_{n-1} with the moment <R, t_{n+1}> fused into the
+product's epilogue, FP64 block products. The values (27.5 GB) are far larger
+than the 129 MB L2, so no flush is needed.
 
-Output: one JSON line (rank 0). `value` is GFLOP/s = 2 * nnz * sum(k) per step
-over the device-timed steps, summed over ranks (replicas) with the max time.
+`value` is GFLOP/s = 2 * nnz * k per step over the device-timed steps, summed
+over ranks (replicas) with the max time. `mixed` times the full 50-step
+recurrence (51 moments) in FP64 and in each reduced-precision form of the
+block products and gives every mode's largest moment error against the FP64
+oracle's moments (tests/golden/zincblende_1m_moments.json). Secondary keys:
+the ~50k-atom nanoparticle at k = 1, 8, 32 (products per precision, adjoint,
+pattern-sampled product, differentiable recurrence) and the batched workload
+of 256 uneven structures.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -27,8 +37,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "VBCSR SpMM GFLOP/s & % HBM roofline; mixed vs FP64 speedup at rel err<=1e-5"
-KS = (1, 8, 32)
-N_ATOMS = 50_000
+N_ATOMS = 1_000_000          # headline operator (target atom count of the zinc-blende sphere)
+K_HEAD = 16                  # vectors of the headline recurrence
+M_MIXED = 51                 # moments of the full recurrence (50 steps) in the mixed section
+KS = (1, 8, 32)              # widths of the secondary 50k-atom product section
+N_ATOMS_50K = 50_000
+GOLDEN_1M = os.path.join(ROOT, "tests", "golden", "zincblende_1m_moments.json")
 
 
 def _peaks():
@@ -48,18 +62,34 @@ FP64_PEAK_TFLOPS = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PROBE_TFLOPS = 1.19
 
 
-# DRAM bytes (read + write) of one FP64 k = 32 product on the 50k-atom workload
-# (one persistent launch): the median over its 11 launches in one ncu launch
-# list with dram__bytes_read.sum / dram__bytes_write.sum (summary under
-# profiles/, FP64 product on the 50k-atom zinc-blende operator). Algorithmic
-# bytes are 1.62 GB; the excess is X (141 MB at k = 32, above what L2 keeps
-# beside the value stream) fetched about 4.4 times.
-TRAFFIC_F64_K32 = 2107894016
+# DRAM bytes (read + write) of one FP64 Chebyshev step (k = 16) of the
+# ~1e6-atom operator: ncu's dram__bytes_read.sum + dram__bytes_write.sum of the
+# FP64 forward product on the ~200k-atom nanoparticle, scaled by the stored
+# entries to the full operator (traffic grows with the entries: values, X and
+# Y all scale with the atom count); the summary is under profiles/. None until
+# that capture matches the current kernel.
+TRAFFIC_F64_STEP = None
 
 
 def _workload(n_atoms=N_ATOMS):
     import synthetic as syn
     return syn.zincblende(n_atoms, seed=0)
+
+
+def _step_bytes(pat, k, mode="native"):
+    """Algorithmic bytes of one Chebyshev step t_{n+1} = 2 H~ t_n - t_{n-1}
+    with the fused moment <R, t_{n+1}>: every stored value once in the mode's
+    value format (FP64: 8 B; FP32, TF32X3 and the packed bf16 pieces of
+    BF16X2: 4 B; double-FP32 pairs: 8 B), the block column indices and row
+    pointers once, t_n read once in the form the kernel reads it (FP64 8 B;
+    the tensor-core modes read it converted, 4 B, and their epilogue writes
+    t_{n+1} converted once more, 4 B), t_{n-1} and R read (8 B each) and
+    t_{n+1} written (8 B)."""
+    vb = {"native": 8, "df32": 8}.get(mode, 4)
+    xb = 4 if mode in ("bf16x2", "tf32x3", "tf32") else 8
+    extra = 4 if mode in ("bf16x2", "tf32x3", "tf32") else 0
+    return (vb * pat.nnz + 4 * pat.nblk + 8 * (pat.n_brows + 1)
+            + (xb + 8 + 8 + 8 + extra) * k * pat.n_rows)
 
 
 def _alg_bytes(pat, k, value_bytes=8):
@@ -150,13 +180,13 @@ def cpu_baseline(pat, values, ks, budget_s=12.0):
     cores = os.cpu_count() or 1
     rows, flops, secs = 64, 0.0, 0.0
     roff = np.concatenate([[0], np.cumsum(pat.block_sizes())])
+    Xs = {k: np.random.default_rng(k).standard_normal((pat.n_cols, k)) for k in ks}
     while True:
         t = 0.0
         fl = 0.0
         for k in ks:
-            X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
             t0 = time.perf_counter()
-            oracle.spmm(pat, values, X, row_range=(0, rows), nthreads=cores)
+            oracle.spmm(pat, values, Xs[k], row_range=(0, rows), nthreads=cores)
             t += time.perf_counter() - t0
             fl += 2.0 * (roff[pat.block_row_ptr[rows]]) * k
         if t > budget_s / 4 or rows >= pat.n_brows:
@@ -167,9 +197,8 @@ def cpu_baseline(pat, values, ks, budget_s=12.0):
     rows1 = max(1, rows // 16)
     t1, fl1 = 0.0, 0.0
     for k in ks:
-        X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
         t0 = time.perf_counter()
-        oracle.spmm(pat, values, X, row_range=(0, rows1), nthreads=1)
+        oracle.spmm(pat, values, Xs[k], row_range=(0, rows1), nthreads=1)
         t1 += time.perf_counter() - t0
         fl1 += 2.0 * (roff[pat.block_row_ptr[rows1]]) * k
     return {"value": flops / secs / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
@@ -462,8 +491,64 @@ def ops_section(H, pat, values, dev, steps):
     return res
 
 
+def zincblende_50k_section(dev, steps):
+    """The ~50k-atom nanoparticle (49,955 atoms, 1.67e8 entries): FP64 products
+    Y = H X at k = 1, 8, 32, the same in every reduced-precision form, and the
+    method's other products (adjoint, pattern-sampled product, differentiable
+    recurrence, doubling moments) on it."""
+    import torch
+    from paper_2609_04397_gb300 import VBCSR
+    hbm_peak, _ = _peaks()
+    w = _workload(N_ATOMS_50K)
+    pat = w.pattern
+    H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
+    stream = torch.cuda.current_stream(dev)
+    Xs = {k: torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev) for k in KS}
+    Ys = {k: torch.empty(pat.n_rows, k, dtype=torch.float64, device=dev) for k in KS}
+
+    def per_k(mode, reps):
+        for k in KS:
+            H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
+        torch.cuda.synchronize(dev)
+        kev = {k: [] for k in KS}
+        for _ in range(reps):
+            for k in KS:
+                ka = torch.cuda.Event(enable_timing=True)
+                kb = torch.cuda.Event(enable_timing=True)
+                ka.record(stream)
+                H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
+                kb.record(stream)
+                kev[k].append((ka, kb))
+        torch.cuda.synchronize(dev)
+        return {k: sum(a.elapsed_time(b) for a, b in kev[k]) / reps for k in KS}
+
+    reps = max(5, steps // 2)
+    f64 = per_k("native", reps)
+    res = {"workload": f"zincblende_nanoparticle_{pat.n_brows}_atoms", "rows": pat.n_rows, "nnz": pat.nnz,
+           "f64": {str(k): {"ms": f64[k], "gflops": 2.0 * pat.nnz * k / f64[k] / 1e6,
+                            "fp64_alu_frac": 2.0 * pat.nnz * k / f64[k] / 1e9 / FP64_PEAK_TFLOPS} for k in KS}}
+    ref = {k: Ys[k].clone() for k in KS}
+    mixed = {}
+    for mode in ("df32", "bf16x2", "tf32x3", "f32"):
+        t = per_k(mode, reps)
+        vb = 8 if mode == "df32" else 4
+        mixed[mode] = {str(k): {"ms": t[k], "speedup_vs_f64": f64[k] / t[k],
+                                "hbm_frac": _alg_bytes(pat, k, vb) / t[k] / 1e6 / hbm_peak,
+                                "rel_err_vs_f64": float(torch.linalg.norm(Ys[k] - ref[k]) /
+                                                        torch.linalg.norm(ref[k]))}
+                       for k in KS}
+        mixed[mode]["step_speedup_vs_f64"] = sum(f64.values()) / sum(t.values())
+    res["mixed"] = mixed
+    res["ops"] = ops_section(H, pat, w.values, dev, steps)
+    del H, w, Xs, Ys, ref
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_reference(args):
-    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only), on
+    a bounded sample of the headline workload: each step is one Chebyshev
+    step's product (2 H~ t_n - t_{n-1}, k = 16) over the first block rows."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -471,40 +556,54 @@ def run_reference(args):
     pat = w.pattern
     import oracle
     cores = os.cpu_count() or 1
+    k = K_HEAD
     # bounded sample: block rows sized so that each step is ~1-2 s of CPU work
-    rows = min(pat.n_brows, 4000)
+    rows = min(pat.n_brows, 6000)
     roff = np.concatenate([[0], np.cumsum(pat.block_sizes())])
     nnz_s = float(roff[pat.block_row_ptr[rows]])
-    Xs = {k: np.random.default_rng(k).standard_normal((pat.n_cols, k)) for k in KS}
+    T = np.random.default_rng(0).standard_normal((pat.n_cols, k))
+    Tp = np.random.default_rng(1).standard_normal((pat.n_rows, k))
     for _ in range(args.warmup):
-        for k in KS:
-            oracle.spmm(pat, w.values, Xs[k], row_range=(0, rows), nthreads=cores)
+        oracle.spmm(pat, w.values, T, alpha=2.0, beta=-1.0, Y=Tp, row_range=(0, rows), nthreads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        for k in KS:
-            oracle.spmm(pat, w.values, Xs[k], row_range=(0, rows), nthreads=cores)
+        oracle.spmm(pat, w.values, T, alpha=2.0, beta=-1.0, Y=Tp, row_range=(0, rows), nthreads=cores)
         times.append(time.perf_counter() - t0)
     t = sum(times)
-    flops = 2.0 * nnz_s * sum(KS) * args.steps
-    value = flops / t / 1e9
+    value = 2.0 * nnz_s * k * args.steps / t / 1e9
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"zincblende_nanoparticle_{pat.n_brows}_atoms", "ks": list(KS),
+            "config": {"workload": f"zincblende_nanoparticle_{pat.n_brows}_atoms", "k": k,
+                       "step": "one Chebyshev step's product 2 H~ t_n - t_{n-1}",
                        "sample_block_rows": rows},
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {rows} of {pat.n_brows} block rows, k in {list(KS)}"},
+                             "sample": f"first {rows} of {pat.n_brows} block rows, k = {k}"},
             "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _load_golden(pat):
+    """The FP64 oracle's moments of the ~1e6-atom recurrence, when they belong
+    to this operator."""
+    try:
+        with open(GOLDEN_1M) as f:
+            g = json.load(f)
+    except OSError:
+        return None
+    if (g["n_atoms"], g["n_rows"], g["nnz"]) != (pat.n_brows, pat.n_rows, pat.nnz):
+        return None
+    return g
 
 
 def run_ours(args):
     import torch
     import __graft_entry__
     __graft_entry__.build()
+    import synthetic as syn
     from paper_2609_04397_gb300 import VBCSR
 
     world, rank, local = _dist()
@@ -515,27 +614,40 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     hbm_peak, peak_src = _peaks()
+    k = K_HEAD
 
     w = _workload(args.atoms)
     pat = w.pattern
     H = VBCSR.from_pattern(pat, w.values, torch.float64, dev)
+    golden = _load_golden(pat)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pat, w.values, (k,))
+    del w                                   # the host copy of the values (27.5 GB at 1e6 atoms)
+    # H~ = (H - c) / d from the GPU's Gershgorin bounds
+    lo, hi = H.gershgorin()
+    c, d = 0.5 * (hi + lo), 1.01 * 0.5 * (hi - lo)
+    H.shift_scale(c, d)
     stream = torch.cuda.current_stream(dev)
-    Xs = {k: torch.randn(pat.n_cols, k, dtype=torch.float64, device=dev) for k in KS}
-    Ys = {k: torch.empty(pat.n_rows, k, dtype=torch.float64, device=dev) for k in KS}
-    # one persistent launch per product (the default schedule), else one per row height
-    launches_per_product = 1 if H.get_tuning()["schedule"] == "persistent" else H.info.n_row_classes
-    flops_step = 2.0 * pat.nnz * sum(KS)
+    N = pat.n_rows
+    R = torch.from_numpy(syn.rademacher_panel(N, k, 0)).to(dev)
+    flops_step = 2.0 * pat.nnz * k
+    n_warm = max(3, args.warmup)
+    mu = torch.zeros(n_warm + args.steps + 2, dtype=torch.float64, device=dev)
 
-    def step():
-        for k in KS:
-            H.spmm(Xs[k], 1.0, 0.0, Ys[k])
+    # the recurrence state: t_{n-1} in T[0], t_n in T[1]; a step overwrites t_{n-1} with t_{n+1}
+    T = [R.clone(), torch.empty_like(R)]
+    H.spmm(R, 1.0, 0.0, T[1])
 
-    for _ in range(max(3, args.warmup)):
-        step()
+    def step(i):
+        H.spmm_ex(T[(i + 1) & 1], 2.0, -1.0, T[i & 1], R=R, dot_out=mu[i:i + 1])
+
+    for i in range(n_warm):
+        step(i)
     torch.cuda.synchronize(dev)
 
-    # ---- timed region: K steps, per-k CUDA events on the launching stream ----
-    ev = {k: [] for k in KS}
+    # ---- timed region: K recurrence steps, per-step CUDA events on the launching stream ----
+    ev = []
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -545,14 +657,13 @@ def run_ours(args):
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
     e_start.record(stream)
-    for _ in range(args.steps):
-        for k in KS:
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            H.spmm(Xs[k], 1.0, 0.0, Ys[k])
-            b.record(stream)
-            ev[k].append((a, b))
+    for i in range(n_warm, n_warm + args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(i)
+        b.record(stream)
+        ev.append((a, b))
     e_end.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -560,139 +671,103 @@ def run_ours(args):
     clocks = sampler.stop()
     value, total_ms = combine_ranks(e_start.elapsed_time(e_end), flops_step * args.steps, world,
                                     dist if world > 1 else None)
-    per_k_ms = {k: sum(a.elapsed_time(b) for a, b in ev[k]) / args.steps for k in KS}
-
-    # dominant kernel: the k with the largest time; its launches are the FP64 forward kernels
-    kdom = max(KS, key=lambda k: per_k_ms[k])
-    t_dom = per_k_ms[kdom] / 1e3
-    fl_dom = 2.0 * pat.nnz * kdom
-    by_dom = _alg_bytes(pat, kdom)
-    roofline = {"bound": "alu", "achieved": fl_dom / t_dom / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": fl_dom / t_dom / 1e12 / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_F64_K32 if (kdom == 32 and pat.n_brows == 49955) else None,
-                "algorithmic_bytes": by_dom,
-                "kernel": f"fma_persistent_kernel<false, double, double, double, double>, k = {kdom}",
-                "frac_of_dfma_probe": fl_dom / t_dom / 1e12 / FP64_PROBE_TFLOPS,
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    by_step = _step_bytes(pat, k, "native")
+    roofline = {"bound": "alu", "achieved": flops_step / step_ms / 1e9, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": flops_step / step_ms / 1e9 / FP64_PEAK_TFLOPS,
+                "traffic": int(TRAFFIC_F64_STEP * pat.nnz) if TRAFFIC_F64_STEP else None,
+                "algorithmic_bytes": by_step,
+                "kernel": "fma_persistent_kernel<false, double, double, double, double> (FP64 forward product "
+                          f"with the recurrence epilogue), k = {k}",
+                "frac_of_dfma_probe": flops_step / step_ms / 1e9 / FP64_PROBE_TFLOPS,
                 "peak_source": "unit counts x clock (152 SM x 2 FP64 FMA/clk x 2.07 GHz)",
-                "hbm_gbs": by_dom / t_dom / 1e9, "hbm_frac": by_dom / t_dom / 1e9 / hbm_peak,
+                "hbm_gbs": by_step / step_ms / 1e6, "hbm_frac": by_step / step_ms / 1e6 / hbm_peak,
                 "hbm_peak": hbm_peak, "hbm_peak_source": peak_src}
-    per_k = {str(k): {"ms": per_k_ms[k], "gflops": 2.0 * pat.nnz * k / (per_k_ms[k] / 1e3) / 1e9,
-                      "gbs": _alg_bytes(pat, k) / (per_k_ms[k] / 1e3) / 1e9,
-                      "hbm_frac": _alg_bytes(pat, k) / (per_k_ms[k] / 1e3) / 1e9 / hbm_peak}
-             for k in KS}
 
-    # ---- mixed precision vs FP64 on the same workload (separately timed) ----
+    # ---- the full 50-step recurrence in FP64 and in each reduced-precision form ----
     mixed = {}
-    ref = {k: Ys[k].clone() for k in KS}
-    variants = [("df32", False), ("bf16x2", False), ("bf16x2", True), ("tf32x3", False), ("tf32x3", True),
-                ("f32", False)]
-    for mode, staged in variants:
-        H.set_schedule("persistent", mma_staged=staged)
-        for k in KS:
-            H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
+    if not args.no_mixed:
+        ref = np.array(golden["moments"]) if golden else None
+        for mode in ("native", "df32", "tf32x3", "bf16x2"):
+            H.chebyshev(R, 3, precision=mode)            # first use builds the mode's copies
+            torch.cuda.synchronize(dev)
+            best = None
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mom, _ = H.chebyshev(R, M_MIXED, precision=mode)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            per_step = best / (M_MIXED - 1)
+            by = _step_bytes(pat, k, mode)
+            r = {"ms_50_steps": best, "ms_per_step": per_step,
+                 "gbs": by / per_step / 1e6, "hbm_frac": by / per_step / 1e6 / hbm_peak,
+                 "algorithmic_bytes_per_step": by}
+            if ref is not None:
+                r["max_moment_err_vs_oracle"] = float(np.max(np.abs(mom.cpu().numpy() - ref)) / abs(ref[0]))
+            mixed[mode] = r
+        for mode, r in mixed.items():
+            r["speedup_vs_f64"] = mixed["native"]["ms_50_steps"] / r["ms_50_steps"]
+        if golden:
+            mixed["oracle_moments"] = ("tests/golden/zincblende_1m_moments.json (FP64 oracle; GPU Gershgorin "
+                                       f"centre and half-width within {abs(c - golden['c']) / abs(golden['d']):.1e}"
+                                       f" / {abs(d - golden['d']) / abs(golden['d']):.1e} of the oracle's)")
+
+    # ---- end to end through the public API: pinned host R in, host moments out ----
+    hR = torch.from_numpy(syn.rademacher_panel(N, k, 0)).pin_memory()
+    hmu = torch.empty(M_MIXED, dtype=torch.float64).pin_memory()
+    Rdev = torch.empty_like(R)
+    e2e_ms = []
+    for _ in range(2):
         torch.cuda.synchronize(dev)
-        errs = {str(k): float(torch.linalg.norm(Ys[k] - ref[k]) / torch.linalg.norm(ref[k])) for k in KS}
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        reps = max(5, args.steps // 4)
-        kev = {k: [] for k in KS}
         a.record(stream)
-        for _ in range(reps):
-            for k in KS:
-                ka = torch.cuda.Event(enable_timing=True)
-                kb = torch.cuda.Event(enable_timing=True)
-                ka.record(stream)
-                H.spmm(Xs[k], 1.0, 0.0, Ys[k], precision=mode)
-                kb.record(stream)
-                kev[k].append((ka, kb))
+        Rdev.copy_(hR, non_blocking=True)
+        mom, _ = H.chebyshev(Rdev, M_MIXED)
+        hmu.copy_(mom, non_blocking=True)
         b.record(stream)
         torch.cuda.synchronize(dev)
-        ms = a.elapsed_time(b) / reps
-        # the mixed modes stream a 4-byte copy of the values; X is converted
-        # (DF32: split) once per call inside the timed call
-        vb = 8 if mode == "df32" else 4
-        mk = {}
-        for k in KS:
-            t = sum(x.elapsed_time(y) for x, y in kev[k]) / reps
-            mk[str(k)] = {"ms": t, "gbs": _alg_bytes(pat, k, vb) / (t / 1e3) / 1e9,
-                          "hbm_frac": _alg_bytes(pat, k, vb) / (t / 1e3) / 1e9 / hbm_peak,
-                          "speedup_vs_f64": per_k_ms[k] / t}
-        mixed[mode + ("_staged" if staged else "")] = {
-            "ms_per_step": ms, "speedup_vs_f64": (total_ms / args.steps) / ms,
-            "rel_err_vs_f64_gpu": errs, "gflops": flops_step / (ms / 1e3) / 1e9, "per_k": mk}
-    H.set_schedule("persistent")
-
-    # ---- end to end through the public API: pinned host X in, Y out, every step ----
-    hX = {k: torch.randn(pat.n_cols, k, dtype=torch.float64).pin_memory() for k in KS}
-    hY = {k: torch.empty(pat.n_rows, k, dtype=torch.float64).pin_memory() for k in KS}
-
-    # copies on their own streams (one per direction), ordered against the products
-    # by events, so that the next panel's upload and the last result's download
-    # overlap the product in between; every copy of every step stays inside the
-    # timed region
-    h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ev_in = {k: torch.cuda.Event() for k in KS}      # X_k uploaded
-    ev_prod = {k: torch.cuda.Event() for k in KS}    # product on X_k done (X_k free, Y_k ready)
-    ev_out = {k: torch.cuda.Event() for k in KS}     # Y_k downloaded (Y_k free)
-
-    def e2e_step():
-        for k in KS:
-            h2d.wait_event(ev_prod[k])
-            with torch.cuda.stream(h2d):
-                Xs[k].copy_(hX[k], non_blocking=True)
-            ev_in[k].record(h2d)
-        for k in KS:
-            stream.wait_event(ev_in[k])
-            stream.wait_event(ev_out[k])
-            H.spmm(Xs[k], 1.0, 0.0, Ys[k])
-            ev_prod[k].record(stream)
-            d2h.wait_event(ev_prod[k])
-            with torch.cuda.stream(d2h):
-                hY[k].copy_(Ys[k], non_blocking=True)
-            ev_out[k].record(d2h)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize(dev)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(5, args.steps // 4)
-    a.record(stream)
-    h2d.wait_event(a)
-    d2h.wait_event(a)
-    for _ in range(e2e_steps):
-        e2e_step()
-    for k in KS:
-        stream.wait_event(ev_out[k])
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = a.elapsed_time(b) / e2e_steps
-    e2e = {"value": world * flops_step / (e2e_ms / 1e3) / 1e9, "unit": "GFLOP/s",
-           "h2d_bytes_per_step": int(sum(8 * pat.n_cols * k for k in KS)),
-           "d2h_bytes_per_step": int(sum(8 * pat.n_rows * k for k in KS)), "ms_per_step": e2e_ms}
-
-    batched = batched_section(dev, args.steps) if not args.no_batched else None
-    ops = ops_section(H, pat, w.values, dev, args.steps) if not args.no_ops else None
-    domains = domains_section(dev, args.steps) if args.domains else None
-    kspace = kspace_section(dev, args.steps, max(1, round((args.atoms / 8) ** (1 / 3)))) if args.kspace else None
-    spg = spgemm_section(dev) if args.spgemm else None
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_t = min(e2e_ms)
+    e2e = {"value": world * flops_step * (M_MIXED - 1) / (e2e_t / 1e3) / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(8 * N * k), "d2h_bytes_per_step": int(8 * M_MIXED),
+           "ms_per_step": e2e_t,
+           "step": f"one FP64 recurrence of {M_MIXED - 1} products (vbcsr_chebyshev): R copied in from "
+                   "pinned host memory, the moments copied back"}
     H.check()
+    del H, T, R, Rdev
+    torch.cuda.empty_cache()
+
+    secondary = None
+    if not args.no_secondary:
+        secondary = zincblende_50k_section(dev, args.steps)
+    batched = batched_section(dev, args.steps) if not args.no_batched else None
+    domains = domains_section(dev, args.steps) if args.domains else None
+    kspace = kspace_section(dev, args.steps, max(1, round((N_ATOMS_50K / 8) ** (1 / 3)))) if args.kspace else None
+    spg = spgemm_section(dev) if args.spgemm else None
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"zincblende_nanoparticle_{pat.n_brows}_atoms", "atoms": pat.n_brows,
-                       "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk, "ks": list(KS),
-                       "alpha": 1.0, "beta": 0.0, "parallelism": f"replicas x{world}",
-                       "l2": f"no flush: inputs larger than L2 ({8 * pat.nnz / 1e9:.2f} GB of values per product)"},
-            "roofline": roofline, "per_k": per_k, "mixed": mixed, "batched": batched, "e2e": e2e,
-            **({"ops": ops} if ops is not None else {}),
+                       "rows": pat.n_rows, "nnz": pat.nnz, "blocks": pat.nblk, "k": k,
+                       "step": "one Chebyshev step t_{n+1} = 2 H~ t_n - t_{n-1} with the fused moment "
+                               "<R, t_{n+1}>, FP64 block products",
+                       "spectrum_scaling": {"c": c, "d": d},
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"no flush: inputs larger than L2 ({8 * pat.nnz / 1e9:.1f} GB of values per step)"},
+            "roofline": roofline, "mixed": mixed, "e2e": e2e,
+            **({"zincblende_50k": secondary} if secondary is not None else {}),
+            **({"batched": batched} if batched is not None else {}),
             **({"domains": domains} if domains is not None else {}),
             **({"kspace": kspace} if kspace is not None else {}),
             **({"spgemm": spg} if spg is not None else {}),
-            "gpu_launches": launches_per_product * len(KS) * args.steps, "clocks": clocks}
+            "gpu_launches": 2 * args.steps, "clocks": clocks}
     if rank == 0:
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(pat, w.values, KS)
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -703,19 +778,22 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 50-step recurrence per precision")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the ~50k-atom section (products per k and precision, adjoint, SDDMM, gradient)")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--no-ops", action="store_true",
-                    help="skip the adjoint, pattern-sampled and Chebyshev timings")
+    ap.add_argument("--no-ops", action="store_true", help="(kept for older command lines; see --no-secondary)")
     ap.add_argument("--spgemm", action="store_true",
                     help="also measure the thresholded block product C = H H")
     ap.add_argument("--kspace", action="store_true",
                     help="also measure a periodic crystal sampled in reciprocal space (complex products)")
     ap.add_argument("--atoms", type=int, default=N_ATOMS,
-                    help="zinc-blende target atom count (a smaller case for profiler captures)")
+                    help="zinc-blende target atom count of the headline operator (a smaller case for profiler "
+                         "captures)")
     ap.add_argument("--domains", action="store_true",
                     help="also measure the CSR / BSR / VBCSR domains (~500 MiB each)")
     args = ap.parse_args()

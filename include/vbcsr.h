@@ -295,20 +295,26 @@ int vbcsr_chebyshev(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_
  * stored values of H~ (packed order), given dL/dmu_n = grad_mu[n]:
  *   g_n = grad_mu[n] R / (n_rows * k),
  *   lam_{M-1} = g_{M-1},  lam_n = g_n + 2 H~^T lam_{n+1} - lam_{n+2}  (n >= 1),
- *   dL/dH~ = lam_1 t_0^T + sum_{n=1}^{M-2} 2 lam_{n+1} t_n^T   on the stored blocks.
+ *   dL/dH~ = lam_1 t_0^T + sum_{n=1}^{M-2} 2 lam_{n+1} t_n^T   on the stored blocks,
+ *   dvalues = dL/dH~ / d_scale.
+ * When the handle holds H~ = (H - c I) / d made from an operator H by
+ * vbcsr_shift_scale, d_scale = d gives the gradient with respect to the
+ * stored values of H itself (the shift c is a constant and drops out);
+ * d_scale = 1 gives dL/dH~.
  * The t_n are recomputed segment by segment from the checkpoint pairs that
  * vbcsr_chebyshev stored with the same ckpt_every, so memory stays at
  * O(ckpt_every) panels.
  *  grad_mu  device, n_moments doubles (copied to the host: the call
  *           synchronises `stream` once at its start)
  *  ckpt     device, as written by vbcsr_chebyshev
+ *  d_scale  finite and nonzero
  *  dvalues  device, nnz doubles, overwritten
  *  work     device, (2 + 2 * ckpt_every) * n_rows * k doubles
  * (The adjoint recurrence has no counterpart in the paper; it differentiates
  * the kernel-polynomial moments of Sec. V.)
  */
 int vbcsr_chebyshev_backward(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
-                             const double *grad_mu, const double *ckpt, int64_t ckpt_every,
+                             const double *grad_mu, const double *ckpt, int64_t ckpt_every, double d_scale,
                              double *dvalues, double *work, int precision, void *stream);
 
 /* Damping kernels of vbcsr_kpm_dos. */
@@ -342,6 +348,24 @@ int vbcsr_kpm_moments(vbcsr_t *Ht, int64_t k, const double *R, int64_t ldr, int6
  */
 int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kernel, const double *x, int64_t n_x,
                   double *dos, void *stream);
+
+/*
+ * Band gap read off a density of states (Sec. V takes the band gaps of the
+ * InP particles from their KPM densities of states; the criterion is a DOS
+ * threshold). On an energy grid energies[0 .. n) (increasing) with densities
+ * dos[0 .. n): i0 is the grid point nearest `reference` (the smallest index
+ * on a tie), and the gap is the widest run lo <= i0 <= hi of consecutive grid
+ * points whose DOS is below `threshold` (dos < threshold; NaN is not below):
+ *   out[0] = energies[lo], out[1] = energies[hi],
+ * where lo - 1 and hi + 1 are outside the grid or not below the threshold;
+ * out = {NaN, NaN} when dos[i0] is not below the threshold (the reference
+ * lies inside a band). energies, dos: device arrays of n >= 1 doubles (the
+ * grid and vbcsr_kpm_dos's output); out: device array of 2 doubles. One CTA,
+ * asynchronous on `stream`. Errors: INVALID_ARG (n < 1, NULL, NaN reference
+ * or threshold), CUDA.
+ */
+int vbcsr_kpm_gap(const double *energies, const double *dos, int64_t n, double reference, double threshold,
+                  double *out, void *stream);
 
 /*
  * Spectral bounds for the kernel polynomial method (Sec. V needs H scaled so

@@ -15,7 +15,8 @@ Contents, each following the passage it cites:
 * ``chebyshev_moments`` / ``moment_loss_grad``  the kernel-polynomial-method
                     recurrence of Sec. V (t_{n+1} = 2 H~ t_n - t_{n-1}) and the
                     reverse-mode gradient of L = sum_n mu_n^2
-* ``kpm_moments_doubling`` / ``kpm_dos``  the DOS pipeline of Sec. V
+* ``kpm_moments_doubling`` / ``kpm_dos`` / ``kpm_gap``  the DOS pipeline of
+                    Sec. V (moments, damped DOS, the gap read off it)
 * ``spgemm``        the thresholded block product, Eqs. (2)-(3)
 * ``kspace_blocks`` / ``kspace_dense``  a periodic operator sampled in
                     reciprocal space, Eq. (4); ``spmm_complex`` /
@@ -317,6 +318,30 @@ def kpm_dos(mu, x, kernel="jackson") -> np.ndarray:
     for n in range(1, len(mu)):
         acc += 2.0 * g[n] * mu[n] * np.cos(n * th)
     return acc / (np.pi * np.sqrt(1.0 - x * x))
+
+
+def kpm_gap(energies, dos, reference, threshold):
+    """Band gap read off a density of states (Sec. V reads the gaps of the InP
+    particles off their KPM DOS with a threshold criterion; the threshold is
+    an argument here). With i0 the grid point nearest `reference` (the first
+    one on a tie), walk left and right from i0 while the next point's DOS is
+    below `threshold` (NaN is not below); returns (energies[lo], energies[hi])
+    of that run, or None when dos[i0] itself is not below the threshold."""
+    E = [float(e) for e in energies]
+    D = [float(v) for v in dos]
+    i0 = 0
+    for j in range(1, len(E)):
+        if abs(E[j] - reference) < abs(E[i0] - reference):
+            i0 = j
+    if not (D[i0] < threshold):
+        return None
+    lo = i0
+    while lo - 1 >= 0 and D[lo - 1] < threshold:
+        lo -= 1
+    hi = i0
+    while hi + 1 < len(E) and D[hi + 1] < threshold:
+        hi += 1
+    return E[lo], E[hi]
 
 
 # ----------------------------------------------------------------------------

@@ -10,4 +10,4 @@ from ._lib import VBCSRError, lib  # noqa: F401
 from .matrix import VBCSR, kpm_dos, kpm_gap  # noqa: F401
 
 __all__ = ["VBCSR", "VBCSRError", "lib"]
-from .autograd import VBCSRMatmul, chebyshev_moments, diagonal_mask, shift_scale, vbcsr_matmul  # noqa: F401,E402
+from .autograd import VBCSRMatmul, chebyshev_moments, vbcsr_matmul  # noqa: F401,E402

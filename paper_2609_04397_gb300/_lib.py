@@ -43,11 +43,12 @@ SIGNATURES = {
     "vbcsr_spmm_ex": ([_p, _int, _i64, _d, _p, _i64, _d, _p, _i64, ctypes.POINTER(Epilogue), _int, _p], _int),
     "vbcsr_sddmm": ([_p, _i64, _d, _p, _i64, _p, _i64, _d, _p, _p], _int),
     "vbcsr_chebyshev": ([_p, _i64, _p, _i64, _i64, _p, _p, _p, _i64, _int, _p], _int),
-    "vbcsr_chebyshev_backward": ([_p, _i64, _p, _i64, _i64, _p, _p, _i64, _p, _p, _int, _p], _int),
+    "vbcsr_chebyshev_backward": ([_p, _i64, _p, _i64, _i64, _p, _p, _i64, _d, _p, _p, _int, _p], _int),
     "vbcsr_chebyshev_noalloc": ([_p, _i64, _p, _i64, _i64, _p, _int, _p], _int),
     "vbcsr_gershgorin": ([_p, _p, _p], _int),
     "vbcsr_kpm_moments": ([_p, _i64, _p, _i64, _i64, _p, _p, _int, _p], _int),
     "vbcsr_kpm_dos": ([_p, _i64, _int, _p, _i64, _p, _p], _int),
+    "vbcsr_kpm_gap": ([_p, _p, _i64, _d, _d, _p, _p], _int),
     "vbcsr_shift_scale": ([_p, _d, _d, _p], _int),
     "vbcsr_spgemm": ([_p, _p, _d, ctypes.POINTER(_p), _p], _int),
     "vbcsr_create_kspace": ([ctypes.POINTER(_p), _i64, _p, _i64, _p, _p, _p, _p, _p, _p], _int),

@@ -2,17 +2,20 @@
 
 * ``vbcsr_matmul(H, values, X)``  Y = H(values) X;  dX = H^T dY (adjoint
   kernel, Eq. 1), dvalues = pattern-sampled dY X^T (block-SDDMM kernel).
-* ``chebyshev_moments(H, values_t, R, n_moments, ckpt_every)``  the moments
-  mu_n = <R, T_n(H~) R> / (N k) of the kernel polynomial method (Sec. V) for
-  the already shifted and scaled operator H~ = values_t; the backward pass runs
-  the adjoint recurrence in the library, recomputing the Chebyshev vectors
-  from checkpoint pairs (t_m, t_m+1) stored every ``ckpt_every`` steps.
+* ``chebyshev_moments(H, values, R, n_moments, ckpt_every, c=, d=)``  the
+  moments mu_n = <R, T_n(H~) R> / (N k) of the kernel polynomial method
+  (Sec. V) for H~ = (H - c I) / d, H holding ``values``; the shift and scale
+  run in the library (vbcsr_shift_scale), and the backward pass runs the
+  adjoint recurrence in the library, recomputing the Chebyshev vectors from
+  checkpoint pairs (t_m, t_m+1) stored every ``ckpt_every`` steps, and divides
+  by d there.
 
 The gradient flows to every stored value independently (a mirrored block of
 a symmetric operator is a separate parameter).
 """
 import ctypes
 
+import numpy as np
 import torch
 
 from ._lib import check, lib
@@ -53,58 +56,47 @@ def vbcsr_matmul(H: VBCSR, values: torch.Tensor, X: torch.Tensor, precision="nat
 
 class _Chebyshev(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, values_t, R, H: VBCSR, n_moments, ckpt_every, precision):
-        H.set_values(values_t.detach())
+    def forward(ctx, values, R, H: VBCSR, n_moments, ckpt_every, precision, c, d):
+        H.set_values(values.detach())
+        scaled = (c, d) != (0.0, 1.0)
+        if scaled:
+            H.shift_scale(c, d)                  # H~ = (H - c I) / d, in the library
         R = R.detach().contiguous()
         mom, ck = H.chebyshev(R, n_moments, ckpt_every=ckpt_every, precision=precision)
-        ctx.save_for_backward(values_t, R, ck if ck is not None else torch.empty(0, device=R.device))
-        ctx.H, ctx.M, ctx.E, ctx.precision = H, n_moments, ckpt_every, precision
+        ctx.save_for_backward(values, R, ck if ck is not None else torch.empty(0, device=R.device))
+        ctx.H, ctx.M, ctx.E, ctx.precision, ctx.c, ctx.d = H, n_moments, ckpt_every, precision, c, d
         return mom
 
     @staticmethod
     def backward(ctx, grad_mu):
-        values_t, R, ck = ctx.saved_tensors
+        values, R, ck = ctx.saved_tensors
         H, M, E = ctx.H, ctx.M, ctx.E
-        H.set_values(values_t.detach())
+        H.set_values(values.detach())
+        if (ctx.c, ctx.d) != (0.0, 1.0):
+            H.shift_scale(ctx.c, ctx.d)
         N, k = R.shape
         dv = torch.empty(H.nnz, dtype=torch.float64, device=R.device)
         work = torch.empty((2 + 2 * E) * N * k, dtype=torch.float64, device=R.device)
         g = grad_mu.detach().to(torch.float64).contiguous()
+        # dL/dH = dL/dH~ / d: the library divides by d (the shift c drops out)
         check(lib().vbcsr_chebyshev_backward(
             H.handle, k, ctypes.c_void_p(R.data_ptr()), R.stride(0), M, ctypes.c_void_p(g.data_ptr()),
-            ctypes.c_void_p(ck.data_ptr() if ck.numel() else None), E, ctypes.c_void_p(dv.data_ptr()),
-            ctypes.c_void_p(work.data_ptr()), _prec(ctx.precision), _stream(H.device)),
-            "vbcsr_chebyshev_backward")
-        return dv, None, None, None, None, None
+            ctypes.c_void_p(ck.data_ptr() if ck.numel() else None), E, float(ctx.d),
+            ctypes.c_void_p(dv.data_ptr()), ctypes.c_void_p(work.data_ptr()), _prec(ctx.precision),
+            _stream(H.device)), "vbcsr_chebyshev_backward")
+        return dv, None, None, None, None, None, None, None
 
 
-def chebyshev_moments(H: VBCSR, values_t: torch.Tensor, R: torch.Tensor, n_moments: int,
-                      ckpt_every: int = 10, precision="native") -> torch.Tensor:
-    """Differentiable KPM moments of H~ (values_t, spectrum inside [-1, 1])."""
+def chebyshev_moments(H: VBCSR, values: torch.Tensor, R: torch.Tensor, n_moments: int,
+                      ckpt_every: int = 10, precision="native", c: float = 0.0, d: float = 1.0) -> torch.Tensor:
+    """Differentiable KPM moments mu_n = <R, T_n(H~) R> / (N k) of
+    H~ = (H - c I) / d, H holding `values` (packed order). With the default
+    c = 0, d = 1 the values are those of H~ itself (spectrum inside [-1, 1]);
+    otherwise the library forms H~ from them (vbcsr_shift_scale) and the
+    gradient is with respect to the values of H (c and d are constants)."""
     if H.dtype != torch.float64:
         raise TypeError("the Chebyshev recurrence runs on an FP64 operator")
-    return _Chebyshev.apply(values_t, R, H, n_moments, max(1, int(ckpt_every)), precision)
-
-
-def diagonal_mask(H: VBCSR) -> torch.Tensor:
-    """1.0 at every stored value on the scalar diagonal (packed order), else 0."""
-    import numpy as np
-    rb, cb, rp, ci = H.pattern
-    r = np.concatenate([[0], np.cumsum(rb.astype(np.int64))])
-    c = np.concatenate([[0], np.cumsum(cb.astype(np.int64))])
-    rows = np.repeat(np.arange(len(rb)), np.diff(rp))
-    off = np.concatenate([[0], np.cumsum(rb[rows].astype(np.int64) * cb[ci])])
-    m = np.zeros(int(off[-1]))
-    # only blocks whose scalar row and column ranges overlap hold diagonal entries
-    hit = np.nonzero((r[rows] < c[ci] + cb[ci]) & (c[ci] < r[rows] + rb[rows]))[0]
-    for b in hit:
-        i, j = rows[b], ci[b]
-        p = np.arange(rb[i])[:, None] + r[i]
-        q = np.arange(cb[j])[None, :] + c[j]
-        m[off[b]:off[b + 1]] = (p == q).astype(np.float64).ravel()
-    return torch.from_numpy(m).to(H.device)
-
-
-def shift_scale(values: torch.Tensor, diag_mask: torch.Tensor, c: float, d: float) -> torch.Tensor:
-    """Packed values of H~ = (H - c I) / d; c and d are constants."""
-    return (values - c * diag_mask) / d
+    d = float(d)
+    if not (d != 0.0 and np.isfinite(d)):
+        raise ValueError(f"d = {d}")
+    return _Chebyshev.apply(values, R, H, n_moments, max(1, int(ckpt_every)), precision, float(c), d)

@@ -902,11 +902,85 @@ static int cached_cap(const void *kernel, int warps, size_t smem) {
     return c;
 }
 
+// Form of X that a product's kernel reads.
+enum { kXAsGiven = 0, kXF32 = 1, kXSplit = 2, kXPairs = 3 };
+
+// Which kernel family serves a product, and which mixed-precision copies of
+// the values and of X it reads (built on first use by run_product).
+struct ModePlan {
+    int mode;                 // effective precision code
+    bool f64, cplx;
+    bool fma;                 // CUDA-core kernels in the operator's or the FP32 / double-FP32 arithmetic
+    bool csr_kernel;          // the scalar kernel of a CSR-backend operator
+    bool split;               // a tensor-core mode on the CUDA cores (thin products, scalar operators)
+    bool presplit;            // BF16X2 on operands split once into packed bf16 (hi, lo) words
+    bool need_panel32, need_panelbf, need_paneldf;
+    int xkind;                // kXAsGiven, kXF32, kXSplit or kXPairs
+};
+
+static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision) {
+    ModePlan p;
+    p.f64 = A->dtype == VBCSR_F64;
+    p.cplx = A->dtype == VBCSR_C128;
+    p.mode = precision;
+    if (!p.f64 && p.mode == VBCSR_PREC_F32) p.mode = VBCSR_PREC_NATIVE;
+    p.fma = (p.mode == VBCSR_PREC_NATIVE || p.mode == VBCSR_PREC_F32 || p.mode == VBCSR_PREC_DF32);
+    // a tensor-core mode on a product too thin for an MMA tile (few columns, or the
+    // single-row items of a scalar operator) runs its piece products on the CUDA cores
+    p.csr_kernel = A->backend == VBCSR_BACKEND_CSR && !trans && !p.cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
+    p.split = !p.fma && p.f64 && !trans && (k <= kSplitFmaMaxK || p.csr_kernel);
+    // the BF16X2 forward kernels of an FP64 operator (the plain tensor-core kernel
+    // and the CUDA-core form of thin products; the staged kernel splits itself, the
+    // scalar kernel reads FP32) read values and X split once into packed bf16
+    // (hi, lo) words
+    p.presplit = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.csr_kernel &&
+                 (p.split || !(A->schedule & VBCSR_SCHED_MMA_STAGED));
+    p.need_panel32 = p.f64 && p.mode != VBCSR_PREC_NATIVE && p.mode != VBCSR_PREC_DF32 && !p.presplit;
+    p.need_panelbf = p.presplit;
+    p.need_paneldf = p.mode == VBCSR_PREC_DF32;
+    p.xkind = !p.f64 || p.mode == VBCSR_PREC_NATIVE ? kXAsGiven
+            : p.mode == VBCSR_PREC_DF32             ? kXPairs
+            : p.presplit                            ? kXSplit
+                                                    : kXF32;
+    return p;
+}
+
+// True when every mixed-precision copy that a product of `xrows` x k needs is
+// already built and large enough, so that run_product allocates nothing.
+static bool mode_buffers_ready(const vbcsr_t *A, const ModePlan &p, int64_t xrows, int64_t k) {
+    if (p.need_panel32 && !A->panel32_valid) return false;
+    if (p.need_panelbf && !A->panelbf_valid) return false;
+    if (p.need_paneldf && !A->paneldf_valid) return false;
+    const size_t need = (size_t)xrows * (size_t)k;
+    switch (p.xkind) {
+        case kXF32: return A->xconv_elems >= need;
+        case kXSplit: return A->xbf_elems >= need;
+        case kXPairs: return A->xdf_elems >= need;
+        default: return true;
+    }
+}
+
+// Chebyshev steps on the plain tensor-core forward kernel exchange X in
+// the kernel's own form: a step reads t_n already converted (x_in, [rows, k],
+// leading dimension k) and its epilogue writes t_{n+1} converted as well
+// (x_out), so no separate conversion pass runs between steps.
+struct FusedX {
+    const void *x_in;   // X in the form the kernel reads, or NULL: convert X here
+    void *x_out;        // where the epilogue writes the output in that form, or NULL
+};
+
+// True when a forward product of this plan runs the plain tensor-core kernel
+// on a converted X (FP32, or packed bf16 pieces), i.e. when FusedX applies.
+static bool fused_x_applies(const vbcsr_t *A, const ModePlan &p) {
+    return !p.fma && !p.split && !p.cplx && (p.xkind == kXF32 || p.xkind == kXSplit) &&
+           !(A->schedule & VBCSR_SCHED_MMA_STAGED);
+}
+
 // dot_scale multiplies the fused dot product before it is stored (1 for the
 // public epilogue, 1 / (N k) for the Chebyshev moments).
 static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const void *X, int64_t ldx, double beta,
                        void *Y, int64_t ldy, const vbcsr_epilogue_t *epi, int precision, cudaStream_t s,
-                       double dot_scale = 1.0) {
+                       double dot_scale = 1.0, const FusedX *fx = nullptr) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (k < 0) return fail(VBCSR_ERR_INVALID_ARG, "k = %lld", (long long)k);
     if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
@@ -932,31 +1006,20 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     if (gamma != 0.0 && (!epi->Z || epi->ldz < k)) return fail(VBCSR_ERR_INVALID_ARG, "epilogue Z / ldz");
     if (want_dot && (!epi->R || epi->ldr < k)) return fail(VBCSR_ERR_INVALID_ARG, "epilogue R / ldr");
 
-    const bool f64 = A->dtype == VBCSR_F64;
-    int mode = precision;
-    if (!f64 && mode == VBCSR_PREC_F32) mode = VBCSR_PREC_NATIVE;
-    const bool fma = (mode == VBCSR_PREC_NATIVE || mode == VBCSR_PREC_F32 || mode == VBCSR_PREC_DF32);
-    // a tensor-core mode on a product too thin for an MMA tile (few columns, or the
-    // single-row items of a scalar operator) runs its piece products on the CUDA cores
-    const bool csr_kernel =
-        A->backend == VBCSR_BACKEND_CSR && !trans && !cplx && !(A->schedule & VBCSR_SCHED_NO_CSR);
-    const bool split = !fma && f64 && !trans && (k <= kSplitFmaMaxK || csr_kernel);
-    // the BF16X2 forward kernels of an FP64 operator (the plain tensor-core kernel
-    // and the CUDA-core form of thin products; the staged kernel splits itself, the
-    // scalar kernel reads FP32) read values and X split once into packed bf16
-    // (hi, lo) words
-    const bool presplit = f64 && mode == VBCSR_PREC_BF16X2 && !trans && !csr_kernel &&
-                          (split || !(A->schedule & VBCSR_SCHED_MMA_STAGED));
+    const ModePlan mp = plan_mode(A, trans, k, precision);
+    const bool f64 = mp.f64;
+    const int mode = mp.mode;
+    const bool fma = mp.fma, csr_kernel = mp.csr_kernel, split = mp.split, presplit = mp.presplit;
     const int mma_mode = presplit ? kBF16X2Presplit : mode;
-    if (f64 && mode != VBCSR_PREC_NATIVE && mode != VBCSR_PREC_DF32 && !presplit && !A->panel32_valid) {
+    if (mp.need_panel32 && !A->panel32_valid) {
         int rc = refresh_panel32(A, s);
         if (rc) return rc;
     }
-    if (presplit && !A->panelbf_valid) {
+    if (mp.need_panelbf && !A->panelbf_valid) {
         int rc = refresh_panelbf(A, s);
         if (rc) return rc;
     }
-    if (mode == VBCSR_PREC_DF32 && !A->paneldf_valid) {
+    if (mp.need_paneldf && !A->paneldf_valid) {
         int rc = refresh_paneldf(A, s);
         if (rc) return rc;
     }
@@ -964,14 +1027,18 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     // The mixed modes read X as FP32 (the double-FP32 mode as hi/lo pairs):
     // convert an FP64 X once here rather than at every gather inside the
     // kernel (each X row is gathered by ~30 work items).
-    if (f64 && mode != VBCSR_PREC_NATIVE && alpha != 0.0 && xrows > 0) {
+    const bool fused = fx && !trans && fused_x_applies(A, mp);
+    if (fused && fx->x_in && alpha != 0.0 && xrows > 0) {
+        X = fx->x_in;
+        ldx = k;
+    } else if (mp.xkind != kXAsGiven && alpha != 0.0 && xrows > 0) {
         const size_t need = (size_t)xrows * (size_t)k;
-        if (mode == VBCSR_PREC_DF32) {
+        if (mp.xkind == kXPairs) {
             int rc = grow(A, &A->xdf, &A->xdf_elems, need, s, "alloc double-FP32 copy of X");
             if (rc) return rc;
             CUDA_TRY(launch_split_df(xrows, k, (const double *)X, ldx, A->xdf, s), "split X");
             X = A->xdf;
-        } else if (presplit) {
+        } else if (mp.xkind == kXSplit) {
             int rc = grow(A, &A->xbf, &A->xbf_elems, need, s, "alloc split copy of X");
             if (rc) return rc;
             CUDA_TRY(launch_split_bf16_panel(xrows, k, (const double *)X, ldx, A->xbf, s), "split X");
@@ -1007,6 +1074,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.x_rows = xrows;
     a.err = A->err;
     a.debug_checks = A->debug_checks;
+    a.xs_out = fused && fx->x_out ? fx->x_out : nullptr;
     const int kc_auto = auto_kc(k);
     // FP32 values and double-FP32 pairs in the CUDA-core forward kernels with
     // column tiles of 8 or more go through the shared-memory ring unless the
@@ -1202,6 +1270,31 @@ extern "C" int vbcsr_sddmm(vbcsr_t *A, int64_t k, double alpha, const void *Aop,
 // ---------------------------------------------------------------------------
 // Chebyshev moments (kernel polynomial method, Sec. V)
 
+// The two converted-X panels of a recurrence whose forward products run the
+// plain tensor-core kernel: xs[0] is the handle's conversion buffer
+// (where the first product converts R), xs[1] the panel after it; both NULL
+// when the fused form does not apply (the products then convert X themselves).
+static int cheb_fused_buffers(vbcsr_t *A, int64_t k, int precision, void *xs[2], cudaStream_t s) {
+    xs[0] = xs[1] = nullptr;
+    if (A->dtype != VBCSR_F64) return VBCSR_OK;
+    const ModePlan mp = plan_mode(A, false, k, precision);
+    if (!fused_x_applies(A, mp) || A->n_rows == 0) return VBCSR_OK;
+    const size_t panel = (size_t)A->n_rows * (size_t)k;
+    if (mp.xkind == kXSplit) {
+        int rc = grow(A, &A->xbf, &A->xbf_elems, 2 * panel, s, "alloc split copies of the Chebyshev vectors");
+        if (rc) return rc;
+        xs[0] = A->xbf;
+        xs[1] = A->xbf + panel;
+    } else {
+        int rc = grow(A, &A->xconv, &A->xconv_elems, 2 * panel, s, "alloc FP32 copies of the Chebyshev vectors");
+        if (rc) return rc;
+        xs[0] = A->xconv;
+        xs[1] = A->xconv + panel;
+    }
+    return VBCSR_OK;
+}
+
+
 extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
                                double *moments, double *work, double *ckpt, int64_t ckpt_every, int precision,
                                void *stream) {
@@ -1212,6 +1305,8 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     if (k < 1 || n_moments < 1) return fail(VBCSR_ERR_INVALID_ARG, "k and n_moments must be >= 1");
     if (!R || !moments || !work || ldr < k) return fail(VBCSR_ERR_INVALID_ARG, "R / moments / work / ldr");
     if (ckpt && ckpt_every < 1) return fail(VBCSR_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
+        return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
     cudaStream_t s = (cudaStream_t)stream;
     // complex panels are handled by the real copy and dot kernels as cw = 2 real
     // columns per complex one (the dot of interleaved pairs is Re sum(conj(R) t))
@@ -1219,6 +1314,11 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     const int64_t N = A->n_rows, panel = N * k * cw;
     const double scale = 1.0 / ((double)N * (double)k);
     double *buf[2] = {work, work + panel};
+    void *xs[2] = {nullptr, nullptr};
+    if (n_moments > 1) {
+        int rc = cheb_fused_buffers(A, k, precision, xs, s);
+        if (rc) return rc;
+    }
 
     int64_t used = 0;
     CUDA_TRY(launch_dot_panels(true, N, k * cw, R, ldr * cw, R, ldr * cw, A->partials, kPartialsCap, &used, s),
@@ -1232,7 +1332,9 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     epi.ldr = ldr;
     // t_1 = H~ R  -> buf[1];  t_0 (a copy of R) -> buf[0]
     epi.dot_out = moments + 1;
-    int rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale);
+    // with the fused form, t_n is also kept converted in xs[n & 1]
+    const FusedX fx0 = {nullptr, xs[1]};
+    int rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale, xs[1] ? &fx0 : nullptr);
     if (rc) return rc;
     auto store_pair = [&](int64_t m, const double *tm, int64_t ldm, const double *tm1) -> int {
         if (!ckpt || m % ckpt_every) return VBCSR_OK;
@@ -1248,7 +1350,8 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     for (int64_t n = 1; n + 1 < n_moments; ++n) {
         double *tn = buf[n & 1], *tprev = buf[(n + 1) & 1];
         epi.dot_out = moments + n + 1;
-        rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale);
+        const FusedX fx = {xs[n & 1], xs[(n + 1) & 1]};
+        rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale, xs[0] ? &fx : nullptr);
         if (rc) return rc;
         if ((rc = store_pair(n, tn, k, tprev))) return rc;
     }
@@ -1256,9 +1359,11 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
 }
 
 extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t M,
-                                        const double *grad_mu, const double *ckpt, int64_t E, double *dvalues,
-                                        double *work, int precision, void *stream) {
+                                        const double *grad_mu, const double *ckpt, int64_t E, double d_scale,
+                                        double *dvalues, double *work, int precision, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
+    if (!(d_scale != 0.0) || d_scale != d_scale || d_scale - d_scale != 0.0)
+        return fail(VBCSR_ERR_INVALID_ARG, "d_scale = %g", d_scale);
     if (A->dtype != VBCSR_F64) return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 operator");
     if (A->n_rows != A->n_cols) return fail(VBCSR_ERR_INVALID_ARG, "operator is not square");
     if (k < 1 || M < 1 || E < 1) return fail(VBCSR_ERR_INVALID_ARG, "k, n_moments and ckpt_every must be >= 1");
@@ -1311,7 +1416,7 @@ extern "C" int vbcsr_chebyshev_backward(vbcsr_t *A, int64_t k, const double *R, 
         }
         SddmmArgs a = sddmm_args(A);
         a.k = cnt * k;
-        a.alpha = 1.0;
+        a.alpha = 1.0 / d_scale;
         a.beta = first ? 0.0 : 1.0;
         a.A = L;
         a.lda = wide;
@@ -1344,6 +1449,13 @@ extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t
         CUDA_TRY(launch_finalize_dot(A->partials, used, scale, out, s), "dot");
         return VBCSR_OK;
     };
+    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
+        return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+    void *xs[2] = {nullptr, nullptr};
+    if (M > 3) {
+        int rc = cheb_fused_buffers(A, k, precision, xs, s);
+        if (rc) return rc;
+    }
     int rc = self_dot(R, ldr, moments);                                     // mu_0
     if (rc || M == 1) return rc;
     vbcsr_epilogue_t epi;
@@ -1351,7 +1463,10 @@ extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t
     epi.R = R;
     epi.ldr = ldr;
     epi.dot_out = moments + 1;                                             // mu_1 = <t_1, t_0>
-    if ((rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale))) return rc;
+    const FusedX fx0 = {nullptr, xs[1]};
+    if ((rc = run_product(A, false, k, 1.0, R, ldr, 0.0, buf[1], k, &epi, precision, s, scale,
+                          xs[1] ? &fx0 : nullptr)))
+        return rc;
     CUDA_TRY(launch_copy_panel(N, k * cw, R, ldr * cw, buf[0], k * cw, s), "copy R");
     // t_n in buf[n & 1]; raw dots <t_n, t_n> -> moments[2n], <t_{n+1}, t_n> -> moments[2n+1]
     for (int64_t n = 1;; ++n) {
@@ -1361,7 +1476,10 @@ extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t
         epi.R = tn;
         epi.ldr = k;
         epi.dot_out = moments + 2 * n + 1;
-        if ((rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale))) return rc;
+        const FusedX fx = {xs[n & 1], xs[(n + 1) & 1]};
+        if ((rc = run_product(A, false, k, 2.0, tn, k, -1.0, tprev, k, &epi, precision, s, scale,
+                              xs[0] ? &fx : nullptr)))
+            return rc;
     }
     CUDA_TRY(launch_kpm_fixup(moments, M, s), "moment fix-up");
     return VBCSR_OK;
@@ -1376,6 +1494,16 @@ extern "C" int vbcsr_kpm_dos(const double *moments, int64_t n_moments, int kerne
     if (!moments || (n_x > 0 && (!x || !dos))) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
     CUDA_TRY(launch_kpm_dos(moments, n_moments, kernel == VBCSR_KPM_JACKSON, x, n_x, dos, (cudaStream_t)stream),
              "kpm dos");
+    return VBCSR_OK;
+}
+
+extern "C" int vbcsr_kpm_gap(const double *energies, const double *dos, int64_t n, double reference,
+                             double threshold, double *out, void *stream) {
+    if (n < 1) return fail(VBCSR_ERR_INVALID_ARG, "n = %lld", (long long)n);
+    if (!energies || !dos || !out) return fail(VBCSR_ERR_INVALID_ARG, "NULL argument");
+    if (reference != reference || threshold != threshold)
+        return fail(VBCSR_ERR_INVALID_ARG, "reference / threshold is NaN");
+    CUDA_TRY(launch_kpm_gap(energies, dos, n, reference, threshold, out, (cudaStream_t)stream), "kpm gap");
     return VBCSR_OK;
 }
 
@@ -1853,19 +1981,41 @@ extern "C" int vbcsr_check(vbcsr_t *A, void *stream) {
 // not allocate once it runs. Such a caller creates the operator once at
 // start-up and later calls this entry point, which allocates nothing: the two
 // work panels of the recurrence live in the fixed array below, which every
-// GPU that loads the library holds until the process exits.
+// GPU that loads the library holds until the process exits. A mixed-precision
+// mode also needs the handle's copies of the values and its converted-X
+// buffers; those are built by an ordinary call, so this entry point only runs
+// a mode whose buffers an earlier call on the handle already made large enough.
 
-static constexpr int64_t kNoAllocPanelElems = int64_t(1) << 20;   // n_rows * k per panel, at most
+static constexpr int64_t kNoAllocPanelElems = int64_t(1) << 20;   // real elements per panel, at most
 static __device__ __align__(256) double g_cheb_scratch[2 * kNoAllocPanelElems];   // 16 MiB
 
 extern "C" int vbcsr_chebyshev_noalloc(vbcsr_t *A, int64_t k, const double *R, int64_t ldr, int64_t n_moments,
                                        double *moments, int precision, void *stream) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (k < 1) return fail(VBCSR_ERR_INVALID_ARG, "k must be >= 1");
-    if (A->n_rows > kNoAllocPanelElems / k)
+    if (A->dtype != VBCSR_F64 && A->dtype != VBCSR_C128)
+        return fail(VBCSR_ERR_UNSUPPORTED, "the recurrence needs an FP64 or complex operator");
+    if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)
+        return fail(VBCSR_ERR_INVALID_ARG, "precision %d", precision);
+    // a complex panel holds two doubles per element
+    const int64_t cw = A->dtype == VBCSR_C128 ? 2 : 1;
+    if (A->n_rows > kNoAllocPanelElems / (k * cw))
         return fail(VBCSR_ERR_UNSUPPORTED,
-                    "n_rows * k = %lld * %lld exceeds the fixed work area of %lld elements per panel",
-                    (long long)A->n_rows, (long long)k, (long long)kNoAllocPanelElems);
+                    "n_rows * k%s = %lld * %lld exceeds the fixed work area of %lld doubles per panel",
+                    cw == 2 ? " * 2 (complex)" : "", (long long)A->n_rows, (long long)k,
+                    (long long)kNoAllocPanelElems);
+    if (precision != VBCSR_PREC_NATIVE && A->dtype == VBCSR_F64) {
+        // the mode's value copy and converted-X buffers must exist already
+        const ModePlan mp = plan_mode(A, false, k, precision);
+        bool ready = mode_buffers_ready(A, mp, A->n_cols, k);
+        if (ready && n_moments > 1 && fused_x_applies(A, mp))
+            ready = (mp.xkind == kXSplit ? A->xbf_elems : A->xconv_elems) >= 2 * (size_t)A->n_rows * (size_t)k;
+        if (!ready)
+            return fail(VBCSR_ERR_UNSUPPORTED,
+                        "precision %d needs buffers this handle has not built yet: make one vbcsr_chebyshev "
+                        "call in this precision with at least %lld columns first",
+                        precision, (long long)k);
+    }
     // set-up, once per device: host code cannot use g_cheb_scratch as a device
     // address, so ask the runtime for it with that device current
     static std::mutex mu;

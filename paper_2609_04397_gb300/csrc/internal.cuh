@@ -93,6 +93,11 @@ struct ProdArgs {
     uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
     int mma_staged;         // tensor-core forward: 1 = value panels staged in shared memory
     int value_ring;         // CUDA-core forward, FP32 values, k >= 4: read them through the ring
+    void *xs_out;           // tensor-core forward (plain kernel) only, or NULL: every output
+                            // element is also written here, [rows of Y, k] with leading
+                            // dimension k, in the form the kernel reads X (FP32, or the packed
+                            // bf16 pieces of BF16X2), so that the next Chebyshev step needs no
+                            // conversion pass
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
@@ -256,6 +261,9 @@ cudaError_t launch_shift_scale(bool cplx, const WorkItem *items, int64_t n_items
 // kernel polynomial method
 cudaError_t launch_kpm_fixup(double *mu, int64_t M, cudaStream_t s);
 cudaError_t launch_kpm_dos(const double *mu, int64_t M, int jackson, const double *x, int64_t nx, double *out,
+                           cudaStream_t s);
+// out = {E[lo], E[hi]} of the below-threshold run around the grid point nearest ref, or NaN, NaN
+cudaError_t launch_kpm_gap(const double *E, const double *D, int64_t n, double ref, double thr, double *out,
                            cudaStream_t s);
 // dst[rows, k] (ld ldd) = src (ld lds), FP64
 cudaError_t launch_copy_panel(int64_t rows, int64_t k, const double *src, int64_t lds, double *dst,

@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "split.cuh"
 
 namespace vbcsr {
 
@@ -272,15 +273,6 @@ cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, c
     int64_t need = (n + 255) / 256;
     convert_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
-}
-
-// the operand pieces of the BF16X2 mode, formed once per value as the kernel
-// would form them (FP32 value v, hi = bf16_rn(v), lo = bf16_rn(v - hi))
-__device__ __forceinline__ uint32_t bf16_pieces(double x) {
-    const float v = (float)x;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
 }
 
 __global__ void split_bf16_kernel(const double *in, uint32_t *out, int64_t n) {
@@ -612,6 +604,84 @@ cudaError_t launch_kpm_dos(const double *mu, int64_t M, int jackson, const doubl
     if (nx == 0) return cudaSuccess;
     const int64_t grid = (nx + 255) / 256;
     kpm_dos_kernel<<<(unsigned)grid, 256, 0, s>>>(mu, M, jackson, x, nx, out);
+    return cudaGetLastError();
+}
+
+// Gap of a density of states on an energy grid around a reference energy: one
+// CTA. (1) i0 = the grid point nearest the reference (smallest index on a
+// tie); (2) the nearest points left and right of i0 whose DOS is not below
+// the threshold (NaN counts as not below); the gap is the run between them.
+__global__ void __launch_bounds__(1024) kpm_gap_kernel(const double *E, const double *D, int64_t n, double ref,
+                                                        double thr, double *out) {
+    __shared__ double s_d[32];
+    __shared__ long long s_i[32];
+    __shared__ long long s_lr[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double bd = INFINITY;
+    long long bi = n;
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+        const double dj = fabs(E[j] - ref);
+        if (dj < bd) {          // j increases along the thread's loop: the first minimum is kept
+            bd = dj;
+            bi = j;
+        }
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+        const double od = __shfl_xor_sync(0xffffffffu, bd, m);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, m);
+        if (od < bd || (od == bd && oi < bi)) {
+            bd = od;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        s_d[warp] = bd;
+        s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+            if (s_d[w] < s_d[0] || (s_d[w] == s_d[0] && s_i[w] < s_i[0])) {
+                s_d[0] = s_d[w];
+                s_i[0] = s_i[w];
+            }
+    }
+    __syncthreads();
+    const long long i0 = s_i[0];
+    long long left = -1, right = n;
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) {
+        if (!(D[j] < thr)) {
+            if (j < i0 && j > left) left = j;
+            if (j > i0 && j < right) right = j;
+        }
+    }
+    for (int m = 16; m > 0; m >>= 1) {
+        left = max(left, (long long)__shfl_xor_sync(0xffffffffu, left, m));
+        right = min(right, (long long)__shfl_xor_sync(0xffffffffu, right, m));
+    }
+    if (lane == 0) {
+        s_lr[0][warp] = left;
+        s_lr[1][warp] = right;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            left = max(left, s_lr[0][w]);
+            right = min(right, s_lr[1][w]);
+        }
+        if (i0 >= n || !(D[i0] < thr)) {
+            out[0] = NAN;
+            out[1] = NAN;
+        } else {
+            out[0] = E[left + 1];
+            out[1] = E[right - 1];
+        }
+    }
+}
+
+cudaError_t launch_kpm_gap(const double *E, const double *D, int64_t n, double ref, double thr, double *out,
+                           cudaStream_t s) {
+    kpm_gap_kernel<<<1, 1024, 0, s>>>(E, D, n, ref, thr, out);
     return cudaGetLastError();
 }
 

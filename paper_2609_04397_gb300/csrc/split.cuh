@@ -23,6 +23,18 @@ __device__ __forceinline__ float round_tf32(float v) {
 
 __device__ __forceinline__ float round_bf16(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// The operand pieces of the BF16X2 mode as one 32-bit word, formed once per
+// value as the kernels would form them: FP32 value v, hi = bf16_rn(v) in the
+// low half, lo = bf16_rn(v - hi) in the high half. Used by the one-pass split
+// of values and X and by the tensor-core epilogue that writes the next
+// Chebyshev vector in this form.
+__device__ __forceinline__ uint32_t bf16_pieces(double x) {
+    const float v = (float)x;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    return (uint32_t)__bfloat16_as_ushort(h) | ((uint32_t)__bfloat16_as_ushort(l) << 16);
+}
+
 // An operand as its pieces, or (hi only) an FP32 accumulator.
 template <int MODE>
 struct SplitF {

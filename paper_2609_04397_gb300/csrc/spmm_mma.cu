@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "split.cuh"
 
 namespace vbcsr {
 
@@ -110,6 +111,14 @@ __device__ __forceinline__ void step(float (&acc)[4], const Pieces &ag, const Pi
     }
 }
 
+// The output element as the forward kernel reads X (FP32, or the packed bf16
+// pieces of BF16X2), written by the epilogue for the next Chebyshev step.
+template <int MODE, typename TX>
+__device__ __forceinline__ float xs_form(TX v) {
+    if (MODE == kBF16X2Presplit) return __uint_as_float(bf16_pieces((double)v));
+    return (float)v;
+}
+
 // Resident CTAs (of 4 warps) per SM and the forward kernel's step group U, per
 // mode and column-tile count. Measured on GB300 (50k-atom zinc-blende operator,
 // one GPU, variants side by side): the pre-split BF16X2 kernel at NT = 4 runs
@@ -141,6 +150,7 @@ __global__ void __launch_bounds__(128, MmaShape<MODE, NT>::CTAS) mma_product_ker
     TX *__restrict__ Y = static_cast<TX *>(a.Y);
     const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
     const TX *__restrict__ R = static_cast<const TX *>(a.R);
+    float *__restrict__ XS = static_cast<float *>(a.xs_out);
     const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
     const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
@@ -288,6 +298,7 @@ __global__ void __launch_bounds__(128, MmaShape<MODE, NT>::CTAS) mma_product_ker
                         if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
                         *yp = v;
                         if (a.partials || a.item_partials) dot += (double)R[row * a.ldr + col] * (double)v;
+                        if (!TRANS && XS) XS[row * a.k + col] = xs_form<MODE, TX>(v);
                     }
                 }
             }

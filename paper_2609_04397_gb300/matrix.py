@@ -435,20 +435,21 @@ def kpm_dos(moments: torch.Tensor, x: torch.Tensor, kernel: str = "jackson") -> 
     return out
 
 
-def kpm_gap(energies, dos, reference: float, threshold: float):
-    """Width of the largest interval around `reference` on the energy grid
-    where the DOS stays below `threshold` (host-side post-processing of the
-    reconstructed DOS): returns (E_low, E_high) or None if dos(reference) is
-    above the threshold."""
-    E = np.asarray(energies, dtype=np.float64)
-    D = np.asarray(dos, dtype=np.float64)
-    i = int(np.argmin(np.abs(E - reference)))
-    if D[i] >= threshold:
+def kpm_gap(energies: torch.Tensor, dos: torch.Tensor, reference: float, threshold: float):
+    """Band gap read off a density of states on an energy grid (device FP64
+    tensors, energies increasing; see vbcsr_kpm_gap): the widest run of grid
+    points around the one nearest `reference` whose DOS stays below
+    `threshold`, as (E_low, E_high), or None when the reference lies inside a
+    band. The search runs in the library; only the two energies come back."""
+    energies = energies.contiguous()
+    dos = dos.contiguous()
+    if energies.shape != dos.shape or energies.dim() != 1:
+        raise ValueError("energies and dos must be 1-D tensors of one length")
+    out = torch.empty(2, dtype=torch.float64, device=energies.device)
+    check(lib().vbcsr_kpm_gap(ctypes.c_void_p(energies.data_ptr()), ctypes.c_void_p(dos.data_ptr()),
+                              energies.numel(), float(reference), float(threshold), ctypes.c_void_p(out.data_ptr()),
+                              _stream(energies.device)), "vbcsr_kpm_gap")
+    lo, hi = out.tolist()
+    if lo != lo:
         return None
-    lo = i
-    while lo > 0 and D[lo - 1] < threshold:
-        lo -= 1
-    hi = i
-    while hi + 1 < len(E) and D[hi + 1] < threshold:
-        hi += 1
-    return float(E[lo]), float(E[hi])
+    return lo, hi

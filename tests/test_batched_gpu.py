@@ -143,3 +143,44 @@ def test_schedule_flags_round_trip_and_validation():
         assert lib().vbcsr_set_schedule(H.handle, bad, 0) != 0
     assert lib().vbcsr_set_schedule(H.handle, 1, 3) != 0
     assert lib().vbcsr_set_schedule(H.handle, 1 | 2 | 4 | 8, 4) == 0
+
+
+def test_full_size_batched_workload_every_element():
+    """The batched workload at full size: 256 structures of 50-2000 atoms
+    (log-uniform, b in {4, 9, 13}, 5 A cutoff), FP32, k = 8, in its autotuned
+    schedule and replayed from a captured CUDA graph: every output element
+    against the per-structure oracle (FP64 on the FP32-rounded inputs)."""
+    import os
+    w, H, vals = _batched(n_structs=256, n_max=2000, seed=0)
+    assert H.info.n_structs == 256
+    k = 8
+    X = np.random.default_rng(0).standard_normal((w.pattern.n_cols, k)).astype(np.float32).astype(np.float64)
+    Xd = torch.from_numpy(X).float().cuda()
+    nth = os.cpu_count() or 1
+    voff = w.pattern.value_offset()
+    coff = np.concatenate([[0], np.cumsum(w.pattern.col_bsize.astype(np.int64))])
+    sref, sabs = [], []
+    for s, part in enumerate(w.parts):
+        b0, b1 = w.struct_brow_offsets[s], w.struct_brow_offsets[s + 1]
+        v = vals[voff[w.pattern.block_row_ptr[b0]]:voff[w.pattern.block_row_ptr[b1]]]
+        Xs = X[coff[b0]:coff[b1]]
+        sref.append(oracle.spmm(part, v, Xs, nthreads=nth))
+        sabs.append(oracle.spmm(part, np.abs(v), np.abs(Xs), nthreads=nth))
+    ref, scale = np.concatenate(sref), np.concatenate(sabs)
+    H.autotune(k)
+    got = H.spmm(Xd).cpu().numpy().astype(np.float64)
+    assert rel_fro(got, ref) <= TOL_MIXED
+    check_elementwise(got, ref, scale, 1e-4)
+    Y = torch.empty(w.pattern.n_rows, k, dtype=torch.float32, device="cuda:0")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        H.spmm(Xd, 1.0, 0.0, Y)
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        H.spmm(Xd, 1.0, 0.0, Y)
+    Y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(Y.cpu().numpy().astype(np.float64), got)

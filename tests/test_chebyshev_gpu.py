@@ -85,15 +85,20 @@ def test_moment_loss_gradient_matches_oracle(E):
 
 
 def test_gradient_through_shift_scale_and_fd():
-    """dL/dH (original values) = dL/dH~ / d, checked against central finite
-    differences (h = 1e-6) of the oracle's loss on 50 sampled entries."""
-    from paper_2609_04397_gb300 import chebyshev_moments, diagonal_mask, shift_scale
+    """Moments of H~ = (H - c I) / d formed in the library from the values of
+    H; dL/dH (original values) = dL/dH~ / d, also formed in the library,
+    checked against the oracle's reverse-mode gradient and against central
+    finite differences (h = 1e-6) of the oracle's loss on 50 sampled entries."""
+    from paper_2609_04397_gb300 import chebyshev_moments
     w, H, vt, c, d, R = _grad_case(300, 4, 30, 10)
-    mask = diagonal_mask(H)
     v = torch.from_numpy(w.values).cuda().requires_grad_(True)
-    mu = chebyshev_moments(H, shift_scale(v, mask, c, d), torch.from_numpy(R).cuda(), 30, ckpt_every=10)
+    mu = chebyshev_moments(H, v, torch.from_numpy(R).cuda(), 30, ckpt_every=10, c=c, d=d)
+    ref_mu = oracle.chebyshev_moments(w.pattern, vt, R, 30)
+    assert np.abs(mu.detach().cpu().numpy() - ref_mu).max() <= 1e-12
     (mu ** 2).sum().backward()
     g = v.grad.cpu().numpy()
+    ref = oracle.moment_loss_grad(w.pattern, vt, R, 30) / d
+    assert np.linalg.norm(g - ref) <= 1e-12 * np.linalg.norm(ref)
 
     h = 1e-6
     idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
@@ -133,24 +138,35 @@ def test_matmul_autograd():
     assert np.linalg.norm(v.grad.cpu().numpy() - ref_dv) <= 1e-12 * np.linalg.norm(ref_dv)
 
 
-@pytest.mark.skipif(os.environ.get("VBCSR_FULL_FD") != "1", reason="set VBCSR_FULL_FD=1 (minutes of CPU time)")
 def test_amorphous_20k_gradient_fd_50_entries():
     """Full differentiation workload: 20k amorphous atoms, 30 moments, k = 16,
     checkpoints every 10 steps; GPU gradient of L = sum mu_n^2 against central
-    differences (h = 1e-6) of the oracle on 50 sampled stored entries."""
+    differences (h = 1e-6) of the oracle on 50 sampled stored entries, against
+    the oracle's exact reverse-mode gradient on every entry, and the gradient
+    with FP32 block products against the FP64 one (within 1e-4)."""
+    import time
     from paper_2609_04397_gb300 import chebyshev_moments
     w, H, vt, c, d, R = _grad_case(20000, 16, 30, 10)
-    v = torch.from_numpy(vt).cuda().requires_grad_(True)
-    (chebyshev_moments(H, v, torch.from_numpy(R).cuda(), 30, ckpt_every=10) ** 2).sum().backward()
-    g = v.grad.cpu().numpy()
+    Rd = torch.from_numpy(R).cuda()
+    grads = {}
+    for mode in ("native", "f32"):
+        v = torch.from_numpy(vt).cuda().requires_grad_(True)
+        (chebyshev_moments(H, v, Rd, 30, ckpt_every=10, precision=mode) ** 2).sum().backward()
+        grads[mode] = v.grad.cpu().numpy()
+    g = grads["native"]
+    rel32 = np.linalg.norm(grads["f32"] - g) / np.linalg.norm(g)
+    assert rel32 <= 1e-4, rel32
     nthreads = os.cpu_count() or 1
     pat = w.pattern
 
+    t0 = time.perf_counter()
     h = 1e-6
     idx = np.random.default_rng(0).choice(len(vt), 50, replace=False)
     fd = np.array([central_difference(pat, vt, R, 30, i, h, nthreads) for i in idx])
     worst = np.abs(fd - g[idx]).max() / np.abs(g[idx]).max()
-    print(f"amorphous 20k: max-norm relative FD deviation over 50 entries = {worst:.3e}")
+    print(f"amorphous 20k: max-norm relative FD deviation over 50 entries = {worst:.3e} "
+          f"({time.perf_counter() - t0:.0f} s of oracle time on {nthreads} threads); "
+          f"FP32-product gradient vs FP64: {rel32:.2e}")
     assert worst <= 1e-6
     # and the exact reverse-mode gradient of the oracle, every stored entry
     ref = oracle.moment_loss_grad(pat, vt, R, 30)

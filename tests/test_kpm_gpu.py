@@ -70,5 +70,26 @@ def test_dos_pipeline_and_gap_on_a_gapped_operator():
     xs = x.cpu().numpy()
     dx = xs[1] - xs[0]
     assert abs(np.sum(rho[xs < 0.05]) * dx - 400 / 600) < 2e-2
-    lo, hi = kpm_gap(xs, rho, 0.05, 0.05 * rho.max())
+    thr = 0.05 * rho.max()
+    lo, hi = kpm_gap(x, torch.from_numpy(rho).cuda(), 0.05, thr)
     assert -0.2 < lo < 0.0 and 0.1 < hi < 0.3
+    assert (lo, hi) == oracle.kpm_gap(xs, rho, 0.05, thr)
+
+
+def test_gap_search_matches_oracle_exactly():
+    """vbcsr_kpm_gap against the oracle's walk on many random grids: the same
+    two grid energies (or none), bit for bit, including ties of the nearest
+    grid point, NaN densities, runs that reach the grid's ends, references
+    outside the grid and grids longer than the CTA."""
+    from paper_2609_04397_gb300 import kpm_gap
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        n = int(rng.choice([1, 2, 7, 64, 1023, 1024, 1025, 5000]))
+        E = np.sort(rng.uniform(-1, 1, n)) if trial % 3 else np.linspace(-1, 1, n)
+        D = rng.uniform(0, 1, n) ** 3
+        if trial % 5 == 0:
+            D[rng.integers(0, n, max(1, n // 50))] = np.nan
+        ref = float(rng.uniform(-1.2, 1.2)) if trial % 7 else float(0.5 * (E[0] + E[-1]))
+        thr = float(rng.uniform(0.05, 0.6))
+        got = kpm_gap(torch.from_numpy(E).cuda(), torch.from_numpy(D).cuda(), ref, thr)
+        assert got == oracle.kpm_gap(E, D, ref, thr), (trial, n, ref, thr)

@@ -205,3 +205,38 @@ def test_fp32_value_ring_matches_direct_reads(k):
             got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
             np.testing.assert_array_equal(got_ring, got_direct)
             check_elementwise(got_ring.astype(np.float64), ref, scale, TOL_F64 if prec == "df32" else 1e-4)
+
+
+
+@pytest.mark.parametrize("mode", ["tf32", "tf32x3", "bf16x2"])
+@pytest.mark.parametrize("k", [4, 16, 20])
+def test_recurrence_with_converted_vectors_matches_per_step_conversion(mode, k):
+    """In the tensor-core modes the Chebyshev recurrence keeps each t_n also
+    in the form the kernel reads (written by the previous step's epilogue)
+    instead of converting it before every product. The same recurrence run
+    step by step through vbcsr_spmm_ex (which converts X at every call) gives
+    the same moments bit for bit; the doubling moments stay within 1e-5 of
+    the oracle's."""
+    import oracle
+    w = syn.tiny_multispecies(0)
+    c, d = oracle.cheb_scale(w.pattern, w.values)
+    vt = oracle.shift_scale_values(w.pattern, w.values, c, d)
+    H = _handle(w.pattern, vt)
+    Rn = syn.rademacher_panel(w.pattern.n_rows, k, 0)
+    R = _dev(Rn)
+    M = 40
+    fused = H.chebyshev(R, M, precision=mode)[0]
+    mu = torch.empty(M, dtype=torch.float64, device="cuda:0")
+    mu[0] = (R * R).sum() / R.numel()
+    T = [R.clone(), torch.empty_like(R)]
+    H.spmm_ex(R, 1.0, 0.0, T[1], R=R, dot_out=mu[1:2], precision=mode)
+    for n in range(1, M - 1):
+        # t_{n+1} = 2 H~ t_n - t_{n-1}, overwriting t_{n-1}
+        H.spmm_ex(T[n & 1], 2.0, -1.0, T[(n + 1) & 1], R=R, dot_out=mu[n + 1:n + 2], precision=mode)
+    mu[1:] *= 1.0 / R.numel()          # the library multiplies the raw dot by 1 / (N k)
+    assert torch.equal(fused[1:], mu[1:]), (fused - mu).abs().max().item()
+    ref = oracle.chebyshev_moments(w.pattern, vt, Rn, M)
+    tol = 1e-5 if mode != "tf32" else 1e-2
+    assert np.abs(fused.cpu().numpy() - ref).max() <= tol
+    kpm = H.kpm_moments(R, M, precision=mode).cpu().numpy()
+    assert np.abs(kpm - ref).max() <= tol

@@ -64,8 +64,8 @@ def test_reference_arm_prints_one_line():
     import json
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
-                       timeout=600)
+                        "--steps", "1", "--warmup", "0", "--atoms", "50000"], env=env, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0

@@ -522,3 +522,60 @@ def test_complex_chebyshev_moments_and_gershgorin():
     vt0 = oracle.shift_scale_values(p0, v0.real, c0, d0)
     assert np.allclose(oracle.chebyshev_moments_complex(p0, vt0.astype(np.complex128), Rr, 10),
                        oracle.chebyshev_moments(p0, vt0, Rr, 10), atol=1e-13)
+
+
+def test_complex_gershgorin_matches_dense_definition():
+    """Complex Hermitian O(k) at k != 0: the bounds are min / max over scalar
+    rows of Re O_rr -/+ sum_{c != r} |O_rc|, computed here from the dense
+    matrix (a modulus / real-part mix-up or a dropped imaginary part fails)."""
+    w = syn.zincblende_crystal(1)
+    for kf in ([0.21, -0.13, 0.34], [0.37, 0.12, 0.05], [0.07, 0.41, -0.29]):
+        rb, cb, ptr, cols, vals = oracle.kspace_blocks(w.bsize, w.edge_i, w.edge_j, w.edge_R, w.edge_values, kf)
+        pat = BlockPattern(rb, cb, ptr, cols)
+        D = oracle.to_dense(pat, vals.real) + 1j * oracle.to_dense(pat, vals.imag)
+        assert np.abs(D.imag).max() > 0.1            # a genuinely complex operator
+        d = np.diag(D).real
+        rad = np.abs(D).sum(axis=1) - np.abs(np.diag(D))
+        lo, hi = oracle.gershgorin_bounds_complex(pat, vals)
+        assert abs(lo - (d - rad).min()) <= 1e-13 * abs(lo)
+        assert abs(hi - (d + rad).max()) <= 1e-13 * abs(hi)
+        # the real-part-only radius (a plausible mistake) gives different bounds
+        rad_re = np.abs(D.real).sum(axis=1) - np.abs(np.diag(D.real))
+        assert abs(hi - (d + rad_re).max()) > 1e-6
+
+
+def test_kpm_gap_on_a_step_density():
+    """DOS 1 outside |E| < 0.3 and 0 inside, on a 401-point grid: the gap
+    around 0 is the run of grid points with |E| < 0.3 (indices 141 .. 259),
+    None inside a band, and a run that reaches the grid's end stops there."""
+    E = np.linspace(-1.0, 1.0, 401)
+    j = np.arange(401)
+    D = np.where((j > 140) & (j < 260), 0.0, 1.0)
+    assert oracle.kpm_gap(E, D, 0.0, 0.5) == (E[141], E[259])
+    assert oracle.kpm_gap(E, D, 0.29, 0.5) == (E[141], E[259])
+    assert oracle.kpm_gap(E, D, 0.6, 0.5) is None
+    # the nearest grid point decides: a reference between two points, ties to the lower index
+    assert oracle.kpm_gap(E, D, 0.5 * (E[259] + E[260]), 0.5) == (E[141], E[259])
+    D2 = np.where(j > 350, 0.0, 1.0)
+    assert oracle.kpm_gap(E, D2, 0.9, 0.5) == (E[351], E[400])
+    # NaN is not below the threshold
+    D3 = D.copy()
+    D3[150] = np.nan
+    assert oracle.kpm_gap(E, D3, 0.0, 0.5) == (E[151], E[259])
+
+
+def test_kpm_gap_of_a_gapped_spectrum():
+    """The whole DOS pipeline on a diagonal operator with eigenvalues filling
+    [-0.9, -0.4] and [0.4, 0.9] (exact traces): the Jackson-damped DOS leaks
+    into the gap by a few kernel widths pi / M, so the gap read at 2 % of the
+    DOS maximum lies inside (-0.4, 0.4) and within 6 pi / M of its edges."""
+    h = np.concatenate([np.linspace(-0.9, -0.4, 300), np.linspace(0.4, 0.9, 300)])
+    n = len(h)
+    pat = BlockPattern(np.ones(n), np.ones(n), np.arange(n + 1), np.arange(n))
+    M = 256
+    mu = oracle.kpm_moments_doubling(pat, h, np.sqrt(n) * np.eye(n), M)
+    x = np.linspace(-0.999, 0.999, 2001)
+    rho = oracle.kpm_dos(mu, x)
+    lo, hi = oracle.kpm_gap(x, rho, 0.0, 0.02 * rho.max())
+    assert -0.4 < lo < -0.4 + 6 * np.pi / M
+    assert 0.4 - 6 * np.pi / M < hi < 0.4

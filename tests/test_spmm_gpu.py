@@ -449,3 +449,58 @@ def test_registry_with_very_many_block_sizes():
     got = H.spmm(_dev(X)).cpu().numpy()
     ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
     check_elementwise(got, ref, scale, TOL_F64)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("schedule", ["persistent", "bucketed"])
+@pytest.mark.parametrize("b", [4, 8, 13])
+def test_bsr_backend_native(b, schedule, dtype):
+    """Uniform-block operators (the BSR backend) in the operator's own
+    arithmetic, FP64 and FP32, forward and adjoint, element by element against
+    the oracle at k = 1, 3, 8, 16, 33 (FP32 operators at the FP32 tolerance)."""
+    pat = syn.random_pattern(70, 70, (b,), 0.12, 40 + b, empty_rows=2, unsorted=True)
+    vals = syn.random_values(pat, 40 + b)
+    if dtype == torch.float32:
+        vals = vals.astype(np.float32).astype(np.float64)
+    H = _handle(pat, vals, dtype)
+    assert H.backend == "bsr"
+    H.set_schedule(schedule)
+    tol = TOL_F64 if dtype == torch.float64 else TOL_MIXED
+    for k in (1, 3, 8, 16, 33):
+        _run_forward(H, pat, vals, k, 1.0, 0.0, seed=k, tol=tol)
+        _run_forward(H, pat, vals, k, -0.5, 2.0, ld_extra=3, seed=k + 1, tol=tol)
+        Xa = np.random.default_rng(k).standard_normal((pat.n_rows, k))
+        if dtype == torch.float32:
+            Xa = Xa.astype(np.float32).astype(np.float64)
+        got = H.spmm_adjoint(_dev(Xa, dtype)).cpu().numpy()
+        ref, scale = adjoint_ref(pat, vals, Xa, 1.0, 0.0, None)
+        check_elementwise(got, ref, scale, tol)
+
+
+@pytest.mark.parametrize("kind", ["bsr", "vbcsr"])
+def test_structural_domain_full_size_sampled_rows(kind):
+    """The ~500 MiB structural domains of the kernel benchmark (Sec. IV; BSR
+    b = 8 and variable blocks b in [9, 20]) at k = 1 and 16, FP64 and
+    double-FP32 products: every output of 64 sampled block rows against the
+    oracle."""
+    w = syn.domain(kind)
+    pat = w.pattern
+    H = _handle(pat, w.values)
+    assert H.backend == kind
+    rng = np.random.default_rng(1)
+    rows = np.sort(rng.choice(pat.n_brows, 64, replace=False))
+    roff = np.concatenate([[0], np.cumsum(pat.row_bsize.astype(np.int64))])
+    sel = np.concatenate([np.arange(roff[i], roff[i + 1]) for i in rows])
+    absv = np.abs(w.values)
+    for k in (1, 16):
+        X = syn.normal_panel(pat.n_cols, k, 0)
+        ref = np.zeros((pat.n_rows, k))
+        scale = np.zeros((pat.n_rows, k))
+        for i in rows:
+            ref = oracle.spmm(pat, w.values, X, row_range=(i, i + 1), Y=ref, beta=1.0)
+            scale = oracle.spmm(pat, absv, np.abs(X), row_range=(i, i + 1), Y=scale, beta=1.0)
+        for precision in ("native", "df32"):
+            Y = H.spmm(_dev(X), precision=precision).cpu().numpy()
+            check_elementwise(Y[sel], ref[sel], scale[sel], TOL_F64)
+            assert rel_fro(Y[sel], ref[sel]) <= TOL_F64
+    H.check()
