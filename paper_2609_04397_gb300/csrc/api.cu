@@ -1,6 +1,7 @@
 // C ABI of the library: validation, the planner (shape-class registry,
 // shape-grouped value pages, work items), and dispatch of the product kernels.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -125,6 +126,10 @@ struct vbcsr_matrix {
     bool panelbf_valid = false;
     uint32_t *xbf = nullptr;      // the current X split the same way
     size_t xbf_elems = 0;
+    uint16_t *panelbp = nullptr;  // the BF16X2 pieces of the values as two bf16 planes (hi, then lo)
+    bool panelbp_valid = false;
+    uint16_t *xbp = nullptr;      // the current X as two bf16 planes [rows, pipe_ldp(k)] (hi, then lo)
+    size_t xbp_elems = 0;
     WorkItem *fwd_items = nullptr, *adj_items = nullptr;   // bucketed by row count
     WorkItem *fwd_lpt = nullptr, *adj_lpt = nullptr;       // all items, descending cost
     int64_t n_fwd_items = 0, n_adj_items = 0;
@@ -261,10 +266,21 @@ static void host_parallel(int64_t n, int64_t grain, F f) {
 
 // Longest-processing-time order for the persistent launch: the costliest
 // items (rows x virtual columns) first, so that the queue ends with small ones.
+// Descending-cost order of the persistent launches. Costs are compared in
+// classes about 19 % wide (a quarter of a binary order of magnitude), and
+// items of one class keep page order: the expensive items still come first,
+// so the last items the warps take are the cheap ones, while warps that take
+// consecutive items work on neighbouring block rows, whose X rows they share
+// through the caches (exact-cost order interleaves the block rows of every
+// structure of a batched operator).
+static int cost_class(const WorkItem &w) {
+    const double c = (double)w.B * (double)(w.K + 8);
+    return (int)std::floor(4.0 * std::log2(c));
+}
+
 static void sort_by_cost(std::vector<WorkItem> &items) {
-    std::stable_sort(items.begin(), items.end(), [](const WorkItem &x, const WorkItem &y) {
-        return (int64_t)x.B * (x.K + 8) > (int64_t)y.B * (y.K + 8);
-    });
+    std::stable_sort(items.begin(), items.end(),
+                     [](const WorkItem &x, const WorkItem &y) { return cost_class(x) > cost_class(y); });
 }
 
 static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_t *row_bsize,
@@ -761,6 +777,16 @@ static int refresh_panelbf(vbcsr_t *A, cudaStream_t s) {
     return VBCSR_OK;
 }
 
+static int refresh_panelbp(vbcsr_t *A, cudaStream_t s) {
+    if (A->dtype != VBCSR_F64) return VBCSR_OK;
+    if (!A->panelbp) CUDA_TRY(A->alloc(&A->panelbp, 2 * (size_t)A->panel_elems), "alloc bf16 value planes");
+    CUDA_TRY(launch_split_bf16_planes((const double *)A->panel, A->panelbp, A->panelbp + A->panel_elems,
+                                      A->panel_elems, s),
+             "split values");
+    A->panelbp_valid = true;
+    return VBCSR_OK;
+}
+
 static int refresh_panel32(vbcsr_t *A, cudaStream_t s) {
     if (A->dtype != VBCSR_F64) return VBCSR_OK;
     if (!A->panel32) CUDA_TRY(A->alloc(&A->panel32, (size_t)A->panel_elems), "alloc FP32 value copy");
@@ -824,6 +850,10 @@ extern "C" int vbcsr_set_values(vbcsr_t *A, const void *values, int on_device, v
     }
     if (A->panelbf) {
         int rc = refresh_panelbf(A, s);
+        if (rc) return rc;
+    }
+    if (A->panelbp) {
+        int rc = refresh_panelbp(A, s);
         if (rc) return rc;
     }
     if (A->paneldf) return refresh_paneldf(A, s);
@@ -903,7 +933,7 @@ static int cached_cap(const void *kernel, int warps, size_t smem) {
 }
 
 // Form of X that a product's kernel reads.
-enum { kXAsGiven = 0, kXF32 = 1, kXSplit = 2, kXPairs = 3 };
+enum { kXAsGiven = 0, kXF32 = 1, kXSplit = 2, kXPairs = 3, kXPlanes = 4 };
 
 // Which kernel family serves a product, and which mixed-precision copies of
 // the values and of X it reads (built on first use by run_product).
@@ -914,8 +944,9 @@ struct ModePlan {
     bool csr_kernel;          // the scalar kernel of a CSR-backend operator
     bool split;               // a tensor-core mode on the CUDA cores (thin products, scalar operators)
     bool presplit;            // BF16X2 on operands split once into packed bf16 (hi, lo) words
-    bool need_panel32, need_panelbf, need_paneldf;
-    int xkind;                // kXAsGiven, kXF32, kXSplit or kXPairs
+    bool pipe;                // BF16X2 on the tensor cores, operands as bf16 planes through shared memory
+    bool need_panel32, need_panelbf, need_paneldf, need_panelbp;
+    int xkind;                // kXAsGiven, kXF32, kXSplit, kXPairs or kXPlanes
 };
 
 static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision) {
@@ -933,13 +964,21 @@ static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision
     // and the CUDA-core form of thin products; the staged kernel splits itself, the
     // scalar kernel reads FP32) read values and X split once into packed bf16
     // (hi, lo) words
-    p.presplit = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.csr_kernel &&
+    // the forward tensor-core product of the BF16X2 mode runs the pipelined kernel on
+    // bf16 planes, except on scalar operators (their panel rows are 16-byte, not
+    // 8-element, aligned) and with the staged variant selected
+    p.pipe = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.split && !p.csr_kernel &&
+             !(A->schedule & VBCSR_SCHED_MMA_STAGED) && A->backend != VBCSR_BACKEND_CSR;
+    p.presplit = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.csr_kernel && !p.pipe &&
                  (p.split || !(A->schedule & VBCSR_SCHED_MMA_STAGED));
-    p.need_panel32 = p.f64 && p.mode != VBCSR_PREC_NATIVE && p.mode != VBCSR_PREC_DF32 && !p.presplit;
+    p.need_panel32 =
+        p.f64 && p.mode != VBCSR_PREC_NATIVE && p.mode != VBCSR_PREC_DF32 && !p.presplit && !p.pipe;
     p.need_panelbf = p.presplit;
+    p.need_panelbp = p.pipe;
     p.need_paneldf = p.mode == VBCSR_PREC_DF32;
     p.xkind = !p.f64 || p.mode == VBCSR_PREC_NATIVE ? kXAsGiven
             : p.mode == VBCSR_PREC_DF32             ? kXPairs
+            : p.pipe                                ? kXPlanes
             : p.presplit                            ? kXSplit
                                                     : kXF32;
     return p;
@@ -951,11 +990,13 @@ static bool mode_buffers_ready(const vbcsr_t *A, const ModePlan &p, int64_t xrow
     if (p.need_panel32 && !A->panel32_valid) return false;
     if (p.need_panelbf && !A->panelbf_valid) return false;
     if (p.need_paneldf && !A->paneldf_valid) return false;
+    if (p.need_panelbp && !A->panelbp_valid) return false;
     const size_t need = (size_t)xrows * (size_t)k;
     switch (p.xkind) {
         case kXF32: return A->xconv_elems >= need;
         case kXSplit: return A->xbf_elems >= need;
         case kXPairs: return A->xdf_elems >= need;
+        case kXPlanes: return A->xbp_elems >= 2 * (size_t)xrows * (size_t)pipe_ldp(k);
         default: return true;
     }
 }
@@ -972,7 +1013,7 @@ struct FusedX {
 // True when a forward product of this plan runs the plain tensor-core kernel
 // on a converted X (FP32, or packed bf16 pieces), i.e. when FusedX applies.
 static bool fused_x_applies(const vbcsr_t *A, const ModePlan &p) {
-    return !p.fma && !p.split && !p.cplx && (p.xkind == kXF32 || p.xkind == kXSplit) &&
+    return !p.fma && !p.split && !p.cplx && (p.xkind == kXF32 || p.xkind == kXSplit || p.xkind == kXPlanes) &&
            !(A->schedule & VBCSR_SCHED_MMA_STAGED);
 }
 
@@ -1023,6 +1064,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         int rc = refresh_paneldf(A, s);
         if (rc) return rc;
     }
+    if (mp.need_panelbp && !A->panelbp_valid) {
+        int rc = refresh_panelbp(A, s);
+        if (rc) return rc;
+    }
+    const int64_t ldp = mp.pipe ? pipe_ldp(k) : 0;   // X row stride of the bf16 planes
 
     // The mixed modes read X as FP32 (the double-FP32 mode as hi/lo pairs):
     // convert an FP64 X once here rather than at every gather inside the
@@ -1030,10 +1076,18 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const bool fused = fx && !trans && fused_x_applies(A, mp);
     if (fused && fx->x_in && alpha != 0.0 && xrows > 0) {
         X = fx->x_in;
-        ldx = k;
+        ldx = mp.pipe ? ldp : k;
     } else if (mp.xkind != kXAsGiven && alpha != 0.0 && xrows > 0) {
         const size_t need = (size_t)xrows * (size_t)k;
-        if (mp.xkind == kXPairs) {
+        if (mp.xkind == kXPlanes) {
+            int rc = grow(A, &A->xbp, &A->xbp_elems, 2 * (size_t)xrows * (size_t)ldp, s, "alloc bf16 planes of X");
+            if (rc) return rc;
+            CUDA_TRY(launch_split_bf16_planes_panel(xrows, k, (const double *)X, ldx, A->xbp,
+                                                    A->xbp + (size_t)xrows * ldp, ldp, s),
+                     "split X");
+            X = A->xbp;
+            ldx = ldp;
+        } else if (mp.xkind == kXPairs) {
             int rc = grow(A, &A->xdf, &A->xdf_elems, need, s, "alloc double-FP32 copy of X");
             if (rc) return rc;
             CUDA_TRY(launch_split_df(xrows, k, (const double *)X, ldx, A->xdf, s), "split X");
@@ -1049,12 +1103,13 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             CUDA_TRY(launch_convert_panel_f64_to_f32(xrows, k, (const double *)X, ldx, A->xconv, s), "convert X");
             X = A->xconv;
         }
-        ldx = k;
+        if (mp.xkind != kXPlanes) ldx = k;
     }
 
     ProdArgs a;
     memset(&a, 0, sizeof(a));
     a.values = mode == VBCSR_PREC_DF32 ? (const void *)A->paneldf
+             : mp.pipe ? (const void *)A->panelbp
              : presplit ? (const void *)A->panelbf
              : (f64 && mode != VBCSR_PREC_NATIVE) ? (const void *)A->panel32 : A->panel;
     a.fl = {A->fl_xrow, A->fl_pcol, A->fl_w};
@@ -1075,6 +1130,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.err = A->err;
     a.debug_checks = A->debug_checks;
     a.xs_out = fused && fx->x_out ? fx->x_out : nullptr;
+    if (mp.pipe) {
+        a.v_plane = A->panel_elems;
+        a.x_plane = xrows * ldp;
+        a.xs_plane = yrows * ldp;
+    }
     const int kc_auto = auto_kc(k);
     // FP32 values and double-FP32 pairs in the CUDA-core forward kernels with
     // column tiles of 8 or more go through the shared-memory ring unless the
@@ -1127,6 +1187,8 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             e = launch_fma_df(B, trans, a, s, df_narrow);
         else if (split)
             e = launch_fma_split(mma_mode, a, s);
+        else if (mp.pipe)
+            e = launch_mma_pipe(a, s);
         else
             e = launch_mma(mma_mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
@@ -1152,9 +1214,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             per_item_dot = true;
             CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         }
-        const void *kern = mma_kernel_ptr(mma_mode, f64, trans, staged, k);
+        const void *kern = mp.pipe ? mma_pipe_kernel_ptr(k) : mma_kernel_ptr(mma_mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
-        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern, mma_smem_bytes(trans, staged, 4));
+        rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern,
+                    mp.pipe ? mma_pipe_smem_bytes(k, 4) : mma_smem_bytes(trans, staged, 4));
     } else if (csr_kernel) {
         // scalar operator: several rows per warp; items are the scalar rows in page order
         const int kind = split ? (mode == VBCSR_PREC_TF32 ? kCsrSplitTF32
@@ -1280,7 +1343,13 @@ static int cheb_fused_buffers(vbcsr_t *A, int64_t k, int precision, void *xs[2],
     const ModePlan mp = plan_mode(A, false, k, precision);
     if (!fused_x_applies(A, mp) || A->n_rows == 0) return VBCSR_OK;
     const size_t panel = (size_t)A->n_rows * (size_t)k;
-    if (mp.xkind == kXSplit) {
+    if (mp.xkind == kXPlanes) {
+        const size_t planes = 2 * (size_t)A->n_rows * (size_t)pipe_ldp(k);
+        int rc = grow(A, &A->xbp, &A->xbp_elems, 2 * planes, s, "alloc bf16 planes of the Chebyshev vectors");
+        if (rc) return rc;
+        xs[0] = A->xbp;
+        xs[1] = A->xbp + planes;
+    } else if (mp.xkind == kXSplit) {
         int rc = grow(A, &A->xbf, &A->xbf_elems, 2 * panel, s, "alloc split copies of the Chebyshev vectors");
         if (rc) return rc;
         xs[0] = A->xbf;
@@ -1536,6 +1605,10 @@ extern "C" int vbcsr_shift_scale(vbcsr_t *A, double c, double d, void *stream) {
     }
     if (A->panelbf) {
         int rc = refresh_panelbf(A, s);
+        if (rc) return rc;
+    }
+    if (A->panelbp) {
+        int rc = refresh_panelbp(A, s);
         if (rc) return rc;
     }
     if (A->paneldf) return refresh_paneldf(A, s);
@@ -2008,8 +2081,12 @@ extern "C" int vbcsr_chebyshev_noalloc(vbcsr_t *A, int64_t k, const double *R, i
         // the mode's value copy and converted-X buffers must exist already
         const ModePlan mp = plan_mode(A, false, k, precision);
         bool ready = mode_buffers_ready(A, mp, A->n_cols, k);
-        if (ready && n_moments > 1 && fused_x_applies(A, mp))
-            ready = (mp.xkind == kXSplit ? A->xbf_elems : A->xconv_elems) >= 2 * (size_t)A->n_rows * (size_t)k;
+        if (ready && n_moments > 1 && fused_x_applies(A, mp)) {
+            const size_t panel = (size_t)A->n_rows * (size_t)k;
+            ready = mp.xkind == kXPlanes ? A->xbp_elems >= 4 * (size_t)A->n_rows * (size_t)pipe_ldp(k)
+                  : mp.xkind == kXSplit  ? A->xbf_elems >= 2 * panel
+                                         : A->xconv_elems >= 2 * panel;
+        }
         if (!ready)
             return fail(VBCSR_ERR_UNSUPPORTED,
                         "precision %d needs buffers this handle has not built yet: make one vbcsr_chebyshev "

@@ -93,11 +93,15 @@ struct ProdArgs {
     uint64_t kc_log2_by_b;  // 3 bits per row count B = 1..16: log2 of its column tile
     int mma_staged;         // tensor-core forward: 1 = value panels staged in shared memory
     int value_ring;         // CUDA-core forward, FP32 values, k >= 4: read them through the ring
-    void *xs_out;           // tensor-core forward (plain kernel) only, or NULL: every output
-                            // element is also written here, [rows of Y, k] with leading
-                            // dimension k, in the form the kernel reads X (FP32, or the packed
-                            // bf16 pieces of BF16X2), so that the next Chebyshev step needs no
-                            // conversion pass
+    void *xs_out;           // tensor-core forward (plain kernels) only, or NULL: every output
+                            // element is also written here, in the form the kernel reads X
+                            // (FP32 or the packed bf16 pieces of BF16X2, [rows of Y, k] with
+                            // leading dimension k; the bf16 hi / lo planes of the pipelined
+                            // BF16X2 kernel, leading dimension ldx, planes xs_plane apart), so
+                            // that the next Chebyshev step needs no conversion pass
+    int64_t xs_plane;       // pipelined BF16X2 kernel: elements between the hi and lo planes of xs_out
+    int64_t v_plane;        //   ... of the value planes
+    int64_t x_plane;        //   ... of the X planes (X row stride: ldx)
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
@@ -115,6 +119,12 @@ cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s, 
 cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t ld, float2 *out, cudaStream_t s);
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
+// BF16X2 forward of an FP64 operator pipelined through shared memory (spmm_mma_pipe.cu):
+// values and X as bf16 hi / lo planes (X rows pipe_ldp(k) elements apart)
+cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s);
+const void *mma_pipe_kernel_ptr(int64_t k);
+size_t mma_pipe_smem_bytes(int64_t k, int warps);
+int64_t pipe_ldp(int64_t k);
 
 // Scalar (all 1 x 1 blocks) operators: L lanes per row (2, 4 or 8 for the
 // FP64 and double-FP32 kinds, 4, 8, 16 or 32 for the FP32 ones; csr_lane_class
@@ -235,6 +245,11 @@ cudaError_t launch_permute_values(int esize, bool to_panel, int64_t nblk, const 
 cudaError_t launch_convert_f64_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
 // FP64 -> FP32 v -> one 32-bit word: bf16_rn(v) in the low half, bf16_rn(v - that) in the high half
 cudaError_t launch_split_bf16(const double *in, uint32_t *out, int64_t n, cudaStream_t s);
+// the same pieces as two planes: hi[i], lo[i] (values), and hi / lo[r * ldp + c] of an
+// [rows, k] panel with leading dimension ld (X)
+cudaError_t launch_split_bf16_planes(const double *in, uint16_t *hi, uint16_t *lo, int64_t n, cudaStream_t s);
+cudaError_t launch_split_bf16_planes_panel(int64_t rows, int64_t k, const double *in, int64_t ld, uint16_t *hi,
+                                           uint16_t *lo, int64_t ldp, cudaStream_t s);
 cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, int64_t ld, uint32_t *out,
                                     cudaStream_t s);
 // out[rows, k] (leading dimension k) = FP32 of the FP64 panel in (leading dimension ld)

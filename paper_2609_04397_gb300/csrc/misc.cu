@@ -303,6 +303,40 @@ cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, i
     return cudaGetLastError();
 }
 
+__global__ void split_planes_kernel(const double *in, uint16_t *hi, uint16_t *lo, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = bf16_pieces(in[i]);
+        hi[i] = (uint16_t)(w & 0xffffu);
+        lo[i] = (uint16_t)(w >> 16);
+    }
+}
+
+__global__ void split_planes_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, uint16_t *hi,
+                                          uint16_t *lo, int64_t ldp) {
+    const int64_t n = rows * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / k, c = e - r * k;
+        const uint32_t w = bf16_pieces(in[r * ld + c]);
+        hi[r * ldp + c] = (uint16_t)(w & 0xffffu);
+        lo[r * ldp + c] = (uint16_t)(w >> 16);
+    }
+}
+
+cudaError_t launch_split_bf16_planes(const double *in, uint16_t *hi, uint16_t *lo, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int64_t need = (n + 255) / 256;
+    split_planes_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(in, hi, lo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16_planes_panel(int64_t rows, int64_t k, const double *in, int64_t ld, uint16_t *hi,
+                                           uint16_t *lo, int64_t ldp, cudaStream_t s) {
+    if (rows * k == 0) return cudaSuccess;
+    const int64_t need = (rows * k + 255) / 256;
+    split_planes_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, in, ld, hi, lo, ldp);
+    return cudaGetLastError();
+}
+
 __global__ void convert_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, float *out) {
     const int64_t n = rows * k;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {

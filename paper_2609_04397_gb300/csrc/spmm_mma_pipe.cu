@@ -1,0 +1,334 @@
+// BF16X2 forward product of an FP64 operator on the tensor cores, pipelined
+// through shared memory (the default forward kernel of the BF16X2 mode for
+// k >= 3).
+//
+// Operands are split once into bf16 pieces v = hi + lo (hi = bf16_rn(v),
+// lo = bf16_rn(v - hi), v rounded to FP32 first) and kept as two planes of
+// the same shape: the values as planes of the value pages (panel layout), X
+// as planes [rows, ldp] with ldp a multiple of the pass width. Products
+// hi*hi + hi*lo + lo*hi accumulate in FP32 (m16n8k16, FP32 accumulators);
+// the epilogue (alpha, beta, gamma * Z, the dot with R) is FP64.
+//
+// One warp owns one work item (up to 16 output rows of a block row) and
+// walks its virtual columns in steps of 16. Each step's operands, 16 rows x
+// 16 columns of both value planes and the 16 gathered X rows x 8 NT columns
+// of both X planes, are copied into a ring of S shared-memory stages by
+// asynchronous 16-byte copies, S - 1 steps ahead of the tensor cores. The
+// copies of columns beyond the panel row or beyond the item's last virtual
+// column are zero-filled, so the tail steps add nothing; value rows >= B are
+// not copied (whatever the stage holds there reaches only output rows that
+// are not written). Fragments come from the stages with ldmatrix (the
+// transposing form for the X tile, whose 16 rows are virtual columns); the
+// 16-byte chunks of a stage row are XOR-swizzled by the row so that the eight
+// rows of each ldmatrix matrix fall on distinct banks.
+//
+// The loads in flight per warp are the ring's, not registers, and the bf16
+// planes feed the MMA fragments directly (no byte permutes).
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "split.cuh"
+
+namespace vbcsr {
+
+namespace {
+
+constexpr int kPipeStages = 4;   // ring depth (stages of 16 virtual columns)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// 16 bytes global -> shared, asynchronously; zero-filled when !valid (src is then not read)
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2_t(uint32_t addr, uint32_t (&r)[2]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Stage layout (bytes), per warp and stage: value plane hi, value plane lo
+// (16 rows x 32 B each), X plane hi, X plane lo (16 rows x 16 NT B each).
+template <int NT>
+struct PipeStage {
+    static constexpr int kVPlane = 16 * 32;
+    static constexpr int kXRow = 16 * NT;
+    static constexpr int kXPlane = 16 * kXRow;
+    static constexpr int kBytes = 2 * kVPlane + 2 * kXPlane;
+};
+
+// byte offset of 16-byte chunk c of row r in a value plane (two chunks per row)
+__device__ __forceinline__ int v_off(int r, int c) { return r * 32 + 16 * (c ^ ((r >> 2) & 1)); }
+
+// byte offset of chunk c of row r in an X plane (NT chunks per row)
+template <int NT>
+__device__ __forceinline__ int x_off(int r, int c) {
+    const int sw = NT == 4 ? ((r >> 1) & 3) : NT == 2 ? ((r >> 2) & 1) : 0;
+    return r * (16 * NT) + 16 * (c ^ sw);
+}
+
+// packed bf16 hi / lo pieces of two FP64 values (lower column in the low half)
+__device__ __forceinline__ void pieces2(double v0, double v1, uint32_t &hi, uint32_t &lo) {
+    const uint32_t w0 = bf16_pieces(v0), w1 = bf16_pieces(v1);
+    hi = (w0 & 0xffffu) | (w1 << 16);
+    lo = (w0 >> 16) | (w1 & 0xffff0000u);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
+    constexpr int S = kPipeStages;
+    using St = PipeStage<NT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warps = a.warps;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    unsigned char *ring = smem_raw + (size_t)warp * S * St::kBytes;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw + (size_t)warps * S * St::kBytes) + warp * kKMax;
+    const uint32_t ring_s = smem_addr(ring);
+
+    const __nv_bfloat16 *__restrict__ vhi = static_cast<const __nv_bfloat16 *>(a.values);
+    const __nv_bfloat16 *__restrict__ vlo = vhi + a.v_plane;
+    const __nv_bfloat16 *__restrict__ xhi = static_cast<const __nv_bfloat16 *>(a.X);
+    const __nv_bfloat16 *__restrict__ xlo = xhi + a.x_plane;
+    double *__restrict__ Y = static_cast<double *>(a.Y);
+    const double *__restrict__ Z = static_cast<const double *>(a.Z);
+    const double *__restrict__ R = static_cast<const double *>(a.R);
+    uint32_t *__restrict__ XS = static_cast<uint32_t *>(a.xs_out);   // hi plane; lo plane at + a.xs_plane / 2
+    const int64_t ldp = a.ldx;
+    const bool do_prod = a.alpha != 0.0;
+    const bool want_dot = a.partials || a.item_partials;
+    double dot = 0.0;
+
+    // this lane's value copies: chunk (row vr, half vh) of both planes
+    const int vr = (lane >> 1) & 15, vh = lane & 1;
+
+    int64_t it = (int64_t)blockIdx.x * warps + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long q = 0;
+            if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+        }
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+        for (int64_t n0 = 0; n0 < a.k; n0 += 8 * NT) {
+            float acc[NT][4];
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[n][j] = 0.f;
+
+            if (do_prod) {
+                for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+                    const int tn = min(kKMax, w.K - t0);
+                    const int nsteps = (tn + 15) >> 4;
+                    if (n0 == 0 || w.K > kKMax) {
+                        __syncwarp();
+                        for (int e = lane; e < w.nlist; e += 32) {
+                            const int64_t l = w.lbegin + e;
+                            const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
+                            const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
+                            for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
+                        }
+                        __syncwarp();
+                    }
+                    // copies of step s into ring slot s % S (an empty group past the last step)
+                    auto issue = [&](int s) {
+                        if (s < nsteps) {
+                            const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
+                            if (vr < w.B) {
+                                const int64_t col = (int64_t)t0 + 16 * s + 8 * vh;
+                                const bool ok = col < w.Kp;   // Kp is a multiple of 8: a chunk is in or out
+                                const int64_t e = ok ? w.vbase + (int64_t)vr * w.Kp + col : 0;
+                                cp16(st + v_off(vr, vh), vhi + e, ok);
+                                cp16(st + St::kVPlane + v_off(vr, vh), vlo + e, ok);
+                            }
+                            // the X tile: 16 rows x NT chunks per plane; lane handles (row, chunk)
+                            // pairs lane, lane + 32, ... below 16 NT, in both planes
+                            for (int idx = lane; idx < 16 * NT; idx += 32) {
+                                const int v = idx / NT, c = idx % NT;
+                                const int t = 16 * s + v;
+                                const bool ok = t < tn;
+                                const int64_t e = ok ? (int64_t)s_x[t] * ldp + n0 + 8 * c : 0;
+                                cp16(st + 2 * St::kVPlane + x_off<NT>(v, c), xhi + e, ok);
+                                cp16(st + 2 * St::kVPlane + St::kXPlane + x_off<NT>(v, c), xlo + e, ok);
+                            }
+                        }
+                        cp_commit();
+                    };
+#pragma unroll
+                    for (int s = 0; s < S - 1; ++s) issue(s);
+                    for (int s = 0; s < nsteps; ++s) {
+                        cp_wait<S - 2>();
+                        __syncwarp();
+                        issue(s + S - 1);
+                        const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
+                        // A fragments: matrices (rows 0-7 | 8-15) x (columns 0-7 | 8-15)
+                        const int am = lane >> 3, ar = (lane & 7) + 8 * (am & 1), ac = am >> 1;
+                        uint32_t ahi[4], alo[4];
+                        ldsm_x4(st + v_off(ar, ac), ahi);
+                        ldsm_x4(st + St::kVPlane + v_off(ar, ac), alo);
+                        // B fragments: the X tile's rows are the step's virtual columns
+                        const uint32_t xs0 = st + 2 * St::kVPlane;
+                        if constexpr (NT == 1) {
+                            const int br = lane & 15;
+                            uint32_t bh[2], bl[2];
+                            ldsm_x2_t(xs0 + x_off<NT>(br, 0), bh);
+                            ldsm_x2_t(xs0 + St::kXPlane + x_off<NT>(br, 0), bl);
+                            mma16816(acc[0], ahi, bh[0], bh[1]);
+                            mma16816(acc[0], ahi, bl[0], bl[1]);
+                            mma16816(acc[0], alo, bh[0], bh[1]);
+                        } else {
+#pragma unroll
+                            for (int n = 0; n < NT; n += 2) {
+                                const int bm = lane >> 3, br = (lane & 7) + 8 * (bm & 1), bc = n + (bm >> 1);
+                                uint32_t bh[4], bl[4];
+                                ldsm_x4_t(xs0 + x_off<NT>(br, bc), bh);
+                                ldsm_x4_t(xs0 + St::kXPlane + x_off<NT>(br, bc), bl);
+                                mma16816(acc[n], ahi, bh[0], bh[1]);
+                                mma16816(acc[n], ahi, bl[0], bl[1]);
+                                mma16816(acc[n], alo, bh[0], bh[1]);
+                                mma16816(acc[n + 1], ahi, bh[2], bh[3]);
+                                mma16816(acc[n + 1], ahi, bl[2], bl[3]);
+                                mma16816(acc[n + 1], alo, bh[2], bh[3]);
+                            }
+                        }
+                    }
+                    cp_wait_all();
+                    __syncwarp();
+                }
+            }
+            // epilogue: acc[n] = {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)} of tile n
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = g + 8 * h;
+                    const int64_t col = n0 + n * 8 + 2 * t4;
+                    if (r >= w.B || col >= a.k) continue;
+                    const int64_t row = w.yrow + r;
+                    const bool pair = col + 1 < a.k;
+                    double v[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (e == 1 && !pair) break;
+                        double *yp = Y + row * a.ldy + col + e;
+                        double o = a.alpha * (double)acc[n][2 * h + e];
+                        if (a.beta != 0.0) o += a.beta * *yp;
+                        if (a.gamma != 0.0) o += a.gamma * Z[row * a.ldz + col + e];
+                        *yp = o;
+                        if (want_dot) dot += R[row * a.ldr + col + e] * o;
+                        v[e] = o;
+                    }
+                    if (XS) {
+                        uint32_t hi, lo;
+                        pieces2(v[0], pair ? v[1] : 0.0, hi, lo);
+                        // col is even and the plane stride ldp even: a 4-byte aligned pair
+                        const int64_t off = (row * ldp + col) >> 1;
+                        XS[off] = hi;
+                        XS[off + (a.xs_plane >> 1)] = lo;
+                    }
+                }
+            }
+        }
+        if (a.item_partials) {
+            // the item's share of the fused dot at the item's index (summed in a fixed
+            // order afterwards, whichever warp took the item)
+            for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+            if (lane == 0) a.item_partials[it] = dot;
+            dot = 0.0;
+        }
+        if (!a.queue) it += (int64_t)gridDim.x * warps;
+    }
+
+    if (a.partials) {
+        for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+        __shared__ double s_dot[32];
+        __syncthreads();
+        if (lane == 0) s_dot[warp] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int i = 0; i < warps; ++i) sum += s_dot[i];
+            a.partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+template <int NT>
+size_t pipe_smem(int warps) {
+    return (size_t)warps * ((size_t)kPipeStages * PipeStage<NT>::kBytes + kKMax * sizeof(int32_t));
+}
+
+template <int NT>
+cudaError_t pipe_launch(const ProdArgs &a, cudaStream_t s) {
+    const size_t smem = pipe_smem<NT>(a.warps);
+    cudaError_t e = cudaFuncSetAttribute((const void *)mma_bf16_pipe_kernel<NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mma_bf16_pipe_kernel<NT><<<a.grid, a.warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int pipe_nt(int64_t k) { return k <= 8 ? 1 : (k <= 16 ? 2 : 4); }
+
+int64_t pipe_ldp(int64_t k) {
+    const int64_t w = 8 * pipe_nt(k);
+    return (k + w - 1) / w * w;
+}
+
+size_t mma_pipe_smem_bytes(int64_t k, int warps) {
+    const int nt = pipe_nt(k);
+    return nt == 1 ? pipe_smem<1>(warps) : nt == 2 ? pipe_smem<2>(warps) : pipe_smem<4>(warps);
+}
+
+const void *mma_pipe_kernel_ptr(int64_t k) {
+    const int nt = pipe_nt(k);
+    return nt == 1 ? (const void *)mma_bf16_pipe_kernel<1>
+                   : nt == 2 ? (const void *)mma_bf16_pipe_kernel<2> : (const void *)mma_bf16_pipe_kernel<4>;
+}
+
+cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s) {
+    const int nt = pipe_nt(a.k);
+    if (nt == 1) return pipe_launch<1>(a, s);
+    if (nt == 2) return pipe_launch<2>(a, s);
+    return pipe_launch<4>(a, s);
+}
+
+}  // namespace vbcsr

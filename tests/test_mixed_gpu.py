@@ -132,7 +132,10 @@ def test_mixed_copy_follows_set_values():
 def test_staged_forward_kernel_matches_plain(mode, k):
     """The shared-memory-staged tensor-core forward kernel computes the same
     products as the plain one (same fragments, same summation order), incl.
-    wide panels that span several stages and rows of every height."""
+    wide panels that span several stages and rows of every height. The plain
+    BF16X2 kernel of an FP64 operator (bf16 planes through a shared-memory
+    ring, k >= 3) feeds each MMA the same 16 virtual columns in another slot
+    order, so there the two agree to FP32 rounding of the accumulation."""
     pat = syn.random_pattern(45, 45, (1, 4, 9, 13, 16, 20, 70), 0.2, 40 + k, empty_rows=3, unsorted=True)
     vals = syn.random_values(pat, 40 + k)
     H = _handle(pat, vals)
@@ -143,7 +146,11 @@ def test_staged_forward_kernel_matches_plain(mode, k):
     H.set_schedule("bucketed", mma_staged=True)
     Ys = Y0.clone()
     H.spmm(X, 2.0, -1.0, Ys, precision=mode)
-    assert torch.equal(Yp, Ys)
+    if mode == "bf16x2" and k >= 3:
+        _, scale = forward_ref(pat, np.abs(vals), np.abs(X.cpu().numpy()), 2.0, 1.0, np.abs(Y0.cpu().numpy()))
+        check_elementwise(Yp.cpu().numpy(), Ys.cpu().numpy().astype(np.float64), scale, 1e-6)
+    else:
+        assert torch.equal(Yp, Ys)
     if mode != "tf32":
         ref, scale = forward_ref(pat, vals, X.cpu().numpy(), 2.0, -1.0, Y0.cpu().numpy())
         assert rel_fro(Ys.cpu().numpy(), ref) <= TOL_MIXED

@@ -82,7 +82,7 @@ def test_noalloc_refuses_a_mode_whose_buffers_are_not_built(prec):
     from paper_2609_04397_gb300 import lib
     L = lib()
     w, H = _scaled_tiny()
-    R = torch.from_numpy(syn.rademacher_panel(w.pattern.n_rows, 8, 0)).cuda()
+    R = torch.from_numpy(syn.rademacher_panel(w.pattern.n_rows, 16, 0)).cuda()
     mom = torch.zeros(6, dtype=torch.float64, device="cuda:0")
     free_before = torch.cuda.mem_get_info()[0]
     assert _moments_noalloc(L, H, R, 6, mom, PREC[prec]) == -5
@@ -90,9 +90,12 @@ def test_noalloc_refuses_a_mode_whose_buffers_are_not_built(prec):
     torch.cuda.synchronize()
     assert torch.count_nonzero(mom).item() == 0       # nothing was launched
     assert torch.cuda.mem_get_info()[0] == free_before
-    # buffers built for fewer columns are not enough for more
-    _moments_existing(L, H, R[:, :4].contiguous(), 6, PREC[prec])
+    # buffers built for 8 columns are not enough for 16
+    _moments_existing(L, H, R[:, :8].contiguous(), 6, PREC[prec])
     assert _moments_noalloc(L, H, R, 6, mom, PREC[prec]) == -5
+    # once an ordinary call has built them for 16 columns, the call runs
+    _moments_existing(L, H, R, 6, PREC[prec])
+    assert _moments_noalloc(L, H, R, 6, mom, PREC[prec]) == 0
 
 
 def test_noalloc_rejects_requests_beyond_its_work_area():
