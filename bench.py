@@ -62,13 +62,13 @@ FP64_PEAK_TFLOPS = FP64_SMS * FP64_FMA_PER_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PROBE_TFLOPS = 1.19
 
 
-# DRAM bytes (read + write) of one FP64 Chebyshev step (k = 16) of the
-# ~1e6-atom operator: ncu's dram__bytes_read.sum + dram__bytes_write.sum of the
-# FP64 forward product on the ~200k-atom nanoparticle, scaled by the stored
-# entries to the full operator (traffic grows with the entries: values, X and
-# Y all scale with the atom count); the summary is under profiles/. None until
-# that capture matches the current kernel.
-TRAFFIC_F64_STEP = None
+# DRAM bytes (read + write) per stored entry of one FP64 Chebyshev step
+# (k = 16): ncu's dram__bytes_read.sum + dram__bytes_write.sum of the FP64
+# forward product with the recurrence epilogue on the ~100k-atom nanoparticle
+# (3.770 GB per launch, mean of two launches, 336,743,405 entries), scaled by
+# the stored entries to the headline operator (values, X, Y and R all grow
+# with the atom count). The summary is under profiles/.
+TRAFFIC_F64_PER_ENTRY = 11.194
 
 
 def _workload(n_atoms=N_ATOMS):
@@ -675,7 +675,8 @@ def run_ours(args):
     by_step = _step_bytes(pat, k, "native")
     roofline = {"bound": "alu", "achieved": flops_step / step_ms / 1e9, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": flops_step / step_ms / 1e9 / FP64_PEAK_TFLOPS,
-                "traffic": int(TRAFFIC_F64_STEP * pat.nnz) if TRAFFIC_F64_STEP else None,
+                "traffic": int(TRAFFIC_F64_PER_ENTRY * pat.nnz),
+                "traffic_source": "ncu DRAM bytes per stored entry on the ~100k-atom operator, scaled by the entries",
                 "algorithmic_bytes": by_step,
                 "kernel": "fma_persistent_kernel<false, double, double, double, double> (FP64 forward product "
                           f"with the recurrence epilogue), k = {k}",

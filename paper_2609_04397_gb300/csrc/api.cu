@@ -142,6 +142,7 @@ struct vbcsr_matrix {
     int32_t *d_row_b = nullptr;
     double *partials = nullptr;
     double *item_partials = nullptr;   // one dot share per work item (persistent launches)
+    double *dot_scratch = nullptr;     // first-stage sums of long fixed-order reductions
     int *err = nullptr;
     int64_t device_bytes = 0;
 
@@ -554,6 +555,7 @@ static int build(vbcsr_matrix *A, int64_t n_brows, int64_t n_bcols, const int32_
     CUDA_TRY(upload(A, &A->d_row_off, A->row_off, s), "upload");
     CUDA_TRY(upload(A, &A->d_row_b, A->row_b, s), "upload");
     CUDA_TRY(A->alloc(&A->partials, kPartialsCap), "alloc partials");
+    CUDA_TRY(A->alloc(&A->dot_scratch, (size_t)kDotScratch), "alloc partials");
     CUDA_TRY(A->alloc(&A->err, 1), "alloc error word");
     CUDA_TRY(A->alloc(&A->queue, 1), "alloc work counter");
     CUDA_TRY(cudaMemsetAsync(A->err, 0, sizeof(int), s), "memset");
@@ -1269,7 +1271,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     if (rc) return rc;
     if (want_dot)
         CUDA_TRY(launch_finalize_dot(per_item_dot ? A->item_partials : A->partials, per_item_dot ? n_all : used,
-                                     dot_scale, epi->dot_out, s),
+                                     dot_scale, epi->dot_out, A->dot_scratch, s),
                  "dot finalize");
     return VBCSR_OK;
 }
@@ -1392,7 +1394,7 @@ extern "C" int vbcsr_chebyshev(vbcsr_t *A, int64_t k, const double *R, int64_t l
     int64_t used = 0;
     CUDA_TRY(launch_dot_panels(true, N, k * cw, R, ldr * cw, R, ldr * cw, A->partials, kPartialsCap, &used, s),
              "dot");
-    CUDA_TRY(launch_finalize_dot(A->partials, used, scale, moments, s), "dot");
+    CUDA_TRY(launch_finalize_dot(A->partials, used, scale, moments, A->dot_scratch, s), "dot");
     if (n_moments == 1) return VBCSR_OK;
 
     vbcsr_epilogue_t epi;
@@ -1515,7 +1517,7 @@ extern "C" int vbcsr_kpm_moments(vbcsr_t *A, int64_t k, const double *R, int64_t
     auto self_dot = [&](const double *t, int64_t ld, double *out) -> int {
         CUDA_TRY(launch_dot_panels(true, N, k * cw, t, ld * cw, t, ld * cw, A->partials, kPartialsCap, &used, s),
                  "dot");
-        CUDA_TRY(launch_finalize_dot(A->partials, used, scale, out, s), "dot");
+        CUDA_TRY(launch_finalize_dot(A->partials, used, scale, out, A->dot_scratch, s), "dot");
         return VBCSR_OK;
     };
     if (precision < VBCSR_PREC_NATIVE || precision > VBCSR_PREC_DF32)

@@ -255,8 +255,10 @@ cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, i
 // out[rows, k] (leading dimension k) = FP32 of the FP64 panel in (leading dimension ld)
 cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
                                             cudaStream_t s);
-// out[0] = scale * sum(partials[0..n)) in a fixed order
-cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out,
+// out[0] = scale * sum(partials[0..n)) in a fixed order (set by n alone); long sums
+// go through `scratch` (kDotScratch doubles, or NULL for the one-CTA sum)
+constexpr int64_t kDotOneStage = 16384, kDotChunk = 4096, kDotScratch = 1024;
+cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out, double *scratch,
                                 cudaStream_t s);
 // partials[b] = sum over CTA b of A .* B ([rows, k] panels); returns CTAs used in *n_used
 cudaError_t launch_dot_panels(bool f64, int64_t rows, int64_t k, const void *A, int64_t lda,

@@ -369,8 +369,39 @@ __global__ void finalize_dot_kernel(const double *partials, int64_t n, double sc
     if (threadIdx.x == 0) *out = scale * sh[0];
 }
 
-cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out, cudaStream_t s) {
-    finalize_dot_kernel<<<1, 256, 0, s>>>(partials, n, scale, out);
+// first stage of a long sum: CTA b adds the contiguous chunk [b * chunk, (b + 1) * chunk)
+__global__ void chunk_sum_kernel(const double *partials, int64_t n, int64_t chunk, double *out) {
+    __shared__ double sh[256];
+    const int64_t b0 = (int64_t)blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+    double s = 0.0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += partials[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int m = blockDim.x / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) sh[threadIdx.x] += sh[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// Fixed-order sum: up to kDotOneStage partials in one CTA; beyond that, chunks of
+// kDotChunk partials summed by one CTA each into `scratch` (kDotScratch doubles),
+// then those by one CTA. The order depends only on n, so repeated calls give the
+// same bits. (One CTA over a million per-item partials took 0.6 ms: one SM's
+// bandwidth and a long dependent chain of FP64 adds per thread.)
+cudaError_t launch_finalize_dot(const double *partials, int64_t n, double scale, double *out, double *scratch,
+                                cudaStream_t s) {
+    if (n <= kDotOneStage || scratch == nullptr) {
+        finalize_dot_kernel<<<1, 256, 0, s>>>(partials, n, scale, out);
+        return cudaGetLastError();
+    }
+    int64_t chunk = kDotChunk;
+    while ((n + chunk - 1) / chunk > kDotScratch) chunk *= 2;
+    const int64_t nb = (n + chunk - 1) / chunk;
+    chunk_sum_kernel<<<(unsigned)nb, 256, 0, s>>>(partials, n, chunk, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    finalize_dot_kernel<<<1, 256, 0, s>>>(scratch, nb, scale, out);
     return cudaGetLastError();
 }
 

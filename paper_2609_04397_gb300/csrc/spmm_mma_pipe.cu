@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
     const uint32_t ring_s = smem_addr(ring);
 
     const __nv_bfloat16 *__restrict__ vhi = static_cast<const __nv_bfloat16 *>(a.values);
-    const __nv_bfloat16 *__restrict__ vlo = vhi + a.v_plane;
     const __nv_bfloat16 *__restrict__ xhi = static_cast<const __nv_bfloat16 *>(a.X);
-    const __nv_bfloat16 *__restrict__ xlo = xhi + a.x_plane;
     double *__restrict__ Y = static_cast<double *>(a.Y);
     const double *__restrict__ Z = static_cast<const double *>(a.Z);
     const double *__restrict__ R = static_cast<const double *>(a.R);
@@ -135,6 +133,10 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
 
     // this lane's value copies: chunk (row vr, half vh) of both planes
     const int vr = (lane >> 1) & 15, vh = lane & 1;
+    const uint32_t v_dst = (uint32_t)v_off(vr, vh);
+    // X offsets in 32-bit arithmetic when the planes are small enough (64-bit
+    // integer arithmetic is slow on this chip); row indices are staged as int32
+    const bool x32 = (uint64_t)a.x_plane < (1ull << 31);
 
     int64_t it = (int64_t)blockIdx.x * warps + warp;
     for (;;) {
@@ -145,6 +147,8 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
         }
         if (it >= a.n_items) break;
         const WorkItem w = a.items[it];
+        // this lane's value row of the item in the hi plane (the lo plane is v_plane further)
+        const __nv_bfloat16 *vrow = vhi + (w.vbase + (int64_t)min(vr, w.B - 1) * w.Kp);
         for (int64_t n0 = 0; n0 < a.k; n0 += 8 * NT) {
             float acc[NT][4];
 #pragma unroll
@@ -171,11 +175,11 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
                         if (s < nsteps) {
                             const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
                             if (vr < w.B) {
-                                const int64_t col = (int64_t)t0 + 16 * s + 8 * vh;
+                                const int col = t0 + 16 * s + 8 * vh;
                                 const bool ok = col < w.Kp;   // Kp is a multiple of 8: a chunk is in or out
-                                const int64_t e = ok ? w.vbase + (int64_t)vr * w.Kp + col : 0;
-                                cp16(st + v_off(vr, vh), vhi + e, ok);
-                                cp16(st + St::kVPlane + v_off(vr, vh), vlo + e, ok);
+                                const __nv_bfloat16 *src = vrow + (ok ? col : 0);
+                                cp16(st + v_dst, src, ok);
+                                cp16(st + St::kVPlane + v_dst, src + a.v_plane, ok);
                             }
                             // the X tile: 16 rows x NT chunks per plane; lane handles (row, chunk)
                             // pairs lane, lane + 32, ... below 16 NT, in both planes
@@ -183,9 +187,12 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
                                 const int v = idx / NT, c = idx % NT;
                                 const int t = 16 * s + v;
                                 const bool ok = t < tn;
-                                const int64_t e = ok ? (int64_t)s_x[t] * ldp + n0 + 8 * c : 0;
-                                cp16(st + 2 * St::kVPlane + x_off<NT>(v, c), xhi + e, ok);
-                                cp16(st + 2 * St::kVPlane + St::kXPlane + x_off<NT>(v, c), xlo + e, ok);
+                                const int xr = ok ? s_x[t] : 0;
+                                const __nv_bfloat16 *src =
+                                    x32 ? xhi + ((uint32_t)xr * (uint32_t)ldp + (uint32_t)n0 + 8u * c)
+                                        : xhi + ((int64_t)xr * ldp + n0 + 8 * c);
+                                cp16(st + 2 * St::kVPlane + x_off<NT>(v, c), src, ok);
+                                cp16(st + 2 * St::kVPlane + St::kXPlane + x_off<NT>(v, c), src + a.x_plane, ok);
                             }
                         }
                         cp_commit();
@@ -234,33 +241,36 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
             }
             // epilogue: acc[n] = {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)} of tile n
 #pragma unroll
-            for (int n = 0; n < NT; ++n) {
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                if (r >= w.B) continue;
+                const int64_t row = w.yrow + r;
+                double *yrow = Y + row * a.ldy + n0;
+                const double *zrow = Z + row * a.ldz + n0;
+                const double *rrow = R + row * a.ldr + n0;
+                uint32_t *xsrow = XS + ((row * ldp + n0) >> 1);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = g + 8 * h;
-                    const int64_t col = n0 + n * 8 + 2 * t4;
-                    if (r >= w.B || col >= a.k) continue;
-                    const int64_t row = w.yrow + r;
-                    const bool pair = col + 1 < a.k;
+                for (int n = 0; n < NT; ++n) {
+                    const int cl = n * 8 + 2 * t4;   // column relative to n0
+                    if (n0 + cl >= a.k) continue;
+                    const bool pair = n0 + cl + 1 < a.k;
                     double v[2];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         if (e == 1 && !pair) break;
-                        double *yp = Y + row * a.ldy + col + e;
                         double o = a.alpha * (double)acc[n][2 * h + e];
-                        if (a.beta != 0.0) o += a.beta * *yp;
-                        if (a.gamma != 0.0) o += a.gamma * Z[row * a.ldz + col + e];
-                        *yp = o;
-                        if (want_dot) dot += R[row * a.ldr + col + e] * o;
+                        if (a.beta != 0.0) o += a.beta * yrow[cl + e];
+                        if (a.gamma != 0.0) o += a.gamma * zrow[cl + e];
+                        yrow[cl + e] = o;
+                        if (want_dot) dot += rrow[cl + e] * o;
                         v[e] = o;
                     }
                     if (XS) {
                         uint32_t hi, lo;
                         pieces2(v[0], pair ? v[1] : 0.0, hi, lo);
-                        // col is even and the plane stride ldp even: a 4-byte aligned pair
-                        const int64_t off = (row * ldp + col) >> 1;
-                        XS[off] = hi;
-                        XS[off + (a.xs_plane >> 1)] = lo;
+                        // the column is even and the plane stride ldp even: a 4-byte aligned pair
+                        xsrow[cl >> 1] = hi;
+                        xsrow[(cl >> 1) + (a.xs_plane >> 1)] = lo;
                     }
                 }
             }
