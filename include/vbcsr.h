@@ -107,11 +107,19 @@ typedef enum {
                                      kernels instead of the scalar kernel (which
                                      otherwise serves its forward products under
                                      either schedule)                                  */
-    VBCSR_SCHED_NO_RING = 8       /* flag: the persistent CUDA-core forward kernel on
-                                     FP32 values (FP32 operators, the F32 mode) reads
-                                     them directly instead of through its ring of
-                                     asynchronous shared-memory copies, which it
-                                     otherwise uses at k >= 8                          */
+    VBCSR_SCHED_NO_RING = 8,      /* flag: the CUDA-core forward kernel on FP32 values
+                                     (FP32 operators, the F32 mode) reads them directly
+                                     instead of through its ring of asynchronous
+                                     shared-memory copies, which it otherwise uses at
+                                     k >= 8 (one launch per row count, or with
+                                     VBCSR_SCHED_NO_FPIPE)                             */
+    VBCSR_SCHED_NO_FPIPE = 16     /* flag: the persistent launch on FP32 values at
+                                     k >= 8 uses the CUDA-core kernel with per-lane
+                                     output columns instead of the pipelined one (each
+                                     lane a 4-row register tile fed from a ring of
+                                     shared-memory stages of values and gathered X),
+                                     which it otherwise uses when X rows are 16-byte
+                                     aligned                                           */
 } vbcsr_schedule;
 
 /* Flags of vbcsr_autotune. */

@@ -1108,6 +1108,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         if (mp.xkind != kXPlanes) ldx = k;
     }
 
+    // FP32 values (an FP32 operator, or the F32 mode of an FP64 one) at k >= 8 under the
+    // persistent schedule run the pipelined CUDA-core kernel when X rows are 16-byte aligned
+    const bool fpipe = fma && !trans && !cplx && !csr_kernel && A->backend != VBCSR_BACKEND_CSR &&
+                       (mode == VBCSR_PREC_F32 || (!f64 && mode == VBCSR_PREC_NATIVE)) && k >= 8 &&
+                       (A->schedule & VBCSR_SCHED_PERSISTENT) && !(A->schedule & VBCSR_SCHED_NO_FPIPE) &&
+                       ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     ProdArgs a;
     memset(&a, 0, sizeof(a));
     a.values = mode == VBCSR_PREC_DF32 ? (const void *)A->paneldf
@@ -1180,7 +1186,9 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             used += a.grid;
         }
         cudaError_t e;
-        if (mode == VBCSR_PREC_NATIVE)
+        if (fpipe)
+            e = launch_fma32_pipe(f64, a, s);
+        else if (mode == VBCSR_PREC_NATIVE)
             e = cplx ? launch_fma_c128(B, trans, a, s)
                      : (f64 ? launch_fma_f64(B, trans, a, s) : launch_fma_f32(B, trans, a, s));
         else if (mode == VBCSR_PREC_F32)
@@ -1241,6 +1249,12 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             used = a.grid;
         }
         CUDA_TRY(launch_csr(kind, L, a, s), "scalar product launch");
+    } else if (fpipe) {
+        // FP32 values, k >= 8, persistent schedule: the pipelined CUDA-core kernel
+        a.queue = A->queue;
+        per_item_dot = true;
+        CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
+        rc = launch(0, A->fwd_lpt, n_all, 4, fma32_pipe_kernel_ptr(k, f64), fma32_pipe_smem_bytes(k, 4));
     } else if (split || (A->schedule & VBCSR_SCHED_PERSISTENT)) {
         // persistent launch over every row count, items in descending cost from a work queue
         // (the only launch shape of the CUDA-core form of the tensor-core modes)
@@ -1913,7 +1927,8 @@ extern "C" int vbcsr_set_bucket_tuning(vbcsr_t *A, int32_t B, int32_t kc, int32_
 extern "C" int vbcsr_set_schedule(vbcsr_t *A, int32_t schedule, int32_t persist_warps) {
     if (!A) return fail(VBCSR_ERR_INVALID_ARG, "handle is NULL");
     if (schedule < 0 ||
-        schedule > (VBCSR_SCHED_PERSISTENT | VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR | VBCSR_SCHED_NO_RING))
+        schedule > (VBCSR_SCHED_PERSISTENT | VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR | VBCSR_SCHED_NO_RING |
+                    VBCSR_SCHED_NO_FPIPE))
         return fail(VBCSR_ERR_INVALID_ARG, "schedule %d", schedule);
     if (!valid_warps(persist_warps)) return fail(VBCSR_ERR_INVALID_ARG, "warps = %d", persist_warps);
     A->schedule = schedule;
@@ -1988,7 +2003,8 @@ extern "C" int vbcsr_autotune(vbcsr_t *A, int transpose, int64_t k, const void *
     // 1) per row count: the column tile and CTA width of its bucket launch
     const int saved_schedule = A->schedule;
     // the tensor-core variant and the scalar-kernel opt-out are the caller's, not tuned here
-    const int mma_bit = saved_schedule & (VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR | VBCSR_SCHED_NO_RING);
+    const int mma_bit =
+        saved_schedule & (VBCSR_SCHED_MMA_STAGED | VBCSR_SCHED_NO_CSR | VBCSR_SCHED_NO_RING | VBCSR_SCHED_NO_FPIPE);
     A->schedule = VBCSR_SCHED_BUCKETED | mma_bit;
     const std::vector<Bucket> &buckets = trans ? A->adj_buckets : A->fwd_buckets;
     int keep_kc[kMaxB + 1], keep_w[kMaxB + 1];

@@ -125,6 +125,11 @@ cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s);
 const void *mma_pipe_kernel_ptr(int64_t k);
 size_t mma_pipe_smem_bytes(int64_t k, int warps);
 int64_t pipe_ldp(int64_t k);
+// FP32-value forward product on the CUDA cores pipelined through shared memory (k >= 8;
+// X rows 16-byte aligned: ldx a multiple of 4); ydouble: FP64 Y (the F32 mode of an FP64 operator)
+cudaError_t launch_fma32_pipe(bool ydouble, const ProdArgs &a, cudaStream_t s);
+const void *fma32_pipe_kernel_ptr(int64_t k, bool ydouble);
+size_t fma32_pipe_smem_bytes(int64_t k, int warps);
 
 // Scalar (all 1 x 1 blocks) operators: L lanes per row (2, 4 or 8 for the
 // FP64 and double-FP32 kinds, 4, 8, 16 or 32 for the FP32 ones; csr_lane_class

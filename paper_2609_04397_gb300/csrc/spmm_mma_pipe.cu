@@ -314,6 +314,236 @@ cudaError_t pipe_launch(const ProdArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FP32-value forward product on the CUDA cores, pipelined the same way: FP32
+// values (an FP32 operator, or the FP32 copy of an FP64 operator in the F32
+// mode) and the gathered FP32 X tile stream through a ring of shared-memory
+// stages of 16 virtual columns; each lane accumulates a register tile of 4
+// rows x CPL output columns in FP32 from the stage (per 4 virtual columns:
+// four 16-byte loads of values, four of X, 16 CPL multiply-adds). Lanes: rg =
+// lane & 3 picks rows rg, rg + 4, rg + 8, rg + 12, cg the column group; for
+// 8-column passes (NT = 1) the two halves of the lanes (vg) take alternate
+// chunks of 4 virtual columns of each stage and are added at the end of the
+// item. Value rows >= B are not copied (their outputs are not written);
+// columns past the row or past the item's last virtual column are
+// zero-filled. Value stage rows are 64 bytes with chunk c of row r at chunk
+// c ^ (2 ((r >> 1) & 1)), so the rows 4i .. 4i + 3 that one load reads (and
+// the two chunks the lane halves read) fall on distinct banks; X rows of an
+// 8-column pass are padded to 48 bytes for the same reason.
+
+template <int NT>
+struct F32Pipe {
+    static constexpr int CPL = NT == 4 ? 4 : 2;           // output columns per lane
+    static constexpr int PW = 8 * NT;                     // output columns per pass
+    static constexpr int CG = PW / CPL;                   // column groups
+    static constexpr int V = 32 / (4 * CG);               // virtual-column groups (1 or 2)
+    static constexpr int kVBytes = 16 * 64;               // values: 16 rows x 16 columns x 4 B
+    static constexpr int kXRow = NT == 1 ? 48 : PW * 4;   // X row stride (bytes)
+    static constexpr int kXBytes = 16 * kXRow;            // X: 16 rows x PW columns
+    static constexpr int kBytes = kVBytes + kXBytes;
+    static constexpr int S = NT == 4 ? 3 : 4;             // ring depth (32-column passes: 3, for occupancy)
+};
+
+__device__ __forceinline__ int f_off(int r, int c) { return r * 64 + 16 * (c ^ (2 * ((r >> 1) & 1))); }
+
+// One stage of the FP32 pipelined kernel: NI row groups (rows rg + 4 i, i < NI)
+// of this lane's tile, from the stage at st.
+template <int NT, int NI>
+__device__ __forceinline__ void f32_stage(const unsigned char *st, int rg, int cg, int vg,
+                                          float (&acc)[4][F32Pipe<NT>::CPL]) {
+    using P = F32Pipe<NT>;
+#pragma unroll
+    for (int q = 0; q < 4 / P::V; ++q) {   // this lane's chunks of 4 virtual columns
+        const int c = P::V == 2 ? 2 * q + vg : q;
+        float4 vv[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) vv[i] = *reinterpret_cast<const float4 *>(st + f_off(rg + 4 * i, c));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned char *xp = st + P::kVBytes + (4 * c + u) * P::kXRow + 4 * cg * P::CPL;
+            float xv[P::CPL];
+            if constexpr (P::CPL == 4) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(xp);
+                xv[0] = x4.x;
+                xv[1] = x4.y;
+                xv[2] = x4.z;
+                xv[3] = x4.w;
+            } else {
+                const float2 x2 = *reinterpret_cast<const float2 *>(xp);
+                xv[0] = x2.x;
+                xv[1] = x2.y;
+            }
+#pragma unroll
+            for (int i = 0; i < NI; ++i) {
+                const float vi = u == 0 ? vv[i].x : u == 1 ? vv[i].y : u == 2 ? vv[i].z : vv[i].w;
+#pragma unroll
+                for (int j = 0; j < P::CPL; ++j) acc[i][j] = fmaf(vi, xv[j], acc[i][j]);
+            }
+        }
+    }
+}
+
+template <int NT, typename TX>
+__global__ void __launch_bounds__(128, 4) fma32_pipe_kernel(ProdArgs a) {
+    constexpr int S = F32Pipe<NT>::S;
+    using P = F32Pipe<NT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warps = a.warps;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    unsigned char *ring = smem_raw + (size_t)warp * S * P::kBytes;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw + (size_t)warps * S * P::kBytes) + warp * kKMax;
+    const uint32_t ring_s = smem_addr(ring);
+    const float *__restrict__ vals = static_cast<const float *>(a.values);
+    const float *__restrict__ X = static_cast<const float *>(a.X);
+    TX *__restrict__ Y = static_cast<TX *>(a.Y);
+    const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
+    const TX *__restrict__ R = static_cast<const TX *>(a.R);
+    const int64_t ldx = a.ldx;
+    const bool do_prod = a.alpha != 0.0;
+    const bool want_dot = a.partials || a.item_partials;
+    double dot = 0.0;
+    const int rg = lane & 3, cg = (lane >> 2) % P::CG, vg = lane / (4 * P::CG);
+    // this lane's copies: value chunk (row vrow_, chunk vc_) x 2; X chunks below
+    const int vrow_ = lane >> 1, vc0 = 2 * (lane & 1);   // rows 0..15, chunks {0,1} or {2,3}
+
+    int64_t it = (int64_t)blockIdx.x * warps + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long q = 0;
+            if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+        }
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+        const float *vrowp = vals + (w.vbase + (int64_t)min(vrow_, w.B - 1) * w.Kp);
+        for (int64_t n0 = 0; n0 < a.k; n0 += P::PW) {
+            float acc[4][P::CPL];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < P::CPL; ++j) acc[i][j] = 0.f;
+            if (do_prod) {
+                for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+                    const int tn = min(kKMax, w.K - t0);
+                    const int nsteps = (tn + 15) >> 4;
+                    if (n0 == 0 || w.K > kKMax) {
+                        __syncwarp();
+                        for (int e = lane; e < w.nlist; e += 32) {
+                            const int64_t l = w.lbegin + e;
+                            const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
+                            const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
+                            for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
+                        }
+                        __syncwarp();
+                    }
+                    auto issue = [&](int s) {
+                        if (s < nsteps) {
+                            const uint32_t st = ring_s + (uint32_t)((s % S) * P::kBytes);
+                            if (vrow_ < w.B) {
+#pragma unroll
+                                for (int c = vc0; c < vc0 + 2; ++c) {
+                                    const int col = t0 + 16 * s + 4 * c;
+                                    const bool ok = col < w.Kp;   // Kp is a multiple of 4
+                                    cp16(st + f_off(vrow_, c), vrowp + (ok ? col : 0), ok);
+                                }
+                            }
+                            // X tile: 16 rows x (PW / 4) chunks
+                            for (int idx = lane; idx < 16 * (P::PW / 4); idx += 32) {
+                                const int v = idx / (P::PW / 4), c = idx % (P::PW / 4);
+                                const int t = 16 * s + v;
+                                const int64_t col = n0 + 4 * c;
+                                const bool ok = t < tn && col + 4 <= ldx;
+                                const float *src = X + (ok ? (int64_t)s_x[t] * ldx + col : 0);
+                                cp16(st + P::kVBytes + v * P::kXRow + 16 * c, src, ok);
+                            }
+                        }
+                        cp_commit();
+                    };
+#pragma unroll
+                    for (int s = 0; s < S - 1; ++s) issue(s);
+                    const int ni = (w.B + 3) >> 2;   // row groups of the item: rows rg + 4 i, i < ni
+                    for (int s = 0; s < nsteps; ++s) {
+                        cp_wait<S - 2>();
+                        __syncwarp();
+                        issue(s + S - 1);
+                        const unsigned char *st = ring + (s % S) * P::kBytes;
+                        // only the row groups the item has (a 4-row item computes a quarter)
+                        switch (ni) {
+                            case 1: f32_stage<NT, 1>(st, rg, cg, vg, acc); break;
+                            case 2: f32_stage<NT, 2>(st, rg, cg, vg, acc); break;
+                            case 3: f32_stage<NT, 3>(st, rg, cg, vg, acc); break;
+                            default: f32_stage<NT, 4>(st, rg, cg, vg, acc); break;
+                        }
+                    }
+                    cp_wait_all();
+                    __syncwarp();
+                }
+            }
+            if (P::V == 2) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < P::CPL; ++j) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], 16);
+            }
+            // epilogue: rows rg + 4 i, columns n0 + cg CPL + j (the first half of the lanes
+            // when the virtual columns were split)
+            if (vg == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = rg + 4 * i;
+                    if (r >= w.B) continue;
+                    const int64_t row = w.yrow + r;
+#pragma unroll
+                    for (int j = 0; j < P::CPL; ++j) {
+                        const int64_t col = n0 + cg * P::CPL + j;
+                        if (col >= a.k) continue;
+                        TX *yp = Y + row * a.ldy + col;
+                        TX o = (TX)a.alpha * (TX)acc[i][j];
+                        if (a.beta != 0.0) o += (TX)a.beta * *yp;
+                        if (a.gamma != 0.0) o += (TX)a.gamma * Z[row * a.ldz + col];
+                        *yp = o;
+                        if (want_dot) dot += (double)R[row * a.ldr + col] * (double)o;
+                    }
+                }
+            }
+        }
+        if (a.item_partials) {
+            for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+            if (lane == 0) a.item_partials[it] = dot;
+            dot = 0.0;
+        }
+        if (!a.queue) it += (int64_t)gridDim.x * warps;
+    }
+    if (a.partials) {
+        for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+        __shared__ double s_dot[32];
+        __syncthreads();
+        if (lane == 0) s_dot[warp] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int i = 0; i < warps; ++i) sum += s_dot[i];
+            a.partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+template <int NT>
+size_t fpipe_smem(int warps) {
+    return (size_t)warps * ((size_t)F32Pipe<NT>::S * F32Pipe<NT>::kBytes + kKMax * sizeof(int32_t));
+}
+
+template <int NT, typename TX>
+cudaError_t fpipe_launch(const ProdArgs &a, cudaStream_t s) {
+    const size_t smem = fpipe_smem<NT>(a.warps);
+    cudaError_t e = cudaFuncSetAttribute((const void *)fma32_pipe_kernel<NT, TX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fma32_pipe_kernel<NT, TX><<<a.grid, a.warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int pipe_nt(int64_t k) { return k <= 8 ? 1 : (k <= 16 ? 2 : 4); }
@@ -339,6 +569,28 @@ cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s) {
     if (nt == 1) return pipe_launch<1>(a, s);
     if (nt == 2) return pipe_launch<2>(a, s);
     return pipe_launch<4>(a, s);
+}
+
+size_t fma32_pipe_smem_bytes(int64_t k, int warps) {
+    const int nt = pipe_nt(k);
+    return nt == 1 ? fpipe_smem<1>(warps) : nt == 2 ? fpipe_smem<2>(warps) : fpipe_smem<4>(warps);
+}
+
+const void *fma32_pipe_kernel_ptr(int64_t k, bool ydouble) {
+    const int nt = pipe_nt(k);
+    if (ydouble)
+        return nt == 1 ? (const void *)fma32_pipe_kernel<1, double>
+                       : nt == 2 ? (const void *)fma32_pipe_kernel<2, double> : (const void *)fma32_pipe_kernel<4, double>;
+    return nt == 1 ? (const void *)fma32_pipe_kernel<1, float>
+                   : nt == 2 ? (const void *)fma32_pipe_kernel<2, float> : (const void *)fma32_pipe_kernel<4, float>;
+}
+
+cudaError_t launch_fma32_pipe(bool ydouble, const ProdArgs &a, cudaStream_t s) {
+    const int nt = pipe_nt(a.k);
+    if (ydouble) return nt == 1 ? fpipe_launch<1, double>(a, s) : nt == 2 ? fpipe_launch<2, double>(a, s)
+                                                                          : fpipe_launch<4, double>(a, s);
+    return nt == 1 ? fpipe_launch<1, float>(a, s) : nt == 2 ? fpipe_launch<2, float>(a, s)
+                                                            : fpipe_launch<4, float>(a, s);
 }
 
 }  // namespace vbcsr

@@ -192,15 +192,17 @@ class VBCSR:
         check(lib().vbcsr_set_bucket_tuning(self._h, B, kc, warps), "vbcsr_set_bucket_tuning")
 
     def set_schedule(self, schedule: str = "persistent", persist_warps: int = 0, mma_staged: bool = False,
-                     scalar_kernel: bool = True, value_ring: bool = True):
+                     scalar_kernel: bool = True, value_ring: bool = True, pipelined_f32: bool = True):
         """'persistent' (one launch over every item, the default) or 'bucketed'
         (one launch per row count);
         mma_staged selects the shared-memory-staged tensor-core forward kernel;
         scalar_kernel=False makes a CSR-backend operator use the block-row kernels;
         value_ring=False makes the FP32-value CUDA-core forward kernel read its
-        values directly instead of through its shared-memory ring (k >= 8)."""
+        values directly instead of through its shared-memory ring (k >= 8);
+        pipelined_f32=False makes the persistent launch on FP32 values at k >= 8
+        use that kernel instead of the pipelined one."""
         code = ({"bucketed": 0, "persistent": 1}[schedule] | (2 if mma_staged else 0)
-                | (0 if scalar_kernel else 4) | (0 if value_ring else 8))
+                | (0 if scalar_kernel else 4) | (0 if value_ring else 8) | (0 if pipelined_f32 else 16))
         check(lib().vbcsr_set_schedule(self._h, code, persist_warps), "vbcsr_set_schedule")
 
     def get_tuning(self) -> dict:
@@ -213,13 +215,13 @@ class VBCSR:
         return {"kc_by_b": kc.tolist(), "warps_by_b": w.tolist(),
                 "schedule": ["bucketed", "persistent"][sch.value & 1], "mma_staged": bool(sch.value & 2),
                 "scalar_kernel": not (sch.value & 4), "value_ring": not (sch.value & 8),
-                "persist_warps": pw.value}
+                "pipelined_f32": not (sch.value & 16), "persist_warps": pw.value}
 
     def apply_tuning(self, t: dict):
         for B in range(1, 17):
             self.set_tuning(t["kc_by_b"][B], t["warps_by_b"][B], B)
         self.set_schedule(t["schedule"], t["persist_warps"], t.get("mma_staged", False),
-                          t.get("scalar_kernel", True), t.get("value_ring", True))
+                          t.get("scalar_kernel", True), t.get("value_ring", True), t.get("pipelined_f32", True))
 
     def autotune(self, k: int, precision="native", transpose: bool = False, allow_persistent: bool = True,
                  cache: Optional[str] = None) -> dict:

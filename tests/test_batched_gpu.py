@@ -53,17 +53,28 @@ def test_batched_matches_per_structure_oracle():
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_persistent_schedule_equals_bucketed(dtype):
+    """The persistent launch runs the bucketed launches' per-item arithmetic
+    (bit for bit); the pipelined FP32 kernel, which the persistent launch on
+    FP32 values uses at k >= 8, sums each entry in another order and agrees to
+    FP32 rounding."""
     w, H, vals = _batched(dtype=dtype)
     X = torch.randn(w.pattern.n_cols, 8, dtype=dtype, device="cuda:0")
     H.set_schedule("bucketed")
     Yb = H.spmm(X)
     for warps in (0, 2, 8):
-        H.set_schedule("persistent", warps)
+        H.set_schedule("persistent", warps, pipelined_f32=False)
         Yp = H.spmm(X)
         assert torch.equal(Yb, Yp)     # same per-item arithmetic, only the launch differs
         Ya = H.spmm_adjoint(X)
         H.set_schedule("bucketed")
         assert torch.equal(Ya, H.spmm_adjoint(X))
+    H.set_schedule("persistent")
+    Yq = H.spmm(X)
+    if dtype == torch.float64:
+        assert torch.equal(Yb, Yq)
+    else:
+        _, scale = forward_ref(w.pattern, np.abs(vals), np.abs(X.double().cpu().numpy()), 1.0, 0.0, None)
+        check_elementwise(Yq.double().cpu().numpy(), Yb.double().cpu().numpy(), scale, 1e-5)
 
 
 @pytest.mark.parametrize("k", [1, 8, 20])
@@ -139,10 +150,12 @@ def test_schedule_flags_round_trip_and_validation():
     H.set_schedule("persistent")
     H.apply_tuning(t)
     assert H.get_tuning()["value_ring"] is False and H.get_tuning()["scalar_kernel"] is False
-    for bad in (16, -1):
+    for bad in (32, -1):
         assert lib().vbcsr_set_schedule(H.handle, bad, 0) != 0
     assert lib().vbcsr_set_schedule(H.handle, 1, 3) != 0
-    assert lib().vbcsr_set_schedule(H.handle, 1 | 2 | 4 | 8, 4) == 0
+    assert lib().vbcsr_set_schedule(H.handle, 1 | 2 | 4 | 8 | 16, 4) == 0
+    H.set_schedule("persistent", pipelined_f32=False)
+    assert H.get_tuning()["pipelined_f32"] is False
 
 
 def test_full_size_batched_workload_every_element():

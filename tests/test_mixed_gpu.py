@@ -192,12 +192,13 @@ def test_tensor_core_products_exact_on_small_integers(mode, staged):
 
 @pytest.mark.parametrize("k", [8, 13, 32, 40])
 def test_fp32_value_ring_matches_direct_reads(k):
-    """The CUDA-core forward kernel on FP32 values or double-FP32 pairs reads
-    them through a shared-memory ring at k >= 8 (default) or directly
-    (schedule flag): the same arithmetic in the same order, so the results
-    agree bit for bit, for an FP32 operator and for the F32 and DF32 modes of
-    an FP64 operator, on rows taller than 16 and panels wider than one staged
-    window."""
+    """The per-lane-column CUDA-core forward kernel on FP32 values or
+    double-FP32 pairs reads them through a shared-memory ring at k >= 8
+    (default) or directly (schedule flag): the same arithmetic in the same
+    order, so the results agree bit for bit, for an FP32 operator and for the
+    F32 and DF32 modes of an FP64 operator, on rows taller than 16 and panels
+    wider than one staged window. The pipelined FP32 kernel of the persistent
+    launch meets the FP32 bound against the oracle on the same cases."""
     pat = syn.random_pattern(12, 14, (3, 9, 20, 60), 0.5, 31 + k, empty_rows=1)
     vals = syn.random_values(pat, 31)
     X = np.random.default_rng(k).standard_normal((pat.n_cols, k))
@@ -206,12 +207,16 @@ def test_fp32_value_ring_matches_direct_reads(k):
         Xd = _dev(X, dtype)
         ref, scale = forward_ref(pat, vals, X, 1.0, 0.0, None)
         for sch in ("persistent", "bucketed"):
-            H.set_schedule(sch)
+            H.set_schedule(sch, pipelined_f32=False)
             got_ring = H.spmm(Xd, precision=prec).cpu().numpy()
-            H.set_schedule(sch, value_ring=False)
+            H.set_schedule(sch, value_ring=False, pipelined_f32=False)
             got_direct = H.spmm(Xd, precision=prec).cpu().numpy()
             np.testing.assert_array_equal(got_ring, got_direct)
             check_elementwise(got_ring.astype(np.float64), ref, scale, TOL_F64 if prec == "df32" else 1e-4)
+        # the persistent default on FP32 values: the pipelined kernel (another summation order)
+        H.set_schedule("persistent")
+        got_pipe = H.spmm(Xd, precision=prec).cpu().numpy()
+        check_elementwise(got_pipe.astype(np.float64), ref, scale, TOL_F64 if prec == "df32" else 1e-4)
 
 
 

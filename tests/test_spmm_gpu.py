@@ -504,3 +504,39 @@ def test_structural_domain_full_size_sampled_rows(kind):
             check_elementwise(Y[sel], ref[sel], scale[sel], TOL_F64)
             assert rel_fro(Y[sel], ref[sel]) <= TOL_F64
     H.check()
+
+
+@pytest.mark.parametrize("k,ld", [(8, 8), (12, 12), (12, 16), (16, 16), (20, 24), (32, 32), (33, 36), (40, 40),
+                                  (16, 18)])
+@pytest.mark.parametrize("prec,dtype", [("native", torch.float32), ("f32", torch.float64)])
+def test_pipelined_fp32_kernel(k, ld, prec, dtype):
+    """FP32 values at k >= 8 under the persistent schedule (the pipelined
+    CUDA-core kernel: 4-row register tiles fed from a shared-memory ring),
+    element by element against the oracle on FP32-rounded inputs: rows of
+    every height (1 to 20, rows above 16 cut into items), panels wider than one
+    512-column window, several column passes (k > 32), leading dimensions
+    above k (a multiple of 4; ld = 18 takes the other kernel), alpha / beta,
+    and the fused gamma Z and dot epilogue."""
+    pat = syn.random_pattern(50, 47, (1, 4, 9, 13, 16, 20), 0.2, 60 + k, empty_rows=2, unsorted=True)
+    wide = syn.random_pattern(3, 60, (13,), 0.9, 61, empty_rows=0)
+    vals = syn.random_values(pat, 60 + k).astype(np.float32).astype(np.float64)
+    for p, v in ((pat, vals), (wide, syn.random_values(wide, 62).astype(np.float32).astype(np.float64))):
+        H = _handle(p, v, dtype)
+        H.set_schedule("persistent")
+        rng = np.random.default_rng(k)
+        X = rng.standard_normal((p.n_cols, ld)).astype(np.float32).astype(np.float64)
+        Y0 = rng.standard_normal((p.n_rows, ld)).astype(np.float32).astype(np.float64)
+        Z = rng.standard_normal((p.n_rows, k)).astype(np.float32).astype(np.float64)
+        R = rng.standard_normal((p.n_rows, k)).astype(np.float32).astype(np.float64)
+        Xd, Yd = _dev(X, dtype), _dev(Y0, dtype)
+        dot = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        H.spmm_ex(Xd[:, :k], 1.5, -0.5, Yd[:, :k], gamma=0.25, Z=_dev(Z, dtype), R=_dev(R, dtype), dot_out=dot,
+                  precision=prec)
+        got = Yd.cpu().numpy().astype(np.float64)
+        ref, scale = forward_ref(p, v, X[:, :k], 1.5, -0.5, Y0[:, :k])
+        ref = ref + 0.25 * Z
+        scale = scale + 0.25 * np.abs(Z)
+        check_elementwise(got[:, :k], ref, scale, 1e-5)
+        assert np.array_equal(got[:, k:], Y0[:, k:])          # columns beyond k untouched
+        dref = float(np.sum(R * got[:, :k]))
+        assert abs(dot.item() - dref) <= 1e-6 * float(np.sum(np.abs(R * got[:, :k])))
