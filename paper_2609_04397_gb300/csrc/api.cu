@@ -935,7 +935,9 @@ static int cached_cap(const void *kernel, int warps, size_t smem) {
 }
 
 // Form of X that a product's kernel reads.
-enum { kXAsGiven = 0, kXF32 = 1, kXSplit = 2, kXPairs = 3, kXPlanes = 4 };
+// kXF32P: FP32 with rows pipe_ldp(k) elements apart (the pipelined TF32 kernels), kept in
+// the buffer of the bf16 planes (the same bytes: 2 x 2 B or 4 B per element)
+enum { kXAsGiven = 0, kXF32 = 1, kXSplit = 2, kXPairs = 3, kXPlanes = 4, kXF32P = 5 };
 
 // Which kernel family serves a product, and which mixed-precision copies of
 // the values and of X it reads (built on first use by run_product).
@@ -947,8 +949,9 @@ struct ModePlan {
     bool split;               // a tensor-core mode on the CUDA cores (thin products, scalar operators)
     bool presplit;            // BF16X2 on operands split once into packed bf16 (hi, lo) words
     bool pipe;                // BF16X2 on the tensor cores, operands as bf16 planes through shared memory
+    bool pipe_tf;             // TF32 / TF32X3 on the tensor cores, FP32 operands through shared memory
     bool need_panel32, need_panelbf, need_paneldf, need_panelbp;
-    int xkind;                // kXAsGiven, kXF32, kXSplit, kXPairs or kXPlanes
+    int xkind;                // kXAsGiven, kXF32, kXSplit, kXPairs, kXPlanes or kXF32P
 };
 
 static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision) {
@@ -971,6 +974,12 @@ static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision
     // 8-element, aligned) and with the staged variant selected
     p.pipe = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.split && !p.csr_kernel &&
              !(A->schedule & VBCSR_SCHED_MMA_STAGED) && A->backend != VBCSR_BACKEND_CSR;
+    // the TF32 modes likewise run the pipelined kernel on the FP32 copy of the values, up
+    // to 16 columns (at 17-32 its 32-column tiles hold 4 CTAs per SM and the register-load
+    // kernel is 3 % faster: 0.58 against 0.60 ms at k = 32 on the 50k-atom operator)
+    p.pipe_tf = p.f64 && (p.mode == VBCSR_PREC_TF32 || p.mode == VBCSR_PREC_TF32X3) && !trans && !p.split &&
+                k <= 16 && !p.csr_kernel && !(A->schedule & VBCSR_SCHED_MMA_STAGED) &&
+                A->backend != VBCSR_BACKEND_CSR;
     p.presplit = p.f64 && p.mode == VBCSR_PREC_BF16X2 && !trans && !p.csr_kernel && !p.pipe &&
                  (p.split || !(A->schedule & VBCSR_SCHED_MMA_STAGED));
     p.need_panel32 =
@@ -981,6 +990,7 @@ static ModePlan plan_mode(const vbcsr_t *A, bool trans, int64_t k, int precision
     p.xkind = !p.f64 || p.mode == VBCSR_PREC_NATIVE ? kXAsGiven
             : p.mode == VBCSR_PREC_DF32             ? kXPairs
             : p.pipe                                ? kXPlanes
+            : p.pipe_tf                             ? kXF32P
             : p.presplit                            ? kXSplit
                                                     : kXF32;
     return p;
@@ -998,7 +1008,8 @@ static bool mode_buffers_ready(const vbcsr_t *A, const ModePlan &p, int64_t xrow
         case kXF32: return A->xconv_elems >= need;
         case kXSplit: return A->xbf_elems >= need;
         case kXPairs: return A->xdf_elems >= need;
-        case kXPlanes: return A->xbp_elems >= 2 * (size_t)xrows * (size_t)pipe_ldp(k);
+        case kXPlanes:
+        case kXF32P: return A->xbp_elems >= 2 * (size_t)xrows * (size_t)pipe_ldp(k);
         default: return true;
     }
 }
@@ -1015,7 +1026,8 @@ struct FusedX {
 // True when a forward product of this plan runs the plain tensor-core kernel
 // on a converted X (FP32, or packed bf16 pieces), i.e. when FusedX applies.
 static bool fused_x_applies(const vbcsr_t *A, const ModePlan &p) {
-    return !p.fma && !p.split && !p.cplx && (p.xkind == kXF32 || p.xkind == kXSplit || p.xkind == kXPlanes) &&
+    return !p.fma && !p.split && !p.cplx &&
+           (p.xkind == kXF32 || p.xkind == kXSplit || p.xkind == kXPlanes || p.xkind == kXF32P) &&
            !(A->schedule & VBCSR_SCHED_MMA_STAGED);
 }
 
@@ -1070,7 +1082,8 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         int rc = refresh_panelbp(A, s);
         if (rc) return rc;
     }
-    const int64_t ldp = mp.pipe ? pipe_ldp(k) : 0;   // X row stride of the bf16 planes
+    const bool piped = mp.pipe || mp.pipe_tf;
+    const int64_t ldp = piped ? pipe_ldp(k) : 0;   // X row stride of the pipelined kernels
 
     // The mixed modes read X as FP32 (the double-FP32 mode as hi/lo pairs):
     // convert an FP64 X once here rather than at every gather inside the
@@ -1078,7 +1091,7 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     const bool fused = fx && !trans && fused_x_applies(A, mp);
     if (fused && fx->x_in && alpha != 0.0 && xrows > 0) {
         X = fx->x_in;
-        ldx = mp.pipe ? ldp : k;
+        ldx = piped ? ldp : k;
     } else if (mp.xkind != kXAsGiven && alpha != 0.0 && xrows > 0) {
         const size_t need = (size_t)xrows * (size_t)k;
         if (mp.xkind == kXPlanes) {
@@ -1087,6 +1100,13 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             CUDA_TRY(launch_split_bf16_planes_panel(xrows, k, (const double *)X, ldx, A->xbp,
                                                     A->xbp + (size_t)xrows * ldp, ldp, s),
                      "split X");
+            X = A->xbp;
+            ldx = ldp;
+        } else if (mp.xkind == kXF32P) {
+            int rc = grow(A, &A->xbp, &A->xbp_elems, 2 * (size_t)xrows * (size_t)ldp, s, "alloc FP32 rows of X");
+            if (rc) return rc;
+            CUDA_TRY(launch_convert_panel_f64_to_f32(xrows, k, (const double *)X, ldx, (float *)A->xbp, ldp, s),
+                     "convert X");
             X = A->xbp;
             ldx = ldp;
         } else if (mp.xkind == kXPairs) {
@@ -1102,10 +1122,10 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
         } else {
             int rc = grow(A, &A->xconv, &A->xconv_elems, need, s, "alloc FP32 copy of X");
             if (rc) return rc;
-            CUDA_TRY(launch_convert_panel_f64_to_f32(xrows, k, (const double *)X, ldx, A->xconv, s), "convert X");
+            CUDA_TRY(launch_convert_panel_f64_to_f32(xrows, k, (const double *)X, ldx, A->xconv, k, s), "convert X");
             X = A->xconv;
         }
-        if (mp.xkind != kXPlanes) ldx = k;
+        if (!piped) ldx = k;
     }
 
     // FP32 values (an FP32 operator, or the F32 mode of an FP64 one) at k >= 8 under the
@@ -1126,6 +1146,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
     a.alpha = alpha;
     a.beta = beta;
     a.gamma = gamma;
+    a.alpha32 = (float)alpha;
+    a.beta32 = (float)beta;
+    a.gamma32 = (float)gamma;
+    a.beta_nz = beta != 0.0;
+    a.gamma_nz = gamma != 0.0;
     a.X = X;
     a.ldx = ldx;
     a.Y = Y;
@@ -1197,8 +1222,8 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             e = launch_fma_df(B, trans, a, s, df_narrow);
         else if (split)
             e = launch_fma_split(mma_mode, a, s);
-        else if (mp.pipe)
-            e = launch_mma_pipe(a, s);
+        else if (piped)
+            e = launch_mma_pipe(mp.pipe ? kBF16X2 : mode, a, s);
         else
             e = launch_mma(mma_mode, f64, trans, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "product launch");
@@ -1224,10 +1249,11 @@ static int run_product(vbcsr_t *A, bool trans, int64_t k, double alpha, const vo
             per_item_dot = true;
             CUDA_TRY(cudaMemsetAsync(A->queue, 0, sizeof(long long), s), "reset work counter");
         }
-        const void *kern = mp.pipe ? mma_pipe_kernel_ptr(k) : mma_kernel_ptr(mma_mode, f64, trans, staged, k);
+        const int pmode = mp.pipe ? kBF16X2 : mode;
+        const void *kern = piped ? mma_pipe_kernel_ptr(pmode, k) : mma_kernel_ptr(mma_mode, f64, trans, staged, k);
         if (!kern) return fail(VBCSR_ERR_UNSUPPORTED, "precision %d not available for this operation", precision);
         rc = launch(0, trans ? A->adj_lpt : A->fwd_lpt, n_all, 4, kern,
-                    mp.pipe ? mma_pipe_smem_bytes(k, 4) : mma_smem_bytes(trans, staged, 4));
+                    piped ? mma_pipe_smem_bytes(pmode, k, 4) : mma_smem_bytes(trans, staged, 4));
     } else if (csr_kernel) {
         // scalar operator: several rows per warp; items are the scalar rows in page order
         const int kind = split ? (mode == VBCSR_PREC_TF32 ? kCsrSplitTF32
@@ -1359,7 +1385,7 @@ static int cheb_fused_buffers(vbcsr_t *A, int64_t k, int precision, void *xs[2],
     const ModePlan mp = plan_mode(A, false, k, precision);
     if (!fused_x_applies(A, mp) || A->n_rows == 0) return VBCSR_OK;
     const size_t panel = (size_t)A->n_rows * (size_t)k;
-    if (mp.xkind == kXPlanes) {
+    if (mp.xkind == kXPlanes || mp.xkind == kXF32P) {
         const size_t planes = 2 * (size_t)A->n_rows * (size_t)pipe_ldp(k);
         int rc = grow(A, &A->xbp, &A->xbp_elems, 2 * planes, s, "alloc bf16 planes of the Chebyshev vectors");
         if (rc) return rc;
@@ -2101,7 +2127,8 @@ extern "C" int vbcsr_chebyshev_noalloc(vbcsr_t *A, int64_t k, const double *R, i
         bool ready = mode_buffers_ready(A, mp, A->n_cols, k);
         if (ready && n_moments > 1 && fused_x_applies(A, mp)) {
             const size_t panel = (size_t)A->n_rows * (size_t)k;
-            ready = mp.xkind == kXPlanes ? A->xbp_elems >= 4 * (size_t)A->n_rows * (size_t)pipe_ldp(k)
+            ready = (mp.xkind == kXPlanes || mp.xkind == kXF32P)
+                        ? A->xbp_elems >= 4 * (size_t)A->n_rows * (size_t)pipe_ldp(k)
                   : mp.xkind == kXSplit  ? A->xbf_elems >= 2 * panel
                                          : A->xconv_elems >= 2 * panel;
         }

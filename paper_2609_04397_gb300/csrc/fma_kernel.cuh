@@ -80,9 +80,10 @@ template <typename TX>
 __device__ __forceinline__ void write_out(const ProdArgs &a, int64_t row, int64_t c, TX acc, double &dot) {
     TX *Y = static_cast<TX *>(a.Y);
     TX *yp = Y + row * a.ldy + c;
-    TX r = (TX)a.alpha * acc;
-    if (a.beta != 0.0) r += (TX)a.beta * *yp;
-    if (a.gamma != 0.0) r += (TX)a.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
+    const EpiScalars<TX> sc = epi_scalars<TX>(a);
+    TX r = sc.alpha * acc;
+    if (a.beta_nz) r += sc.beta * *yp;
+    if (a.gamma_nz) r += sc.gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
     *yp = r;
     if (a.partials || a.item_partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
 }
@@ -94,12 +95,12 @@ __device__ __forceinline__ void write_out<double2>(const ProdArgs &a, int64_t ro
                                                    double &dot) {
     double2 *yp = static_cast<double2 *>(a.Y) + row * a.ldy + c;
     double2 r = make_double2(a.alpha * acc.x, a.alpha * acc.y);
-    if (a.beta != 0.0) {
+    if (a.beta_nz) {
         const double2 y = *yp;
         r.x += a.beta * y.x;
         r.y += a.beta * y.y;
     }
-    if (a.gamma != 0.0) {
+    if (a.gamma_nz) {
         const double2 z = static_cast<const double2 *>(a.Z)[row * a.ldz + c];
         r.x += a.gamma * z.x;
         r.y += a.gamma * z.y;

@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace vbcsr {
 
 constexpr int kMaxB = 16;        // rows per work item
@@ -76,6 +78,8 @@ struct ProdArgs {
     int64_t k;
     int kc;                 // output columns per warp pass (power of two <= 32)
     double alpha, beta, gamma;
+    float alpha32, beta32, gamma32;   // the same rounded to FP32 once on the host (FP32 epilogues)
+    int beta_nz, gamma_nz;  // beta != 0, gamma != 0 (tested once on the host, not per element)
     const void *X; int64_t ldx;
     void *Y; int64_t ldy;
     const void *Z; int64_t ldz;
@@ -105,6 +109,18 @@ struct ProdArgs {
     __host__ __device__ int kc_of(int B) const { return 1 << ((kc_log2_by_b >> (3 * B)) & 7); }
 };
 
+// alpha, beta, gamma in an epilogue's type: the FP32 copies for FP32 outputs,
+// so that no element pays an FP64 conversion
+template <typename TX>
+struct EpiScalars {
+    TX alpha, beta, gamma;
+};
+template <typename TX>
+__device__ __forceinline__ EpiScalars<TX> epi_scalars(const ProdArgs &a) {
+    if constexpr (std::is_same<TX, float>::value) return {a.alpha32, a.beta32, a.gamma32};
+    else return {(TX)a.alpha, (TX)a.beta, (TX)a.gamma};
+}
+
 // Kernel families (defined in spmm_fma_*.cu and spmm_mma.cu). B = 0 selects
 // the persistent launch over items of every row count.
 // value/accumulate/X types: f64 = <double,double,double>; f32 = <float,float,float>;
@@ -119,11 +135,12 @@ cudaError_t launch_fma_df(int B, bool trans, const ProdArgs &a, cudaStream_t s, 
 cudaError_t launch_split_df(int64_t rows, int64_t k, const double *in, int64_t ld, float2 *out, cudaStream_t s);
 // mode: 2 = TF32, 3 = TF32X3, 4 = BF16X2 (vbcsr_precision values); xdouble: X/Y are FP64
 cudaError_t launch_mma(int mode, bool xdouble, bool trans, const ProdArgs &a, cudaStream_t s);
-// BF16X2 forward of an FP64 operator pipelined through shared memory (spmm_mma_pipe.cu):
-// values and X as bf16 hi / lo planes (X rows pipe_ldp(k) elements apart)
-cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s);
-const void *mma_pipe_kernel_ptr(int64_t k);
-size_t mma_pipe_smem_bytes(int64_t k, int warps);
+// Tensor-core forward of an FP64 operator pipelined through shared memory (spmm_mma_pipe.cu):
+// mode kBF16X2: values and X as bf16 hi / lo planes; kTF32 / kTF32X3: the FP32 copy of the
+// values and X as FP32; X rows pipe_ldp(k) elements apart in either form
+cudaError_t launch_mma_pipe(int mode, const ProdArgs &a, cudaStream_t s);
+const void *mma_pipe_kernel_ptr(int mode, int64_t k);
+size_t mma_pipe_smem_bytes(int mode, int64_t k, int warps);
 int64_t pipe_ldp(int64_t k);
 // FP32-value forward product on the CUDA cores pipelined through shared memory (k >= 8;
 // X rows 16-byte aligned: ldx a multiple of 4); ydouble: FP64 Y (the F32 mode of an FP64 operator)
@@ -259,6 +276,7 @@ cudaError_t launch_split_bf16_panel(int64_t rows, int64_t k, const double *in, i
                                     cudaStream_t s);
 // out[rows, k] (leading dimension k) = FP32 of the FP64 panel in (leading dimension ld)
 cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
+                                            int64_t ldo,
                                             cudaStream_t s);
 // out[0] = scale * sum(partials[0..n)) in a fixed order (set by n alone); long sums
 // go through `scratch` (kDotScratch doubles, or NULL for the one-CTA sum)

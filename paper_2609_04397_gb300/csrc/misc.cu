@@ -337,19 +337,20 @@ cudaError_t launch_split_bf16_planes_panel(int64_t rows, int64_t k, const double
     return cudaGetLastError();
 }
 
-__global__ void convert_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, float *out) {
+__global__ void convert_panel_kernel(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
+                                     int64_t ldo) {
     const int64_t n = rows * k;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / k, c = e - r * k;
-        out[e] = (float)in[r * ld + c];
+        out[r * ldo + c] = (float)in[r * ld + c];
     }
 }
 
 cudaError_t launch_convert_panel_f64_to_f32(int64_t rows, int64_t k, const double *in, int64_t ld, float *out,
-                                            cudaStream_t s) {
+                                            int64_t ldo, cudaStream_t s) {
     const int64_t need = (rows * k + 255) / 256;
     if (need == 0) return cudaSuccess;
-    convert_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, in, ld, out);
+    convert_panel_kernel<<<(int)(need < 65536 ? need : 65536), 256, 0, s>>>(rows, k, in, ld, out, ldo);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(256) csr_kernel(ProdArgs a) {
     const TV *__restrict__ vals = static_cast<const TV *>(a.values);
     const TXI *__restrict__ X = static_cast<const TXI *>(a.X);
     TX *__restrict__ Y = static_cast<TX *>(a.Y);
-    const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
+    const EpiScalars<TX> sc = epi_scalars<TX>(a);
+    const TX alpha = sc.alpha, beta = sc.beta, gamma = sc.gamma;
     const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
     for (int64_t base = ((int64_t)blockIdx.x * warps + warp) * RPW; base < a.n_items;
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(256) csr_kernel(ProdArgs a) {
                 if (valid && lr == (j % L) && c0 + j < a.k) {
                     const int64_t row = w.yrow, c = c0 + j;
                     TX r = alpha * (TX)acc[j];
-                    if (a.beta != 0.0) r += beta * Y[row * a.ldy + c];
-                    if (a.gamma != 0.0) r += gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
+                    if (a.beta_nz) r += beta * Y[row * a.ldy + c];
+                    if (a.gamma_nz) r += gamma * static_cast<const TX *>(a.Z)[row * a.ldz + c];
                     Y[row * a.ldy + c] = r;
                     if (a.partials) dot += (double)static_cast<const TX *>(a.R)[row * a.ldr + c] * (double)r;
                 }

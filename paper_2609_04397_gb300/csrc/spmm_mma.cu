@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(128, MmaShape<MODE, NT>::CTAS) mma_product_ker
     const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
     const TX *__restrict__ R = static_cast<const TX *>(a.R);
     float *__restrict__ XS = static_cast<float *>(a.xs_out);
-    const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
+    const EpiScalars<TX> sc = epi_scalars<TX>(a);
+    const TX alpha = sc.alpha, beta = sc.beta, gamma = sc.gamma;
     const bool do_prod = a.alpha != 0.0;
     double dot = 0.0;
 
@@ -294,8 +295,8 @@ __global__ void __launch_bounds__(128, MmaShape<MODE, NT>::CTAS) mma_product_ker
                         const int64_t row = w.yrow + r;
                         TX *yp = Y + row * a.ldy + col;
                         TX v = alpha * (TX)acc[n][j];
-                        if (a.beta != 0.0) v += beta * *yp;
-                        if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
+                        if (a.beta_nz) v += beta * *yp;
+                        if (a.gamma_nz) v += gamma * Z[row * a.ldz + col];
                         *yp = v;
                         if (a.partials || a.item_partials) dot += (double)R[row * a.ldr + col] * (double)v;
                         if (!TRANS && XS) XS[row * a.k + col] = xs_form<MODE, TX>(v);
@@ -403,7 +404,8 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
     TX *__restrict__ Y = static_cast<TX *>(a.Y);
     const TX *__restrict__ Z = static_cast<const TX *>(a.Z);
     const TX *__restrict__ R = static_cast<const TX *>(a.R);
-    const TX alpha = (TX)a.alpha, beta = (TX)a.beta, gamma = (TX)a.gamma;
+    const EpiScalars<TX> sc = epi_scalars<TX>(a);
+    const TX alpha = sc.alpha, beta = sc.beta, gamma = sc.gamma;
     const bool do_prod = a.alpha != 0.0;
     const int64_t stride = (int64_t)gridDim.x * warps;
     const int64_t npass = (a.k + 8 * NT - 1) / (8 * NT);
@@ -449,8 +451,8 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
             for (int64_t col = lane; col < (int64_t)w.B * a.k; col += 32) {
                 const int64_t row = w.yrow + col / a.k, c = col % a.k;
                 TX v = (TX)0;
-                if (a.beta != 0.0) v += beta * Y[row * a.ldy + c];
-                if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + c];
+                if (a.beta_nz) v += beta * Y[row * a.ldy + c];
+                if (a.gamma_nz) v += gamma * Z[row * a.ldz + c];
                 Y[row * a.ldy + c] = v;
                 if (a.partials) dot += (double)R[row * a.ldr + c] * (double)v;
             }
@@ -569,8 +571,8 @@ __global__ void __launch_bounds__(128, 4) mma_staged_kernel(ProdArgs a) {
                             const int64_t row = wc.yrow + r;
                             TX *yp = Y + row * a.ldy + col;
                             TX v = alpha * (TX)acc[n][j];
-                            if (a.beta != 0.0) v += beta * *yp;
-                            if (a.gamma != 0.0) v += gamma * Z[row * a.ldz + col];
+                            if (a.beta_nz) v += beta * *yp;
+                            if (a.gamma_nz) v += gamma * Z[row * a.ldz + col];
                             *yp = v;
                             if (a.partials) dot += (double)R[row * a.ldr + col] * (double)v;
                         }

@@ -315,6 +315,242 @@ cudaError_t pipe_launch(const ProdArgs &a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// TF32 / TF32X3 forward product of an FP64 operator pipelined the same way:
+// the FP32 copy of the values and X as FP32 rows of ldp elements stream
+// through the per-warp ring (16 virtual columns per stage). The value tile
+// is read by ldmatrix (a 16 x 8 FP32 tile viewed as four 8 x 8 b16 matrices
+// lands in exactly the m16n8k8 TF32 A-fragment layout), the X tile by 32-bit
+// shared loads; each operand is cut into tf32 pieces in registers (hi =
+// rna(v), lo = rna(v - hi)), and TF32 multiplies hi*hi, TF32X3 adds hi*lo +
+// lo*hi, all accumulated in FP32 (m16n8k8); the epilogue is FP64 and writes
+// the output also as FP32 rows of ldp elements when the next product of a
+// recurrence reads it.
+
+template <int NT>
+struct TfStage {
+    static constexpr int kV = 16 * 64;         // values: 16 rows x 16 FP32
+    static constexpr int kXRow = 32 * NT;      // X: 16 rows x 8 NT FP32
+    static constexpr int kBytes = kV + 16 * kXRow;
+};
+
+// byte offset of 16-byte chunk c (4 FP32) of value row r: XOR-swizzled so that
+// the eight rows of each ldmatrix matrix fall on distinct banks
+__device__ __forceinline__ int tv_off(int r, int c) { return r * 64 + 16 * (c ^ ((r >> 1) & 3)); }
+
+// physical chunk of chunk c of X row r: swizzled so that the four rows t, or
+// t + 4, of one B-fragment load fall on distinct banks
+template <int NT>
+__device__ __forceinline__ int tx_chunk(int r, int c) {
+    return NT == 4 ? (c ^ (2 * (r & 3))) : NT == 2 ? (c ^ (2 * ((r >> 1) & 1))) : c;
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void mma1688(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(128, 4) mma_tf32_pipe_kernel(ProdArgs a) {
+    constexpr int S = kPipeStages;
+    using St = TfStage<NT>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warps = a.warps;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    unsigned char *ring = smem_raw + (size_t)warp * S * St::kBytes;
+    int32_t *s_x = reinterpret_cast<int32_t *>(smem_raw + (size_t)warps * S * St::kBytes) + warp * kKMax;
+    const uint32_t ring_s = smem_addr(ring);
+
+    const float *__restrict__ vals = static_cast<const float *>(a.values);
+    const float *__restrict__ X = static_cast<const float *>(a.X);
+    double *__restrict__ Y = static_cast<double *>(a.Y);
+    const double *__restrict__ Z = static_cast<const double *>(a.Z);
+    const double *__restrict__ R = static_cast<const double *>(a.R);
+    float *__restrict__ XS = static_cast<float *>(a.xs_out);   // [rows, ldp], or NULL
+    const int64_t ldp = a.ldx;
+    const bool do_prod = a.alpha != 0.0;
+    const bool want_dot = a.partials || a.item_partials;
+    double dot = 0.0;
+
+    // this lane's value copies: row vr, chunks vc, vc + 1 (columns 8 (lane & 1) .. + 7)
+    const int vr = lane >> 1, vc = 2 * (lane & 1);
+    const bool x32 = (uint64_t)a.x_rows * (uint64_t)ldp < (1ull << 31);
+    // A fragments: lane supplies row ar of matrix lane / 8 (chunk ac of a substep)
+    const int ar = ((lane >> 3) & 1) * 8 + (lane & 7), ac = lane >> 4;
+
+    int64_t it = (int64_t)blockIdx.x * warps + warp;
+    for (;;) {
+        if (a.queue) {
+            unsigned long long q = 0;
+            if (lane == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(a.queue), 1ull);
+            it = (int64_t)__shfl_sync(0xffffffffu, q, 0);
+        }
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+        const float *vrow = vals + (w.vbase + (int64_t)min(vr, w.B - 1) * w.Kp);
+        for (int64_t n0 = 0; n0 < a.k; n0 += 8 * NT) {
+            float acc[NT][4];
+#pragma unroll
+            for (int n = 0; n < NT; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[n][j] = 0.f;
+
+            if (do_prod) {
+                for (int t0 = 0; t0 < w.K; t0 += kKMax) {
+                    const int tn = min(kKMax, w.K - t0);
+                    const int nsteps = (tn + 15) >> 4;
+                    if (n0 == 0 || w.K > kKMax) {
+                        __syncwarp();
+                        for (int e = lane; e < w.nlist; e += 32) {
+                            const int64_t l = w.lbegin + e;
+                            const int xr = a.fl.xrow[l], pc = a.fl.pcol[l], wd = a.fl.w[l];
+                            const int lo = max(pc, t0), hi = min(pc + wd, t0 + tn);
+                            for (int t = lo; t < hi; ++t) s_x[t - t0] = xr + (t - pc);
+                        }
+                        __syncwarp();
+                    }
+                    auto issue = [&](int s) {
+                        if (s < nsteps) {
+                            const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
+                            if (vr < w.B) {
+#pragma unroll
+                                for (int c = vc; c < vc + 2; ++c) {
+                                    const int col = t0 + 16 * s + 4 * c;
+                                    const bool ok = col < w.Kp;   // Kp is a multiple of 8
+                                    cp16(st + tv_off(vr, c), vrow + (ok ? col : 0), ok);
+                                }
+                            }
+                            // the X tile: 16 rows x 2 NT chunks; lane takes (row, chunk) pairs
+                            // lane, lane + 32, ... below 32 NT
+#pragma unroll
+                            for (int i = 0; i < NT; ++i) {
+                                const int idx = lane + 32 * i;
+                                const int v = idx / (2 * NT), c = idx % (2 * NT);
+                                const int t = 16 * s + v;
+                                const bool ok = t < tn;
+                                const int xr = ok ? s_x[t] : 0;
+                                const float *src = x32 ? X + ((uint32_t)xr * (uint32_t)ldp + (uint32_t)n0 + 4u * c)
+                                                       : X + ((int64_t)xr * ldp + n0 + 4 * c);
+                                cp16(st + St::kV + v * St::kXRow + 16 * tx_chunk<NT>(v, c), src, ok);
+                            }
+                        }
+                        cp_commit();
+                    };
+#pragma unroll
+                    for (int s = 0; s < S - 1; ++s) issue(s);
+                    for (int s = 0; s < nsteps; ++s) {
+                        cp_wait<S - 2>();
+                        __syncwarp();
+                        issue(s + S - 1);
+                        const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
+                        const unsigned char *stp = ring + (s % S) * St::kBytes;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {   // two k8 substeps per stage
+                            uint32_t av[4], ahi[4], alo[4];
+                            ldsm_x4(st + tv_off(ar, 2 * j + ac), av);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                ahi[q] = tf32_bits(__uint_as_float(av[q]));
+                                if (MODE == kTF32X3)
+                                    alo[q] = tf32_bits(__uint_as_float(av[q]) - __uint_as_float(ahi[q]));
+                            }
+                            const int r0 = 8 * j + t4, r1 = r0 + 4;
+#pragma unroll
+                            for (int n = 0; n < NT; ++n) {
+                                const int col = 8 * n + g;
+                                const float b0 = *reinterpret_cast<const float *>(
+                                    stp + St::kV + r0 * St::kXRow + 16 * tx_chunk<NT>(r0, col >> 2) + 4 * (col & 3));
+                                const float b1 = *reinterpret_cast<const float *>(
+                                    stp + St::kV + r1 * St::kXRow + 16 * tx_chunk<NT>(r1, col >> 2) + 4 * (col & 3));
+                                const uint32_t bh0 = tf32_bits(b0), bh1 = tf32_bits(b1);
+                                mma1688(acc[n], ahi, bh0, bh1);
+                                if (MODE == kTF32X3) {
+                                    const uint32_t bl0 = tf32_bits(b0 - __uint_as_float(bh0));
+                                    const uint32_t bl1 = tf32_bits(b1 - __uint_as_float(bh1));
+                                    mma1688(acc[n], ahi, bl0, bl1);
+                                    mma1688(acc[n], alo, bh0, bh1);
+                                }
+                            }
+                        }
+                    }
+                    cp_wait_all();
+                    __syncwarp();
+                }
+            }
+            // epilogue: acc[n] = {(g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)} of tile n
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = g + 8 * h;
+                if (r >= w.B) continue;
+                const int64_t row = w.yrow + r;
+                double *yrow = Y + row * a.ldy + n0;
+                const double *zrow = Z + row * a.ldz + n0;
+                const double *rrow = R + row * a.ldr + n0;
+                float *xsrow = XS + (row * ldp + n0);
+#pragma unroll
+                for (int n = 0; n < NT; ++n) {
+                    const int cl = n * 8 + 2 * t4;   // column relative to n0
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (n0 + cl + e >= a.k) break;
+                        double o = a.alpha * (double)acc[n][2 * h + e];
+                        if (a.beta != 0.0) o += a.beta * yrow[cl + e];
+                        if (a.gamma != 0.0) o += a.gamma * zrow[cl + e];
+                        yrow[cl + e] = o;
+                        if (want_dot) dot += rrow[cl + e] * o;
+                        if (XS) xsrow[cl + e] = (float)o;
+                    }
+                }
+            }
+        }
+        if (a.item_partials) {
+            for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+            if (lane == 0) a.item_partials[it] = dot;
+            dot = 0.0;
+        }
+        if (!a.queue) it += (int64_t)gridDim.x * warps;
+    }
+
+    if (a.partials) {
+        for (int m = 16; m > 0; m >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, m);
+        __shared__ double s_dot[32];
+        __syncthreads();
+        if (lane == 0) s_dot[warp] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int i = 0; i < warps; ++i) sum += s_dot[i];
+            a.partials[blockIdx.x] = sum;
+        }
+    }
+}
+
+template <int NT>
+size_t tf_smem(int warps) {
+    return (size_t)warps * ((size_t)kPipeStages * TfStage<NT>::kBytes + kKMax * sizeof(int32_t));
+}
+
+template <int NT, int MODE>
+cudaError_t tf_launch(const ProdArgs &a, cudaStream_t s) {
+    const size_t smem = tf_smem<NT>(a.warps);
+    cudaError_t e = cudaFuncSetAttribute((const void *)mma_tf32_pipe_kernel<NT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    mma_tf32_pipe_kernel<NT, MODE><<<a.grid, a.warps * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // FP32-value forward product on the CUDA cores, pipelined the same way: FP32
 // values (an FP32 operator, or the FP32 copy of an FP64 operator in the F32
 // mode) and the gathered FP32 X tile stream through a ring of shared-memory
@@ -384,7 +620,7 @@ __device__ __forceinline__ void f32_stage(const unsigned char *st, int rg, int c
 }
 
 template <int NT, typename TX>
-__global__ void __launch_bounds__(128, 4) fma32_pipe_kernel(ProdArgs a) {
+__global__ void __launch_bounds__(128, NT <= 2 ? 5 : 4) fma32_pipe_kernel(ProdArgs a) {
     constexpr int S = F32Pipe<NT>::S;
     using P = F32Pipe<NT>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -402,6 +638,7 @@ __global__ void __launch_bounds__(128, 4) fma32_pipe_kernel(ProdArgs a) {
     const int64_t ldx = a.ldx;
     const bool do_prod = a.alpha != 0.0;
     const bool want_dot = a.partials || a.item_partials;
+    const EpiScalars<TX> sc = epi_scalars<TX>(a);
     double dot = 0.0;
     const int rg = lane & 3, cg = (lane >> 2) % P::CG, vg = lane / (4 * P::CG);
     // this lane's copies: value chunk (row vrow_, chunk vc_) x 2; X chunks below
@@ -499,9 +736,9 @@ __global__ void __launch_bounds__(128, 4) fma32_pipe_kernel(ProdArgs a) {
                         const int64_t col = n0 + cg * P::CPL + j;
                         if (col >= a.k) continue;
                         TX *yp = Y + row * a.ldy + col;
-                        TX o = (TX)a.alpha * (TX)acc[i][j];
-                        if (a.beta != 0.0) o += (TX)a.beta * *yp;
-                        if (a.gamma != 0.0) o += (TX)a.gamma * Z[row * a.ldz + col];
+                        TX o = sc.alpha * (TX)acc[i][j];
+                        if (a.beta_nz) o += sc.beta * *yp;
+                        if (a.gamma_nz) o += sc.gamma * Z[row * a.ldz + col];
                         *yp = o;
                         if (want_dot) dot += (double)R[row * a.ldr + col] * (double)o;
                     }
@@ -553,19 +790,32 @@ int64_t pipe_ldp(int64_t k) {
     return (k + w - 1) / w * w;
 }
 
-size_t mma_pipe_smem_bytes(int64_t k, int warps) {
+size_t mma_pipe_smem_bytes(int mode, int64_t k, int warps) {
     const int nt = pipe_nt(k);
+    if (mode != kBF16X2) return nt == 1 ? tf_smem<1>(warps) : nt == 2 ? tf_smem<2>(warps) : tf_smem<4>(warps);
     return nt == 1 ? pipe_smem<1>(warps) : nt == 2 ? pipe_smem<2>(warps) : pipe_smem<4>(warps);
 }
 
-const void *mma_pipe_kernel_ptr(int64_t k) {
+const void *mma_pipe_kernel_ptr(int mode, int64_t k) {
     const int nt = pipe_nt(k);
+    if (mode == kTF32)
+        return nt == 1 ? (const void *)mma_tf32_pipe_kernel<1, kTF32>
+                       : nt == 2 ? (const void *)mma_tf32_pipe_kernel<2, kTF32>
+                                 : (const void *)mma_tf32_pipe_kernel<4, kTF32>;
+    if (mode == kTF32X3)
+        return nt == 1 ? (const void *)mma_tf32_pipe_kernel<1, kTF32X3>
+                       : nt == 2 ? (const void *)mma_tf32_pipe_kernel<2, kTF32X3>
+                                 : (const void *)mma_tf32_pipe_kernel<4, kTF32X3>;
     return nt == 1 ? (const void *)mma_bf16_pipe_kernel<1>
                    : nt == 2 ? (const void *)mma_bf16_pipe_kernel<2> : (const void *)mma_bf16_pipe_kernel<4>;
 }
 
-cudaError_t launch_mma_pipe(const ProdArgs &a, cudaStream_t s) {
+cudaError_t launch_mma_pipe(int mode, const ProdArgs &a, cudaStream_t s) {
     const int nt = pipe_nt(a.k);
+    if (mode == kTF32) return nt == 1 ? tf_launch<1, kTF32>(a, s) : nt == 2 ? tf_launch<2, kTF32>(a, s)
+                                                                           : tf_launch<4, kTF32>(a, s);
+    if (mode == kTF32X3) return nt == 1 ? tf_launch<1, kTF32X3>(a, s) : nt == 2 ? tf_launch<2, kTF32X3>(a, s)
+                                                                               : tf_launch<4, kTF32X3>(a, s);
     if (nt == 1) return pipe_launch<1>(a, s);
     if (nt == 2) return pipe_launch<2>(a, s);
     return pipe_launch<4>(a, s);

@@ -131,11 +131,13 @@ def test_mixed_copy_follows_set_values():
 @pytest.mark.parametrize("k", [1, 8, 16, 40])
 def test_staged_forward_kernel_matches_plain(mode, k):
     """The shared-memory-staged tensor-core forward kernel computes the same
-    products as the plain one (same fragments, same summation order), incl.
-    wide panels that span several stages and rows of every height. The plain
-    BF16X2 kernel of an FP64 operator (bf16 planes through a shared-memory
-    ring, k >= 3) feeds each MMA the same 16 virtual columns in another slot
-    order, so there the two agree to FP32 rounding of the accumulation."""
+    products as the plain one, incl. wide panels that span several stages and
+    rows of every height. At k <= 2 both run the same CUDA-core piece products
+    and agree bit for bit; at k >= 3 the plain forward of an FP64 operator is
+    the pipelined kernel (bf16 planes, or FP32 operands, through a
+    shared-memory ring), which feeds each MMA the same virtual columns in
+    another slot order, so there the two agree to FP32 rounding of the
+    accumulation."""
     pat = syn.random_pattern(45, 45, (1, 4, 9, 13, 16, 20, 70), 0.2, 40 + k, empty_rows=3, unsorted=True)
     vals = syn.random_values(pat, 40 + k)
     H = _handle(pat, vals)
@@ -146,9 +148,10 @@ def test_staged_forward_kernel_matches_plain(mode, k):
     H.set_schedule("bucketed", mma_staged=True)
     Ys = Y0.clone()
     H.spmm(X, 2.0, -1.0, Ys, precision=mode)
-    if mode == "bf16x2" and k >= 3:
+    if k >= 3:
         _, scale = forward_ref(pat, np.abs(vals), np.abs(X.cpu().numpy()), 2.0, 1.0, np.abs(Y0.cpu().numpy()))
-        check_elementwise(Yp.cpu().numpy(), Ys.cpu().numpy().astype(np.float64), scale, 1e-6)
+        check_elementwise(Yp.cpu().numpy(), Ys.cpu().numpy().astype(np.float64), scale,
+                          1e-6 if mode == "bf16x2" else 1e-5)
     else:
         assert torch.equal(Yp, Ys)
     if mode != "tf32":
@@ -252,3 +255,43 @@ def test_recurrence_with_converted_vectors_matches_per_step_conversion(mode, k):
     assert np.abs(fused.cpu().numpy() - ref).max() <= tol
     kpm = H.kpm_moments(R, M, precision=mode).cpu().numpy()
     assert np.abs(kpm - ref).max() <= tol
+
+
+
+@pytest.mark.parametrize("k", [3, 8, 16, 20, 32])
+def test_pipelined_kernels_on_ragged_shapes(k):
+    """The pipelined tensor-core (BF16X2, TF32X3, TF32 of an FP64 operator)
+    and FP32 (FP32 operator, F32 mode) forward kernels on an operator with empty block rows (items without
+    columns), rows taller than 16 (several items per block row) and rows wider
+    than 512 virtual columns (several shared-memory windows per item), with
+    alpha, beta, gamma Z and the fused dot: every element within the mode's
+    bound of the oracle, the dot equal to the oracle's sum of R * Y within
+    the same bound, and alpha = 0 reading no product."""
+    pat = syn.random_pattern(14, 40, (3, 9, 20, 60), 0.6, 70 + k, empty_rows=2)
+    vals = syn.random_values(pat, 71)
+    assert int(pat.row_bsize.max()) > 16
+    kw = [int(pat.col_bsize[pat.block_col_idx[pat.block_row_ptr[i]:pat.block_row_ptr[i + 1]]].sum())
+          for i in range(len(pat.row_bsize))]
+    assert max(kw) > 512 and min(kw) == 0
+    rng = np.random.default_rng(k)
+    X = rng.standard_normal((pat.n_cols, k))
+    Y0 = rng.standard_normal((pat.n_rows, k))
+    Zn = rng.standard_normal((pat.n_rows, k))
+    Rn = rng.standard_normal((pat.n_rows, k))
+    cases = [(torch.float64, "bf16x2", 1e-4), (torch.float64, "tf32x3", 1e-4), (torch.float64, "tf32", 2.0 ** -9)]
+    if k >= 8:
+        cases += [(torch.float32, "native", 1e-4), (torch.float64, "f32", 1e-4)]
+    for dtype, prec, tol in cases:
+        H = _handle(pat, vals.astype(np.float32) if dtype == torch.float32 else vals, dtype)
+        for alpha, beta, gamma in ((1.0, 0.0, 0.0), (2.0, -1.0, 0.5), (0.0, 1.5, 0.0)):
+            Yd = _dev(Y0, dtype)
+            dot = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+            H.spmm_ex(_dev(X, dtype), alpha, beta, Yd, gamma=gamma, Z=_dev(Zn, dtype), R=_dev(Rn, dtype),
+                      dot_out=dot, precision=prec)
+            ref, scale = forward_ref(pat, vals, X, alpha, beta, Y0)
+            ref = ref + gamma * Zn
+            got = Yd.cpu().numpy().astype(np.float64)
+            check_elementwise(got, ref, scale + abs(gamma) * np.abs(Zn), tol)
+            rdot = float(np.sum(Rn * ref))
+            bound = tol * float(np.sum(np.abs(Rn) * (scale + abs(gamma) * np.abs(Zn))))
+            assert abs(dot.item() - rdot) <= bound, (prec, alpha, dot.item(), rdot)
