@@ -68,7 +68,7 @@ FP64_PROBE_TFLOPS = 1.19
 # (3.770 GB per launch, mean of two launches, 336,743,405 entries), scaled by
 # the stored entries to the headline operator (values, X, Y and R all grow
 # with the atom count). The summary is under profiles/.
-TRAFFIC_F64_PER_ENTRY = 11.194
+TRAFFIC_F64_PER_ENTRY = 11.197
 
 
 def _workload(n_atoms=N_ATOMS):

@@ -202,7 +202,6 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
                     for (int s = 0; s < nsteps; ++s) {
                         cp_wait<S - 2>();
                         __syncwarp();
-                        issue(s + S - 1);
                         const uint32_t st = ring_s + (uint32_t)((s % S) * St::kBytes);
                         // A fragments: matrices (rows 0-7 | 8-15) x (columns 0-7 | 8-15)
                         const int am = lane >> 3, ar = (lane & 7) + 8 * (am & 1), ac = am >> 1;
@@ -234,6 +233,7 @@ __global__ void __launch_bounds__(128, 4) mma_bf16_pipe_kernel(ProdArgs a) {
                                 mma16816(acc[n + 1], alo, bh[2], bh[3]);
                             }
                         }
+                        issue(s + S - 1);
                     }
                     cp_wait_all();
                     __syncwarp();
