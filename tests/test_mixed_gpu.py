@@ -260,8 +260,9 @@ def test_recurrence_with_converted_vectors_matches_per_step_conversion(mode, k):
 
 @pytest.mark.parametrize("k", [3, 8, 16, 20, 32])
 def test_pipelined_kernels_on_ragged_shapes(k):
-    """The pipelined tensor-core (BF16X2, TF32X3, TF32 of an FP64 operator)
-    and FP32 (FP32 operator, F32 mode) forward kernels on an operator with empty block rows (items without
+    """The pipelined tensor-core (BF16X2, TF32X3, TF32 of an FP64 operator),
+    FP32 (FP32 operator, F32 mode) and double-FP32 (DF32 mode) forward
+    kernels on an operator with empty block rows (items without
     columns), rows taller than 16 (several items per block row) and rows wider
     than 512 virtual columns (several shared-memory windows per item), with
     alpha, beta, gamma Z and the fused dot: every element within the mode's
@@ -280,7 +281,7 @@ def test_pipelined_kernels_on_ragged_shapes(k):
     Rn = rng.standard_normal((pat.n_rows, k))
     cases = [(torch.float64, "bf16x2", 1e-4), (torch.float64, "tf32x3", 1e-4), (torch.float64, "tf32", 2.0 ** -9)]
     if k >= 8:
-        cases += [(torch.float32, "native", 1e-4), (torch.float64, "f32", 1e-4)]
+        cases += [(torch.float32, "native", 1e-4), (torch.float64, "f32", 1e-4), (torch.float64, "df32", TOL_F64)]
     for dtype, prec, tol in cases:
         H = _handle(pat, vals.astype(np.float32) if dtype == torch.float32 else vals, dtype)
         for alpha, beta, gamma in ((1.0, 0.0, 0.0), (2.0, -1.0, 0.5), (0.0, 1.5, 0.0)):
