@@ -23,6 +23,7 @@ of 256 uneven structures.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
+import contextlib
 import json
 import os
 import statistics
@@ -43,6 +44,23 @@ M_MIXED = 51                 # moments of the full recurrence (50 steps) in the 
 KS = (1, 8, 32)              # widths of the secondary 50k-atom product section
 N_ATOMS_50K = 50_000
 GOLDEN_1M = os.path.join(ROOT, "tests", "golden", "zincblende_1m_moments.json")
+
+
+@contextlib.contextmanager
+def _section(name):
+    """An NVTX range around a bench section, so that a profiler can be told to
+    capture the kernels of one section only (ncu --nvtx --nvtx-include name/)."""
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+        pushed = True
+    except Exception:
+        pushed = False
+    try:
+        yield
+    finally:
+        if pushed:
+            torch.cuda.nvtx.range_pop()
 
 
 def _peaks():
@@ -763,8 +781,12 @@ def run_ours(args):
 
     secondary = None
     if not args.no_secondary:
-        secondary = zincblende_50k_section(dev, args.steps)
-    batched = batched_section(dev, args.steps) if not args.no_batched else None
+        with _section("zincblende_50k"):
+            secondary = zincblende_50k_section(dev, args.steps)
+    batched = None
+    if not args.no_batched:
+        with _section("batched"):
+            batched = batched_section(dev, args.steps)
     domains = domains_section(dev, args.steps) if args.domains else None
     kspace = kspace_section(dev, args.steps, max(1, round((N_ATOMS_50K / 8) ** (1 / 3)))) if args.kspace else None
     spg = spgemm_section(dev) if args.spgemm else None
