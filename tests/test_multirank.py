@@ -69,3 +69,15 @@ def test_reference_arm_prints_one_line():
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
+
+
+def test_build_waves_bound_host_memory():
+    """The ranks of a multi-GPU bench build their operators in waves small
+    enough for the host's memory: all at once for small operators, fewer at a
+    time as the operator grows, never zero."""
+    import bench
+    assert bench._build_waves(1, 1_000_000) == 1
+    assert bench._build_waves(8, 1000) == 8
+    assert bench._build_waves(8, 10 ** 12) == 1
+    w = bench._build_waves(8, 1_000_000)
+    assert 1 <= w <= 8
