@@ -563,10 +563,20 @@ def zincblende_50k_section(dev, steps):
     return res
 
 
+def _first_rows(pat, values, rows):
+    """The first `rows` block rows as an operator of their own (every block
+    column kept): the sample the CPU arms time, without full-size copies."""
+    nb = int(pat.block_row_ptr[rows])
+    nnz = int(np.sum(pat.block_sizes()[:nb]))
+    sub = type(pat)(pat.row_bsize[:rows], pat.col_bsize, pat.block_row_ptr[:rows + 1], pat.block_col_idx[:nb])
+    return sub, values[:nnz]
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores (rank 0 only), on
     a bounded sample of the headline workload: each step is one Chebyshev
-    step's product (2 H~ t_n - t_{n-1}, k = 16) over the first block rows."""
+    step's product (2 H~ t_n - t_{n-1}, k = 16) over the first block rows,
+    as many as take about a second and a half per step."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -575,18 +585,24 @@ def run_reference(args):
     import oracle
     cores = os.cpu_count() or 1
     k = K_HEAD
-    # bounded sample: block rows sized so that each step is ~1-2 s of CPU work
-    rows = min(pat.n_brows, 6000)
-    roff = np.concatenate([[0], np.cumsum(pat.block_sizes())])
-    nnz_s = float(roff[pat.block_row_ptr[rows]])
     T = np.random.default_rng(0).standard_normal((pat.n_cols, k))
-    Tp = np.random.default_rng(1).standard_normal((pat.n_rows, k))
+    rows = min(pat.n_brows, 6000)
+    while True:
+        sub, vals = _first_rows(pat, w.values, rows)
+        Tp = np.random.default_rng(1).standard_normal((sub.n_rows, k))
+        t0 = time.perf_counter()
+        oracle.spmm(sub, vals, T, alpha=2.0, beta=-1.0, Y=Tp, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > 0.3 or rows >= pat.n_brows:
+            break
+        rows = min(pat.n_brows, int(rows * min(16.0, 1.5 / max(dt, 1e-3))))
+    nnz_s = float(sub.nnz)
     for _ in range(args.warmup):
-        oracle.spmm(pat, w.values, T, alpha=2.0, beta=-1.0, Y=Tp, row_range=(0, rows), nthreads=cores)
+        oracle.spmm(sub, vals, T, alpha=2.0, beta=-1.0, Y=Tp, nthreads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.spmm(pat, w.values, T, alpha=2.0, beta=-1.0, Y=Tp, row_range=(0, rows), nthreads=cores)
+        oracle.spmm(sub, vals, T, alpha=2.0, beta=-1.0, Y=Tp, nthreads=cores)
         times.append(time.perf_counter() - t0)
     t = sum(times)
     value = 2.0 * nnz_s * k * args.steps / t / 1e9
