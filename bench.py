@@ -344,7 +344,7 @@ def domains_section(dev, steps):
                     b.record()
                     torch.cuda.synchronize(dev)
                     ms = a.elapsed_time(b) / reps
-                    by = _alg_bytes(pat, k)
+                    by = _alg_bytes(pat, k, 4 if prec == "bf16x2" else 8)   # bf16 pieces: 4 B a value
                     res[f"k{k}_{prec}{tag}"] = {"ms": ms, "gflops": 2.0 * pat.nnz * k / ms / 1e6,
                                                 "gbs": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / hbm}
         out[kind] = res
