@@ -643,6 +643,15 @@ def _build_waves(world, atoms):
         host_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 1e9
     except (ValueError, OSError):
         return world
+    # a container's memory limit, when it has one below the machine's
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            with open(path) as f:
+                lim = f.read().strip()
+            if lim.isdigit():
+                host_gb = min(host_gb, int(lim) / 1e9)
+        except OSError:
+            pass
     per_rank_gb = 3.2e-5 * atoms
     return max(1, min(world, int(0.7 * host_gb / max(per_rank_gb, 1e-9))))
 
