@@ -577,7 +577,7 @@ struct F32Pipe {
     static constexpr int kXRow = NT == 1 ? 48 : PW * 4;   // X row stride (bytes)
     static constexpr int kXBytes = 16 * kXRow;            // X: 16 rows x PW columns
     static constexpr int kBytes = kVBytes + kXBytes;
-    static constexpr int S = NT == 4 ? 3 : 4;             // ring depth (32-column passes: 3, for occupancy)
+    static constexpr int S = NT == 4 ? 3 : NT == 1 ? 5 : 4;   // ring depth: as deep as 5 CTAs per SM allow
 };
 
 __device__ __forceinline__ int f_off(int r, int c) { return r * 64 + 16 * (c ^ (2 * ((r >> 1) & 1))); }
